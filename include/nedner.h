@@ -1,0 +1,166 @@
+/*
+ * nedner.h -- C-ABI of the GB300 NEDNER-NUFFT reconstruction library.
+ *
+ * Schmid et al., "Non-Equispaced Grid Sampling in Photoacoustics with a
+ * Non-Uniform FFT", arXiv:1510.01078.
+ *
+ * The library reconstructs the initial pressure p0(x, y, z) from pressure
+ * time series recorded at M non-equispaced positions (x_m, y_m) of the plane
+ * z = 0 through the discretised Fourier inversion formula (Sec. 2, Eq. exact
+ * and Eq. disc_rec), evaluated with the three-step NEDNER algorithm of Sec. 3:
+ *   (a) a 2-D NED-NUFFT over the sensor positions (Sec. 3.2, Eq. NED_NUFFT),
+ *   (b) a 1-D NER-NUFFT at the non-equispaced temporal frequencies
+ *       nu = sign(l) c Nt dt |k| (Sec. 3.1, Eq. NER_NUFFT),
+ *   (c) the Jacobian factor 2 l / kappa of Eq. exact,
+ *   (d) a uniform inverse 3-D FFT (Sec. 3, step 3).
+ * Every stage runs in hand-written CUDA kernels for sm_103a, in FP32.
+ *
+ * Conventions shared by every entry point
+ *   - Output grid: nx x ny x nz voxels of size dx x dy x dz; voxel (qx,qy,qz)
+ *     is at x = (qx - nx/2) dx, y = (qy - ny/2) dy, z = qz dz.  X = nx dx,
+ *     Y = ny dy, Z = nz dz.
+ *   - The reconstruction R computes
+ *       G[j,n]  = sum_m w_m g[m,n] exp(-2 pi i (jx x_m/X + jy y_m/Y))
+ *       F[j,l]  = W s sum_n G[j,n] exp(-2 pi i nu[j,l] n / Nt)
+ *       p0[q]   = Re (1/(nx ny nz)) sum_{j,l} F[j,l] exp(2 pi i (jx (qx-nx/2)/nx
+ *                                     + jy (qy-ny/2)/ny + l qz/nz))
+ *     over jx in {-nx/2..nx/2-1}, jy in {-ny/2..ny/2-1}, l in {-nz/2..nz/2-1},
+ *     with w_m = h_m/(dx dy), W = 2|l/Z|/|k| (W(0,0) = 2, W(j!=0,0) = 0),
+ *     s = c dt / dz.  With apply_weights = 0, w_m = 1 and W s = 1.
+ *   - Array layouts (row-major, last index fastest):
+ *       sensor_xy  host double [M][2]   positions in metres
+ *       g          device float [M][Nt] time series, t_n = n dt, n fastest
+ *       p0         device float [nz][ny][nx]
+ *       dL_dxy     device float [M][2]
+ *   - All device buffers belong to the caller; the plan owns its tables and
+ *     its workspace.  Calls are asynchronous on the given CUDA stream
+ *     (cudaStream_t passed as void*, NULL = legacy default stream); a status
+ *     other than NEDNER_OK is returned synchronously for argument errors and
+ *     launch failures.  There is no CPU fallback.
+ *   - A plan may be used from one host thread at a time.
+ */
+#ifndef NEDNER_H_
+#define NEDNER_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nedner_plan_s* nedner_plan_t;
+
+typedef enum {
+    NEDNER_OK = 0,
+    NEDNER_EINVAL = 1,  /* bad argument: sizes not powers of two, NULL pointer, ... */
+    NEDNER_ERANGE = 2,  /* a sensor outside the open aperture (-X/2, X/2) x (-Y/2, Y/2) */
+    NEDNER_ENOMEM = 3,  /* host or device allocation failed, or workspace above the limit */
+    NEDNER_ECUDA = 4,   /* a CUDA call failed (no device, launch error, ...) */
+    NEDNER_ENAN = 5     /* reserved: non-finite input detected */
+} nedner_status;
+
+typedef struct {
+    int nx, ny, nz;          /* voxels; each a power of two, 8 <= n <= 2048 */
+    double dx, dy, dz;       /* voxel size (metres), > 0 */
+} nedner_grid;
+
+enum { NEDNER_WINDOW_KB = 0, NEDNER_WINDOW_GAUSS = 1 };
+
+typedef struct {
+    int kind;    /* NEDNER_WINDOW_KB (Kaiser-Bessel, Sec. 3.1) or NEDNER_WINDOW_GAUSS */
+    int width;   /* taps per dimension, w = 2K of Eq. NER_NUFFT; even, 4 <= w <= 16 */
+} nedner_window;
+
+typedef struct {
+    int apply_weights;            /* 1: h_m/(dx dy) and W s (the reconstruction R);
+                                     0: both replaced by 1 */
+    int band_mask;                /* 1: zero F where nu is outside [-Nt/2, Nt/2) */
+    size_t max_workspace_bytes;   /* 0 = no limit; plan fails with ENOMEM above it */
+    const double* sensor_w;       /* host [M] detector areas h_m (m^2), or NULL for X Y / M */
+} nedner_opts;
+
+/*
+ * Build a plan (host tables, device tables, device workspace).
+ *   sensor_xy  host [M][2] metres, each strictly inside (-X/2, X/2) x (-Y/2, Y/2)
+ *              (Sec. 2: x_m in (-X/2, X/2)^{d-1}), else NEDNER_ERANGE.  M >= 0.
+ *   Nt, dt     number (power of two, 8 <= Nt <= 4096) and spacing (s) of time samples.
+ *   c          sound speed (m/s), > 0.
+ *   out_grid   output grid (see nedner_grid).
+ *   window     interpolation window of both NUFFTs (Sec. 3.1-3.2).
+ *   sigma      oversampling factor (the paper's c > 1); this build supports 2.0.
+ *   opts       NULL for defaults {1, 0, 0, NULL}.
+ *   stream     stream used for the table uploads (synchronised before return).
+ *   out        receives the plan; untouched on error.
+ * Returns NEDNER_OK, NEDNER_EINVAL, NEDNER_ERANGE, NEDNER_ENOMEM or NEDNER_ECUDA.
+ */
+nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt, double c,
+                          const nedner_grid* out_grid, nedner_window window, double sigma,
+                          const nedner_opts* opts, void* stream, nedner_plan_t* out);
+
+/*
+ * Move the sensors (same M): rebuilds the per-sensor window taps and the
+ * sensor-to-row tables (Sec. 3.2, the mu_{m,k} and Psi-hat of Eq. NED_NUFFT).
+ * Areas h_m are kept.  Synchronous.  Same range rule as nedner_plan.
+ */
+nedner_status nedner_set_positions(nedner_plan_t plan, const double* sensor_xy);
+
+/*
+ * p0 = R g: the reconstruction of Eq. disc_rec by the NEDNER algorithm (Sec. 3).
+ *   g   device float [M][Nt], read only.
+ *   p0  device float [nz][ny][nx], written (every element).
+ */
+nedner_status nedner_forward(nedner_plan_t plan, const float* g, float* p0, void* stream);
+
+/*
+ * g = R^T p0: the exact transpose of nedner_forward (same real-linear map,
+ * transposed; spreading and interpolation of both NUFFTs swapped).
+ *   p0  device float [nz][ny][nx], read only.
+ *   g   device float [M][Nt], written.
+ */
+nedner_status nedner_adjoint(nedner_plan_t plan, const float* p0, float* g, void* stream);
+
+/*
+ * Sensor-position gradient of a loss L(p0) with p0 = R(x) g and h_m held fixed:
+ *   dL_dxy[m][0] = dL/dx_m,  dL_dxy[m][1] = dL/dy_m   (units: 1/metre times L)
+ * obtained by differentiating the NED exponent of Eq. disc_rec (derivative
+ * window in the interpolation).
+ *   g       device float [M][Nt], dL_dp0 device float [nz][ny][nx], read only.
+ *   dL_dxy  device float [M][2], written.
+ */
+nedner_status nedner_grad_positions(nedner_plan_t plan, const float* g, const float* dL_dp0,
+                                    float* dL_dxy, void* stream);
+
+/*
+ * Stage (a) alone, for inspection: the NED output G[j,n] (without the NER,
+ * weight and inverse FFT) on the half lattice used internally,
+ *   Ghat  device float2 [nx/2+1][ny+1][Nt],  Ghat[a][b][n] = G[(jx=a, jy=b-ny/2), n],
+ * i.e. jx = 0..nx/2 and jy = -ny/2..ny/2 (both Nyquist rows included).
+ */
+nedner_status nedner_ned_stage(nedner_plan_t plan, const float* g, void* Ghat, void* stream);
+
+/*
+ * nedner_forward with per-kernel timing, for measurement: records a CUDA event
+ * around each of the forward kernels on `stream`, waits for the stream, and
+ * writes each kernel's device time in milliseconds to stage_ms (host array of
+ * NEDNER_FORWARD_KERNELS floats, in launch order: spread + x-FFT, y-FFT, NER
+ * lines, y-IFFT, x-c2r).  Synchronous.  Same arguments and errors otherwise.
+ */
+#define NEDNER_FORWARD_KERNELS 5
+nedner_status nedner_forward_profiled(nedner_plan_t plan, const float* g, float* p0, void* stream,
+                                      float* stage_ms);
+
+/* Bytes of device workspace held by the plan. */
+size_t nedner_workspace_bytes(nedner_plan_t plan);
+
+/* Free the plan (synchronises its device work first).  NULL is allowed. */
+nedner_status nedner_destroy(nedner_plan_t plan);
+
+/* Static string for a status code. */
+const char* nedner_strerror(nedner_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEDNER_H_ */

@@ -63,7 +63,7 @@ def _load():
         I64, I, D = ctypes.c_int64, ctypes.c_int, ctypes.c_double
         lib.orc_ned.argtypes = [I64, P, P, I, P, D, D, I, P, I, P, P, I]
         lib.orc_ned.restype = I
-        lib.orc_ner.argtypes = [I64, I, P, I, P, P, I]
+        lib.orc_ner.argtypes = [I64, I, I, P, P, I, P, P, I]
         lib.orc_ner.restype = None
         lib.orc_ner_adj.argtypes = [I64, I, P, I, P, P, I]
         lib.orc_ner_adj.restype = None
@@ -207,12 +207,16 @@ def ned(pr: Problem, g: np.ndarray, jx=None, jy=None) -> np.ndarray:
     return out
 
 
-def ner(pr: Problem, G: np.ndarray, nus: np.ndarray) -> np.ndarray:
-    """NER sum of Eq. disc_rec: F[j, l] = sum_n G[j, n] exp(-2 pi i nu[j, l] n / Nt)."""
-    G = np.ascontiguousarray(G, dtype=np.complex128).reshape(-1, pr.Nt)
+def ner(pr: Problem, G: np.ndarray, nus: np.ndarray, ns=None) -> np.ndarray:
+    """NER sum of Eq. disc_rec: F[j, l] = sum_n G[j, n] exp(-2 pi i nu[j, l] n / Nt).
+    With ``ns`` given, G's columns are the time samples ns (the others zero)."""
+    nn = pr.Nt if ns is None else len(ns)
+    G = np.ascontiguousarray(G, dtype=np.complex128).reshape(-1, nn)
     nus = np.ascontiguousarray(nus, dtype=np.float64).reshape(G.shape[0], -1)
     out = np.zeros(nus.shape, dtype=np.complex128)
-    _load().orc_ner(G.shape[0], pr.Nt, _p(G), nus.shape[1], _p(nus), _p(out), _nthreads())
+    ns32 = None if ns is None else np.ascontiguousarray(ns, dtype=np.int32)
+    _load().orc_ner(G.shape[0], pr.Nt, nn, None if ns32 is None else _p(ns32), _p(G), nus.shape[1],
+                    _p(nus), _p(out), _nthreads())
     return out
 
 
@@ -236,13 +240,20 @@ def _grid_indices(pr: Problem):
     return jx, jy, l, JX, JY, L
 
 
-def spectrum(pr: Problem, g: np.ndarray) -> np.ndarray:
+def spectrum(pr: Problem, g: np.ndarray, ns=None) -> np.ndarray:
     """F[jx, jy, l] over G_x x G_Ky: the right-hand side of Eq. disc_rec times
-    the Riemann step (Sec. 2)."""
+    the Riemann step (Sec. 2).  ``ns``: optional list of the time samples where
+    g may be non-zero (g then has len(ns) columns); the sums skip the zeros."""
     jx, jy, l, JX, JY, L = _grid_indices(pr)
-    G = ned(pr, g, jx, jy)                                   # (nx, ny, Nt)
+    if ns is None:
+        G = ned(pr, g, jx, jy)                               # (nx, ny, Nt)
+        nn = pr.Nt
+    else:
+        nn = len(ns)
+        sub = Problem(**{**pr.__dict__, "Nt": nn})
+        G = ned(sub, g, jx, jy)                              # (nx, ny, nn)
     nus = nu(pr, JX, JY, L).reshape(pr.nx * pr.ny, pr.nz)
-    F = ner(pr, G.reshape(pr.nx * pr.ny, pr.Nt), nus)
+    F = ner(pr, G.reshape(pr.nx * pr.ny, nn), nus, ns)
     return F.reshape(pr.nx, pr.ny, pr.nz) * coef(pr, JX, JY, L)
 
 
@@ -275,9 +286,10 @@ def image_from_spectrum(pr: Problem, F: np.ndarray) -> np.ndarray:
     return np.real(np.fft.ifftn(A))
 
 
-def forward(pr: Problem, g: np.ndarray) -> np.ndarray:
-    """p0 = R g (Sec. 2 Eq. disc_rec followed by Sec. 3 step 3).  (nz, ny, nx)."""
-    return image_from_spectrum(pr, spectrum(pr, g))
+def forward(pr: Problem, g: np.ndarray, ns=None) -> np.ndarray:
+    """p0 = R g (Sec. 2 Eq. disc_rec followed by Sec. 3 step 3).  (nz, ny, nx).
+    ``ns`` as in ``spectrum``."""
+    return image_from_spectrum(pr, spectrum(pr, g, ns))
 
 
 def _dual_spectrum(pr: Problem, p: np.ndarray, sign: int) -> np.ndarray:

@@ -107,21 +107,24 @@ int orc_ned(int64_t M, const double* xy, const double* w, int Nt, const double* 
  * NER sum of Eq. disc_rec (Sec. 2; Eq. NUDFT1 of Sec. 3.1), one line at a time:
  *   F[j][l] = sum_{n=0}^{Nt-1} G[j][n] exp(-2 pi i nu[j][l] n / Nt)
  * with nu the non-equispaced temporal frequency of the kappa mapping.
+ * G holds nn columns per line, column i being time sample ns[i] (ns = NULL:
+ * all Nt samples in order); samples not listed are zero and add nothing.
  */
-void orc_ner(int64_t nlines, int Nt, const double* G, int nl, const double* nu,
-             double* F, int nthreads) {
+void orc_ner(int64_t nlines, int Nt, int nn, const int* ns, const double* G, int nl,
+             const double* nu, double* F, int nthreads) {
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t j = 0; j < nlines; ++j) {
-        const double* Gj = G + 2 * (size_t)j * Nt;
+        const double* Gj = G + 2 * (size_t)j * nn;
         for (int l = 0; l < nl; ++l) {
             double v = nu[(size_t)j * nl + l];
             double sr = 0.0, si = 0.0;
-            for (int n = 0; n < Nt; ++n) {
+            for (int i = 0; i < nn; ++i) {
+                int n = ns ? ns[i] : i;
                 double ph = -TWO_PI * (v * (double)n / (double)Nt);
                 double c = cos(ph), s = sin(ph);
-                sr += Gj[2 * n] * c - Gj[2 * n + 1] * s;
-                si += Gj[2 * n] * s + Gj[2 * n + 1] * c;
+                sr += Gj[2 * i] * c - Gj[2 * i + 1] * s;
+                si += Gj[2 * i] * s + Gj[2 * i + 1] * c;
             }
             F[2 * ((size_t)j * nl + l) + 0] = sr;
             F[2 * ((size_t)j * nl + l) + 1] = si;

@@ -1,0 +1,390 @@
+// Forward NEDNER kernels (the reconstruction R of Eq. disc_rec, Sec. 3).
+//
+// Data flow (all intermediates complex64, n / qz / qy fastest as noted):
+//   g [M][Nt]
+//     -- ned_spread_xfft -->  R    [nx/2+1][Ly][Nt]   spread along y and x, x-FFT
+//     -- ned_yfft         -->  Ghat [nx/2+1][ny+1][Nt] y-FFT, crop, deconvolve
+//     -- ner_lines        -->  V    [nx/2+1][ny][nz]   NER, Jacobian, z-IFFT
+//     -- img_yifft        -->  Y    [nx/2+1][nz][ny]   y-IFFT
+//     -- img_xc2r         -->  p0   [nz][ny][nx]       x complex-to-real IFFT
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace nedner {
+
+// ---------------------------------------------------------------------------
+// Stage (a), part 1: NED spreading (Eq. NED_NUFFT) fused with the x-FFT.
+// One CTA owns grid row gy and C consecutive time samples.  It spreads every
+// (sensor, y tap) entry of that row into a shared-memory row [Lx][C] (window
+// taps w along x), then transforms the row along x (two real columns packed
+// into one complex FFT) and keeps jx = 0..nx/2, divided by phihat(jx/Lx).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ned_spread_xfft(Geo G, int C, const float* __restrict__ g,
+                                                         const int* __restrict__ row_ptr,
+                                                         const int* __restrict__ row_m,
+                                                         const float* __restrict__ row_w,
+                                                         const int* __restrict__ sens_bx,
+                                                         const float* __restrict__ sens_wx,
+                                                         const float* __restrict__ deconv_x,
+                                                         const float2* __restrict__ tw, float2* __restrict__ R) {
+    extern __shared__ float4 smem4[];
+    float* S = reinterpret_cast<float*>(smem4);                  // [Lx][C] real row
+    float2* B2 = reinterpret_cast<float2*>(S + (size_t)G.Lx * C);  // [Lx][C/2] scratch
+    const int gy = blockIdx.x;
+    const int n0 = blockIdx.y * C;
+    const int Lx = G.Lx;
+
+    for (int i = threadIdx.x; i < Lx * C; i += blockDim.x) S[i] = 0.f;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int per_warp = 32 / C;                 // entries handled side by side in a warp
+    const int sub = lane / C;
+    const int ln = lane - sub * C;
+    const int groups = (blockDim.x >> 5) * per_warp;
+    const int e_end = row_ptr[gy + 1];
+    if (sub < per_warp) {
+        for (int e = row_ptr[gy] + warp * per_warp + sub; e < e_end; e += groups) {
+            const int m = row_m[e];
+            const float val = row_w[e] * __ldg(&g[(size_t)m * G.Nt + n0 + ln]);
+            const int bx = sens_bx[m];
+            const float* wx = sens_wx + (size_t)m * G.w;
+            for (int k = 0; k < G.w; ++k) atomicAdd(&S[((bx + k) & (Lx - 1)) * C + ln], __ldg(&wx[k]) * val);
+        }
+    }
+
+    const int nb = C / 2;
+    float2* res = block_fft(reinterpret_cast<float2*>(S), B2, Lx, nb, nb, -1, tw);
+
+    const int items = G.nxh * C;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int jx = it / C;
+        const int c = it - jx * C;
+        const int b = c >> 1;
+        const float2 zk = res[jx * nb + b];
+        const float2 zm = cconj(res[((Lx - jx) & (Lx - 1)) * nb + b]);
+        // column 2b = (Z[k] + conj Z[-k]) / 2, column 2b+1 = -i (Z[k] - conj Z[-k]) / 2
+        float2 x = (c & 1) ? mul_i(csub(zk, zm), -1) : cadd(zk, zm);
+        x = cscale(x, 0.5f * __ldg(&deconv_x[jx]));
+        R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage (a), part 2: y-FFT of length Ly for one jx and C time samples; keeps
+// jy = -ny/2..ny/2 (both Nyquist rows) divided by phihat(jy/Ly).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ned_yfft(Geo G, int C, const float2* __restrict__ R,
+                                                  const float* __restrict__ deconv_y,
+                                                  const float2* __restrict__ tw, float2* __restrict__ Ghat) {
+    extern __shared__ float4 smem4[];
+    float2* A = reinterpret_cast<float2*>(smem4);
+    float2* B = A + (size_t)G.Ly * C;
+    const int jx = blockIdx.x;
+    const int n0 = blockIdx.y * C;
+    for (int it = threadIdx.x; it < G.Ly * C; it += blockDim.x) {
+        const int gy = it / C;
+        const int c = it - gy * C;
+        A[it] = R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c];
+    }
+    float2* res = block_fft(A, B, G.Ly, C, C, -1, tw);
+    const int items = G.nyp * C;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int b = it / C;                  // jy = b - ny/2
+        const int c = it - b * C;
+        const int q = (b - G.ny / 2 + G.Ly) & (G.Ly - 1);
+        Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c] = cscale(res[q * C + c], __ldg(&deconv_y[b]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage (b)+(c)+(z part of d): one CTA per line group (kx, ky),
+// kx = 0..nx/2, ky = -ny/2..ny/2-1.
+//
+// NER (Eq. NER_NUFFT): the line's samples, divided by phihat((n - Nt/2)/Lt)
+// and centred (theta = 2 pi n/N - pi), are zero-padded to Lt and FFT'd; the
+// value at nu is exp(-i pi nu) sum_k P_k(t) B[mu0 + k] with v = sigma nu,
+// mu0 = floor(v) - w/2 + 1, t = v - floor(v).  nu = sign(l) sqrt(axy + az l^2)
+// is formed in float-float arithmetic (FP32 pairs) so that the fractional
+// offset t keeps FP32 accuracy for |v| in the thousands.
+//
+// The real part of the inverse 3-D DFT over G_x x G_Ky is rebuilt from the
+// half lattice kx = 0..nx/2 (kx = nx/2 standing for -nx/2):
+//   kx < nx/2 : U[l] = (F(kx, ky, l) + F(kx, ky*, l*)) / 2
+//   kx = nx/2 : U[l] = F(nx/2, ky*, l*)
+// where * maps -n/2 to +n/2 and leaves other indices alone (ky* = ky except
+// ky* = +ny/2 for ky = -ny/2, which brings in the extra line jy = +ny/2).
+// U is multiplied by the Jacobian W, the scale and the voxel-centring sign
+// (-1)^(kx+ky), then inverse-transformed along z.
+// ---------------------------------------------------------------------------
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+__device__ __forceinline__ FF quick_two_sum(float a, float b) {
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+
+// nu^2 = axy + az * l^2 (float-float), then nu = sqrt(.) (float-float)
+__device__ __forceinline__ FF nu_abs(const Geo& G, float2 axy, int l) {
+    const float L2 = (float)(l * l);              // exact for |l| < 4096
+    const float p_hi = G.az_hi * L2;
+    const float p_lo = fmaf(G.az_hi, L2, -p_hi) + G.az_lo * L2;
+    FF s = two_sum(axy.x, p_hi);
+    s = quick_two_sum(s.hi, s.lo + axy.y + p_lo);
+    if (s.hi <= 0.f) return {0.f, 0.f};
+    const float r = sqrtf(s.hi);
+    const float resid = fmaf(-r, r, s.hi) + s.lo;
+    return quick_two_sum(r, resid * (0.5f / r));
+}
+
+__device__ __forceinline__ float tap_poly(const float* __restrict__ cf, int D, float s) {
+    float p = cf[D];
+    for (int d = D - 1; d >= 0; --d) p = fmaf(p, s, cf[d]);
+    return p;
+}
+
+__global__ void __launch_bounds__(256) k_ner_lines(Geo G, const float2* __restrict__ Ghat,
+                                                   const float2* __restrict__ axy_tab,
+                                                   const float* __restrict__ deconv_t,
+                                                   const float* __restrict__ tapcoef,
+                                                   const float2* __restrict__ tw, float2* __restrict__ V) {
+    extern __shared__ float4 smem4[];
+    float2* LA = reinterpret_cast<float2*>(smem4);   // [Lt]
+    float2* LB = LA + G.Lt;                          // [Lt]
+    float2* T = LB + G.Lt;                           // [nz + 1] values at l = -nz/2..nz/2
+    float2* UA = T + (G.nz + 1);                     // [nz]
+    float2* UB = UA + G.nz;                          // [nz]
+    float* cf = reinterpret_cast<float*>(UB + G.nz); // [w][D+1]
+
+    const int grp = blockIdx.x;
+    const int kx = grp / G.ny;
+    const int ky = grp - kx * G.ny - G.ny / 2;       // -ny/2..ny/2-1
+    const int kyb = (ky == -G.ny / 2) ? G.ny / 2 : ky;
+    const bool nyq_x = (kx == G.nx / 2);
+    const float ca = nyq_x ? 0.f : 0.5f;
+    const float cb = nyq_x ? 1.f : 0.5f;
+    const int half_nz = G.nz / 2;
+    const int ncf = G.w * (G.D + 1);
+
+    for (int i = threadIdx.x; i < ncf; i += blockDim.x) cf[i] = tapcoef[i];
+    for (int i = threadIdx.x; i < G.nz; i += blockDim.x) UA[i] = make_float2(0.f, 0.f);
+
+    // lines to evaluate: a = (kx, ky) unless its coefficient is zero, b = (kx, kyb)
+    const int nlines = (nyq_x || ky == kyb) ? 1 : 2;
+    for (int li = 0; li < nlines; ++li) {
+        const int lky = (li == 0 && nlines == 2) ? ky : kyb;
+        const size_t line = (size_t)kx * G.nyp + (lky + G.ny / 2);
+        const float2 axy = __ldg(&axy_tab[line]);
+        const bool is_a = !nyq_x && (lky == ky);
+        const bool is_b = (lky == kyb);
+
+        // centred, deconvolved, zero-padded line
+        __syncthreads();
+        for (int p = threadIdx.x; p < G.Lt; p += blockDim.x) LA[p] = make_float2(0.f, 0.f);
+        __syncthreads();
+        const float2* src = Ghat + line * G.Nt;
+        for (int n = threadIdx.x; n < G.Nt; n += blockDim.x)
+            LA[(n - G.Nt / 2) & (G.Lt - 1)] = cscale(src[n], __ldg(&deconv_t[n]));
+        float2* Bf = block_fft(LA, LB, G.Lt, 1, 1, -1, tw);
+
+        // NER values at l = -nz/2..nz/2
+        for (int e = threadIdx.x; e <= G.nz; e += blockDim.x) {
+            const int l = e - half_nz;
+            float2 val = make_float2(0.f, 0.f);
+            FF nu = nu_abs(G, axy, l);
+            float W;
+            if (l == 0) {
+                W = (kx == 0 && lky == 0) ? 2.f : 0.f;
+                nu = {0.f, 0.f};
+            } else {
+                W = 2.f * G.sqrt_az * (float)abs(l) / nu.hi;
+                if (l < 0) nu = {-nu.hi, -nu.lo};
+            }
+            float cl = G.apply_weights ? W * G.scale : G.scale;
+            if (G.band_mask) {
+                const double nd = (double)nu.hi + (double)nu.lo;
+                if (!(nd >= -0.5 * G.Nt - 1e-9 && nd < 0.5 * G.Nt - 1e-9)) cl = 0.f;
+            }
+            if (cl != 0.f) {
+                // v = sigma nu (sigma = 2): exact scaling of the pair
+                const float vh = 2.f * nu.hi, vl = 2.f * nu.lo;
+                float fl = floorf(vh);
+                float t = (vh - fl) + vl;
+                if (t < 0.f) { t += 1.f; fl -= 1.f; }
+                if (t >= 1.f) { t -= 1.f; fl += 1.f; }
+                const int ifl = (int)fl;
+                const int mu0 = ifl - G.w / 2 + 1;
+                const float s = 2.f * t - 1.f;
+                float2 acc = make_float2(0.f, 0.f);
+                for (int k = 0; k < G.w; ++k) {
+                    const float wk = tap_poly(cf + k * (G.D + 1), G.D, s);
+                    const float2 b = Bf[(mu0 + k) & (G.Lt - 1)];
+                    acc.x = fmaf(wk, b.x, acc.x);
+                    acc.y = fmaf(wk, b.y, acc.y);
+                }
+                // exp(-i pi nu) = exp(-i pi v/2) = (-i)^floor(v) exp(-i pi t / 2)
+                float sn, cs;
+                sincospif(0.5f * t, &sn, &cs);
+                float2 ph = make_float2(cs, -sn);
+                const int q = ifl & 3;
+                if (q == 1) ph = make_float2(ph.y, -ph.x);
+                else if (q == 2) ph = make_float2(-ph.x, -ph.y);
+                else if (q == 3) ph = make_float2(-ph.y, ph.x);
+                val = cscale(cmul(ph, acc), cl);
+            }
+            T[e] = val;
+        }
+        __syncthreads();
+        // fold into U (slot l mod nz, l = -nz/2..nz/2-1)
+        for (int l0 = threadIdx.x; l0 < G.nz; l0 += blockDim.x) {
+            const int l = l0 - half_nz;
+            float2 u = UA[l & (G.nz - 1)];
+            if (is_a) u = cadd(u, cscale(T[l0], ca));
+            if (is_b) {
+                const int estar = (l == -half_nz) ? G.nz : l0;    // l* = +nz/2 for l = -nz/2
+                u = cadd(u, cscale(T[estar], cb));
+            }
+            UA[l & (G.nz - 1)] = u;
+        }
+    }
+
+    float2* Uz = block_fft(UA, UB, G.nz, 1, 1, +1, tw);
+    const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
+    float2* dst = V + ((size_t)kx * G.ny + (ky & (G.ny - 1))) * G.nz;
+    for (int q = threadIdx.x; q < G.nz; q += blockDim.x) dst[q] = cscale(Uz[q], sg);
+}
+
+// ---------------------------------------------------------------------------
+// Stage (d), y part: inverse FFT along ky for one kx and C depth planes,
+// written transposed as Y[kx][qz][qy].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_img_yifft(Geo G, int C, const float2* __restrict__ V,
+                                                   const float2* __restrict__ tw, float2* __restrict__ Y) {
+    extern __shared__ float4 smem4[];
+    const int ld = C + 1;
+    float2* A = reinterpret_cast<float2*>(smem4);
+    float2* B = A + (size_t)G.ny * ld;
+    const int kx = blockIdx.x;
+    const int z0 = blockIdx.y * C;
+    for (int it = threadIdx.x; it < G.ny * C; it += blockDim.x) {
+        const int ky = it / C;
+        const int c = it - ky * C;
+        A[ky * ld + c] = V[((size_t)kx * G.ny + ky) * G.nz + z0 + c];
+    }
+    float2* res = block_fft(A, B, G.ny, C, ld, +1, tw);
+    for (int it = threadIdx.x; it < G.ny * C; it += blockDim.x) {
+        const int c = it / G.ny;
+        const int qy = it - c * G.ny;
+        Y[((size_t)kx * G.nz + z0 + c) * G.ny + qy] = res[qy * ld + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage (d), x part: complex-to-real inverse FFT of length nx from the half
+// spectrum kx = 0..nx/2 (imaginary parts of kx = 0 and nx/2 dropped, i.e. the
+// real part of the full inverse DFT), for one qz and C rows qy.  Uses the
+// half-length complex transform: Z[k] = E[k] + i O[k],
+// E = X[k] + conj X[H-k], O = (X[k] - conj X[H-k]) exp(2 pi i k / nx),
+// z = IFFT_H(Z), p0[2p] = Re z[p], p0[2p+1] = Im z[p].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, const float2* __restrict__ Y,
+                                                  const float2* __restrict__ tw, float* __restrict__ p0) {
+    extern __shared__ float4 smem4[];
+    const int H = G.nx / 2;
+    const int ld = C + 1;
+    float2* X = reinterpret_cast<float2*>(smem4);   // [H+1][ld]
+    float2* A = X + (size_t)(H + 1) * ld;           // [H][ld]
+    float2* B = A + (size_t)H * ld;                 // [H][ld]
+    const int qz = blockIdx.x;
+    const int y0 = blockIdx.y * C;
+    for (int it = threadIdx.x; it < (H + 1) * C; it += blockDim.x) {
+        const int kx = it / C;
+        const int c = it - kx * C;
+        X[kx * ld + c] = Y[((size_t)kx * G.nz + qz) * G.ny + y0 + c];
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < H * C; it += blockDim.x) {
+        const int k = it / C;
+        const int c = it - k * C;
+        float2 xk = X[k * ld + c];
+        float2 xm = X[(H - k) * ld + c];
+        if (k == 0) {
+            xk.y = 0.f;
+            xm.y = 0.f;
+        }
+        const float2 xmc = cconj(xm);
+        const float2 E = cadd(xk, xmc);
+        const float2 O = cmul(csub(xk, xmc), twiddle(tw, k, G.nx, +1));
+        A[k * ld + c] = cadd(E, mul_i(O, +1));
+    }
+    float2* res = block_fft(A, B, H, C, ld, +1, tw);
+    for (int it = threadIdx.x; it < H * C; it += blockDim.x) {
+        const int c = it / H;
+        const int pp = it - c * H;
+        const float2 z = res[pp * ld + c];
+        reinterpret_cast<float2*>(p0 + ((size_t)qz * G.ny + y0 + c) * G.nx)[pp] = z;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem1))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_yfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2))) return e;
+    if ((e = cudaFuncSetAttribute(k_ner_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem3))) return e;
+    if ((e = cudaFuncSetAttribute(k_img_yifft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem4))) return e;
+    if ((e = cudaFuncSetAttribute(k_img_xc2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem5))) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float2* R, cudaStream_t s) {
+    const Geo& G = p.geo;
+    dim3 grid(G.Ly, G.Nt / p.ch.c1);
+    k_ned_spread_xfft<<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.row_ptr, p.t.row_m, p.t.row_w,
+                                                    p.t.sens_bx, p.t.sens_wx, p.t.deconv_x, p.t.tw, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s) {
+    const Geo& G = p.geo;
+    dim3 grid(G.nxh, G.Nt / p.ch.c2);
+    k_ned_yfft<<<grid, 256, p.ch.smem2, s>>>(G, p.ch.c2, R, p.t.deconv_y, p.t.tw, Ghat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ner_lines(const nedner_plan_s& p, const float2* Ghat, float2* V, cudaStream_t s) {
+    const Geo& G = p.geo;
+    dim3 grid(G.nxh * G.ny);
+    k_ner_lines<<<grid, 256, p.ch.smem3, s>>>(G, Ghat, p.t.axy, p.t.deconv_t, p.t.tapcoef, p.t.tw, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_img_yifft(const nedner_plan_s& p, const float2* V, float2* Y, cudaStream_t s) {
+    const Geo& G = p.geo;
+    dim3 grid(G.nxh, G.nz / p.ch.c4);
+    k_img_yifft<<<grid, 256, p.ch.smem4, s>>>(G, p.ch.c4, V, p.t.tw, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_img_xc2r(const nedner_plan_s& p, const float2* Y, float* p0, cudaStream_t s) {
+    const Geo& G = p.geo;
+    dim3 grid(G.nz, G.ny / p.ch.c5);
+    k_img_xc2r<<<grid, 256, p.ch.smem5, s>>>(G, p.ch.c5, Y, p.t.tw, p0);
+    return cudaGetLastError();
+}
+
+}  // namespace nedner

@@ -1,0 +1,220 @@
+"""Thin Python binding of the C-ABI in ``include/nedner.h`` (ctypes).
+
+Argument marshalling only: every stage of the reconstruction runs in the CUDA
+library ``_build/libnedner.so``.  Tensors are torch CUDA tensors (device
+memory and streams come from PyTorch); there is no CPU fallback -- opening the
+library fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libnedner.so")
+
+OK, EINVAL, ERANGE, ENOMEM, ECUDA, ENAN = range(6)
+WINDOW_KB, WINDOW_GAUSS = 0, 1
+
+_lib = None
+
+
+class NednerError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _load().nedner_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__("%s: %s (status %d)" % (where, msg, status))
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+class _Window(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("width", ctypes.c_int)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("apply_weights", ctypes.c_int), ("band_mask", ctypes.c_int),
+                ("max_workspace_bytes", ctypes.c_size_t), ("sensor_w", ctypes.c_void_p)]
+
+
+# symbol -> (restype, argtypes); mirrors include/nedner.h
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "nedner_plan": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(_Grid), _Window, ctypes.c_double, ctypes.POINTER(_Opts),
+                                   _P, ctypes.POINTER(_P)]),
+    "nedner_set_positions": (ctypes.c_int, [_P, _P]),
+    "nedner_forward": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nedner_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nedner_grad_positions": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "nedner_ned_stage": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nedner_forward_profiled": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
+    "nedner_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "nedner_destroy": (ctypes.c_int, [_P]),
+    "nedner_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing; build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def library():
+    """The loaded ctypes library (raises if missing)."""
+    return _load()
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise NednerError(status, where)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, shape: Sequence[int], name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s tensor of shape %s (got %s %s)"
+                         % (name, dtype, tuple(shape), t.dtype, tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A reconstruction plan (``nedner_plan``): geometry, tables, workspace.
+
+    sensor_xy: (M, 2) positions in metres (array-like, float64 on the host).
+    grid: (nx, ny, nz, dx, dy, dz).  window: ("kb"|"gauss", width).
+    """
+
+    def __init__(self, sensor_xy, Nt: int, dt: float, c: float, grid, window=("kb", 12), sigma: float = 2.0,
+                 apply_weights: bool = True, band_mask: bool = False, sensor_w=None,
+                 max_workspace_bytes: int = 0, stream=None):
+        lib = _load()
+        self._xy = np.ascontiguousarray(np.asarray(sensor_xy, dtype=np.float64).reshape(-1, 2))
+        self.M = int(self._xy.shape[0])
+        self.Nt = int(Nt)
+        self.nx, self.ny, self.nz = int(grid[0]), int(grid[1]), int(grid[2])
+        self.grid = tuple(grid)
+        g = _Grid(self.nx, self.ny, self.nz, float(grid[3]), float(grid[4]), float(grid[5]))
+        kind = {"kb": WINDOW_KB, "gauss": WINDOW_GAUSS}[window[0]] if isinstance(window[0], str) else int(window[0])
+        w = _Window(kind, int(window[1]))
+        self._h = None if sensor_w is None else np.ascontiguousarray(np.asarray(sensor_w, dtype=np.float64))
+        opts = _Opts(int(bool(apply_weights)), int(bool(band_mask)), int(max_workspace_bytes),
+                     None if self._h is None else self._h.ctypes.data)
+        handle = ctypes.c_void_p()
+        st = lib.nedner_plan(self._xy.ctypes.data if self.M else None, self.M, self.Nt, float(dt), float(c),
+                             ctypes.byref(g), w, float(sigma), ctypes.byref(opts), _stream_ptr(stream),
+                             ctypes.byref(handle))
+        _check(st, "nedner_plan")
+        self._handle = handle
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_handle", None) is not None and self._handle.value:
+            _load().nedner_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(_load().nedner_workspace_bytes(self._handle))
+
+    def set_positions(self, sensor_xy):
+        xy = np.ascontiguousarray(np.asarray(sensor_xy, dtype=np.float64).reshape(self.M, 2))
+        _check(_load().nedner_set_positions(self._handle, xy.ctypes.data if self.M else None),
+               "nedner_set_positions")
+        self._xy = xy
+
+    # -- compute ----------------------------------------------------------
+    def forward(self, g, out=None, stream=None):
+        """p0 = R g.  g: (M, Nt) float32 CUDA tensor -> (nz, ny, nx)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.nz, self.ny, self.nx), dtype=torch.float32, device=g.device)
+        st = _load().nedner_forward(self._handle, _dev_ptr(g, torch.float32, (self.M, self.Nt), "g"),
+                                    _dev_ptr(out, torch.float32, (self.nz, self.ny, self.nx), "p0"),
+                                    _stream_ptr(stream))
+        _check(st, "nedner_forward")
+        return out
+
+    FORWARD_KERNELS = ("ned_spread_xfft", "ned_yfft", "ner_lines", "img_yifft", "img_xc2r")
+
+    def forward_profiled(self, g, out, stream=None):
+        """forward() that also returns each kernel's device time (ms), synchronously."""
+        import torch
+        ms = (ctypes.c_float * len(self.FORWARD_KERNELS))()
+        st = _load().nedner_forward_profiled(self._handle, _dev_ptr(g, torch.float32, (self.M, self.Nt), "g"),
+                                             _dev_ptr(out, torch.float32, (self.nz, self.ny, self.nx), "p0"),
+                                             _stream_ptr(stream), ms)
+        _check(st, "nedner_forward_profiled")
+        return dict(zip(self.FORWARD_KERNELS, [float(v) for v in ms]))
+
+    def adjoint(self, p0, out=None, stream=None):
+        """g = R^T p0.  p0: (nz, ny, nx) -> (M, Nt)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.M, self.Nt), dtype=torch.float32, device=p0.device)
+        st = _load().nedner_adjoint(self._handle, _dev_ptr(p0, torch.float32, (self.nz, self.ny, self.nx), "p0"),
+                                    _dev_ptr(out, torch.float32, (self.M, self.Nt), "g"), _stream_ptr(stream))
+        _check(st, "nedner_adjoint")
+        return out
+
+    def grad_positions(self, g, dL_dp0, out=None, stream=None):
+        """dL/d(x_m, y_m): (M, 2)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.M, 2), dtype=torch.float32, device=g.device)
+        st = _load().nedner_grad_positions(
+            self._handle, _dev_ptr(g, torch.float32, (self.M, self.Nt), "g"),
+            _dev_ptr(dL_dp0, torch.float32, (self.nz, self.ny, self.nx), "dL_dp0"),
+            _dev_ptr(out, torch.float32, (self.M, 2), "dL_dxy"), _stream_ptr(stream))
+        _check(st, "nedner_grad_positions")
+        return out
+
+    def ned_stage(self, g, stream=None):
+        """Stage (a) output: complex64 (nx/2+1, ny+1, Nt), jx = 0..nx/2, jy = -ny/2..ny/2."""
+        import torch
+        out = torch.empty((self.nx // 2 + 1, self.ny + 1, self.Nt), dtype=torch.complex64, device=g.device)
+        st = _load().nedner_ned_stage(self._handle, _dev_ptr(g, torch.float32, (self.M, self.Nt), "g"),
+                                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+        _check(st, "nedner_ned_stage")
+        return out
+
+
+def plan_from_config(cfg, **kw) -> Plan:
+    """Plan for a workload dict as produced by ``inputs.make_config``/``small_case``."""
+    return Plan(cfg["sensor_xy"], cfg["Nt"], cfg["dt"], cfg["c"],
+                (cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"]),
+                sensor_w=kw.pop("sensor_w", cfg.get("h")), **kw)
+
+
+__all__ = ["Plan", "plan_from_config", "NednerError", "library", "LIB_PATH", "SIGNATURES",
+           "WINDOW_KB", "WINDOW_GAUSS"]

@@ -1,0 +1,164 @@
+"""Parity of the CUDA forward path (nedner_forward, nedner_ned_stage) with the
+FP64 oracle, element by element, on seeded inputs.
+
+Tolerance: relative L2 error <= 1e-5 over the whole output for the FP32 path
+with the Kaiser-Bessel window, w = 12, sigma = 2.  The window's own
+interpolation error there is ~1e-11, so the budget is FP32 rounding: about
+1e-7 per operation through a spread of 144 taps and five FFT passes of length
+up to 4096 (log2 N ~ 12 stages each), i.e. a few 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Problem
+from paper_1510_01078_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def nd():
+    from paper_1510_01078_gb300 import build
+    build.build()
+    from paper_1510_01078_gb300 import nedner
+    assert torch.cuda.is_available()
+    return nedner
+
+
+def problem(case, **kw):
+    return Problem(sensor_xy=case["sensor_xy"], h=case["h"], Nt=case["Nt"], dt=case["dt"], c=case["c"],
+                   nx=case["nx"], ny=case["ny"], nz=case["nz"], dx=case["dx"], dy=case["dy"], dz=case["dz"], **kw)
+
+
+def gpu_forward(nd, case, g=None, **kw):
+    plan = nd.plan_from_config(case, **kw)
+    gg = torch.as_tensor(np.asarray(case["g"] if g is None else g, dtype=np.float32), device="cuda")
+    out = plan.forward(gg)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy().astype(np.float64)
+    plan.close()
+    return res
+
+
+SMALL = [
+    dict(nx=16, ny=16, nz=32, M=37, Nt=64, seed=1, layout="scatter"),
+    dict(nx=32, ny=16, nz=64, M=301, Nt=128, seed=2, layout="disc"),
+    dict(nx=16, ny=32, nz=16, M=1000, Nt=32, seed=3, layout="scatter"),
+    dict(nx=8, ny=8, nz=8, M=5, Nt=16, seed=4, layout="scatter"),
+    dict(nx=32, ny=32, nz=32, M=333, Nt=256, seed=5, layout="disc", data="balls"),
+    dict(nx=16, ny=16, nz=16, M=256, Nt=32, seed=6, layout="grid"),
+]
+
+
+@pytest.mark.parametrize("spec", SMALL, ids=lambda s: "{nx}x{ny}x{nz}_M{M}_Nt{Nt}_{layout}".format(**s))
+def test_forward_matches_oracle_small(nd, spec):
+    case = inputs.small_case(**spec)
+    want = oracle.forward(problem(case), case["g"])
+    got = gpu_forward(nd, case)
+    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+
+
+@pytest.mark.parametrize("spec", SMALL[:3], ids=lambda s: "{nx}x{ny}_M{M}_Nt{Nt}".format(**s))
+def test_ned_stage_matches_oracle(nd, spec):
+    case = inputs.small_case(**spec)
+    pr = problem(case)
+    jx = np.arange(0, pr.nx // 2 + 1)
+    jy = np.arange(-(pr.ny // 2), pr.ny // 2 + 1)
+    want = oracle.ned(pr, case["g"], jx, jy)
+    plan = nd.plan_from_config(case)
+    got = plan.ned_stage(torch.as_tensor(case["g"], dtype=torch.float32, device="cuda")).cpu().numpy()
+    plan.close()
+    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+
+
+def test_forward_c1_tiny(nd):
+    """Workload 1: 16x16 centre-dense tensor sensors, Nt 64, 16x16x32 voxels, two balls."""
+    case = inputs.make_config(0)
+    want = oracle.forward(problem(case), case["g"])
+    got = gpu_forward(nd, case)
+    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+
+
+def test_forward_c2_full_size(nd):
+    """Workload 2 at full size (64x64 sensors, Nt 512, 128x128x256), dense noisy data."""
+    case = inputs.make_config(1)
+    want = oracle.forward(problem(case), case["g"])
+    got = gpu_forward(nd, case)
+    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+
+
+def test_forward_c3_full_size_sparse_time(nd):
+    """Workload 3 geometry at full size (16384 scattered sensors, Nt 2048,
+    256x256x512) with data non-zero at four time samples only, so the oracle's
+    direct sums finish in seconds; every voxel is compared."""
+    case = inputs.make_config(2, with_data=False)
+    rng = np.random.default_rng(77)
+    ns = np.array([3, 400, 1023, 1990])
+    gs = rng.standard_normal((case["sensor_xy"].shape[0], len(ns)))
+    g = np.zeros((gs.shape[0], case["Nt"]))
+    g[:, ns] = gs
+    want = oracle.forward(problem(case), gs, ns=ns)
+    got = gpu_forward(nd, case, g=g)
+    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+
+
+@pytest.mark.parametrize("opt", ["unweighted", "band_mask", "gauss16", "kb8"])
+def test_forward_options(nd, opt):
+    case = inputs.small_case(16, 16, 32, 77, 64, seed=11, layout="disc")
+    kw, okw, tol = {}, {}, TOL
+    if opt == "unweighted":
+        kw["apply_weights"] = okw["apply_weights"] = False
+    elif opt == "band_mask":
+        kw["band_mask"] = okw["band_mask"] = True
+    elif opt == "gauss16":
+        kw["window"] = ("gauss", 16)
+        tol = 1e-4                      # Gaussian w = 16 interpolation error ~ 3e-8 per axis, times FP32
+    elif opt == "kb8":
+        kw["window"] = ("kb", 8)
+        tol = 1e-4                      # KB w = 8 interpolation error ~ 2e-7
+    want = oracle.forward(problem(case, **okw), case["g"])
+    got = gpu_forward(nd, case, **kw)
+    assert rel_l2(got, want) <= tol, rel_l2(got, want)
+
+
+def test_forward_no_sensors(nd):
+    case = inputs.small_case(16, 16, 16, 0, 32, seed=12)
+    plan = nd.plan_from_config(case)
+    out = plan.forward(torch.zeros((0, 32), dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) == 0.0
+    plan.close()
+
+
+def test_forward_is_linear_and_repeatable(nd):
+    case = inputs.small_case(16, 16, 32, 50, 64, seed=13)
+    plan = nd.plan_from_config(case)
+    g = torch.as_tensor(case["g"], dtype=torch.float32, device="cuda")
+    a = plan.forward(g).clone()
+    b = plan.forward(2.0 * g)
+    c = plan.forward(g)
+    torch.cuda.synchronize()
+    assert rel_l2((b / 2).cpu().numpy(), a.cpu().numpy()) < 1e-6
+    assert rel_l2(c.cpu().numpy(), a.cpu().numpy()) < 1e-6
+    plan.close()
+
+
+def test_set_positions_matches_fresh_plan(nd):
+    case = inputs.small_case(16, 16, 32, 40, 64, seed=14)
+    plan = nd.plan_from_config(case)
+    xy2 = case["sensor_xy"] * 0.9 + 1e-5
+    plan.set_positions(xy2)
+    g = torch.as_tensor(case["g"], dtype=torch.float32, device="cuda")
+    a = plan.forward(g).cpu().numpy()
+    case2 = dict(case, sensor_xy=xy2)
+    want = oracle.forward(problem(case2), case["g"])
+    assert rel_l2(a, want) <= TOL
+    plan.close()
