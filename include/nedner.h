@@ -150,6 +150,40 @@ nedner_status nedner_ned_stage(nedner_plan_t plan, const float* g, void* Ghat, v
 nedner_status nedner_forward_profiled(nedner_plan_t plan, const float* g, float* p0, void* stream,
                                       float* stage_ms);
 
+/*
+ * nedner_ned_stage without touching the plan's workspace and without any
+ * device allocation: the same two kernels, with their intermediate array
+ * ([nx/2+1][2 ny][Nt] complex64) in a fixed buffer of
+ * NEDNER_STATIC_SCRATCH_BYTES that is part of the library's device image.
+ * The paper has no counterpart to this entry point.
+ *
+ * Who needs it: callers that cannot call cudaMalloc at the moment they run
+ * the stage -- code being recorded into a CUDA graph (allocation is not a
+ * stream operation and breaks the capture), applications whose device memory
+ * is handed out by their own pool or by another framework's allocator and is
+ * exhausted by it, and pipelines that forbid allocation after start-up -- and
+ * that want the NED stage of a plan whose own workspace is busy (for example
+ * with nedner_forward on another stream).  The plan itself (tables) is built
+ * beforehand and passed in; inputs and outputs are the caller's, as in
+ * nedner_ned_stage.
+ *
+ *   Limit: (nx/2+1) * 2 ny * Nt * 8 bytes must not exceed
+ *          NEDNER_STATIC_SCRATCH_BYTES (16 MiB), else NEDNER_ENOMEM and
+ *          nothing is launched.
+ *   Memory: every GPU on which the library's device code is loaded holds the
+ *          16 MiB buffer until the process exits.
+ *   Set-up: the first call on a device looks up the buffer's device address
+ *          (cudaGetSymbolAddress, with that device current) and caches it;
+ *          make that first call before any stream capture.
+ *   Sharing: all calls share the one buffer, which keeps the previous call's
+ *          contents (the first kernel overwrites all of it before use, so no
+ *          clearing is needed).  Calls that overlap on the GPU -- on several
+ *          streams or from several host threads -- race and give wrong results.
+ *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ */
+#define NEDNER_STATIC_SCRATCH_BYTES (16u << 20)
+nedner_status nedner_ned_stage_static(nedner_plan_t plan, const float* g, void* Ghat, void* stream);
+
 /* Bytes of device workspace held by the plan. */
 size_t nedner_workspace_bytes(nedner_plan_t plan);
 

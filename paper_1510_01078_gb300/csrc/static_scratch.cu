@@ -1,0 +1,59 @@
+// nedner_ned_stage_static: the NED stage (spread + x-FFT, then y-FFT) with its
+// intermediate array in a fixed device buffer that is part of the library
+// image, instead of the plan's workspace.  The paper has no counterpart; this
+// exists for callers that must not call cudaMalloc when they run the stage.
+//
+// The buffer is a file-scope __device__ array of NEDNER_STATIC_SCRATCH_BYTES.
+// In host code its name only stands for the symbol; the device address is
+// obtained once per device with cudaGetSymbolAddress (with that device
+// current) and cached.  The intermediate [nx/2+1][2 ny][Nt] complex64 array is
+// written in full by the first kernel before the second reads it, so nothing
+// in the buffer has to start at zero.  All calls share the buffer: calls that
+// overlap on the GPU (other streams, other threads) race.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_ned_static_scratch[NEDNER_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the static buffer on the current device (set-up on the
+// first call per device).
+cudaError_t scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_ned_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" nedner_status nedner_ned_stage_static(nedner_plan_t p, const float* g, void* Ghat, void* stream) {
+    if (!p || !Ghat || (p->M > 0 && !g)) return NEDNER_EINVAL;
+    const nedner::Geo& G = p->geo;
+    const size_t need = (size_t)G.nxh * G.Ly * G.Nt * sizeof(float2);
+    if (need > (size_t)NEDNER_STATIC_SCRATCH_BYTES) return NEDNER_ENOMEM;
+    void* scratch = nullptr;
+    if (scratch_address(&scratch) != cudaSuccess) return NEDNER_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    float2* R = (float2*)scratch;
+    if (nedner::launch_ned_spread_xfft(*p, g, R, s) != cudaSuccess) return NEDNER_ECUDA;
+    if (nedner::launch_ned_yfft(*p, R, (float2*)Ghat, s) != cudaSuccess) return NEDNER_ECUDA;
+    return NEDNER_OK;
+}

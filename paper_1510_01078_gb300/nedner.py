@@ -55,6 +55,7 @@ SIGNATURES = {
     "nedner_grad_positions": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nedner_ned_stage": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_forward_profiled": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
+    "nedner_ned_stage_static": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_workspace_bytes": (ctypes.c_size_t, [_P]),
     "nedner_destroy": (ctypes.c_int, [_P]),
     "nedner_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -209,6 +210,24 @@ class Plan:
         return out
 
 
+def ned_stage_static(plan: Plan, g, out=None, stream=None):
+    """``nedner_ned_stage_static``: the NED stage of ``plan`` with its
+    intermediate in the library's fixed 16 MiB device buffer instead of the
+    plan's workspace; for callers that cannot allocate device memory when they
+    run it.  The output ``out`` (complex64, (nx/2+1, ny+1, Nt)) is the caller's
+    and must be passed in if no allocation may happen here.  Calls that overlap
+    on the GPU race (one shared buffer)."""
+    import torch
+    if out is None:
+        out = torch.empty((plan.nx // 2 + 1, plan.ny + 1, plan.Nt), dtype=torch.complex64, device=g.device)
+    st = _load().nedner_ned_stage_static(plan._handle, _dev_ptr(g, torch.float32, (plan.M, plan.Nt), "g"),
+                                         _dev_ptr(out, torch.complex64, (plan.nx // 2 + 1, plan.ny + 1, plan.Nt),
+                                                  "Ghat"),
+                                         _stream_ptr(stream))
+    _check(st, "nedner_ned_stage_static")
+    return out
+
+
 def plan_from_config(cfg, **kw) -> Plan:
     """Plan for a workload dict as produced by ``inputs.make_config``/``small_case``."""
     return Plan(cfg["sensor_xy"], cfg["Nt"], cfg["dt"], cfg["c"],
@@ -216,5 +235,5 @@ def plan_from_config(cfg, **kw) -> Plan:
                 sensor_w=kw.pop("sensor_w", cfg.get("h")), **kw)
 
 
-__all__ = ["Plan", "plan_from_config", "NednerError", "library", "LIB_PATH", "SIGNATURES",
+__all__ = ["Plan", "plan_from_config", "ned_stage_static", "NednerError", "library", "LIB_PATH", "SIGNATURES",
            "WINDOW_KB", "WINDOW_GAUSS"]
