@@ -1,17 +1,19 @@
 // Batched in-shared-memory FFTs used by every stage of the NEDNER path.
 //
-// Each call transforms nb columns of length N (a power of two, 2..8192) that
-// sit in shared memory as buf[p * ld + b] (point p, column b).  The whole
-// thread block cooperates; the call begins and ends with __syncthreads().
-// The algorithm is the self-sorting (Stockham) formulation: log2(N) is
-// covered by radix-4 passes plus at most one radix-2 pass, each pass reading
-// one buffer and writing the other, so no bit-reversal step is needed.
+// Each call transforms nb columns (nb a power of two) of length N (a power of
+// two, 2..8192) that sit in shared memory as buf[p * ld + b] (point p,
+// column b).  The whole thread block cooperates; the call begins and ends
+// with __syncthreads().  The algorithm is the self-sorting (Stockham)
+// formulation: log2(N) is covered by radix-16 passes (4 x 4 decomposition in
+// registers) plus one radix-2, -4 or -8 pass, each pass reading one buffer
+// and writing the other, so no bit-reversal step is needed.
 //
-//   dir = -1 : X[k] = sum_p x[p] exp(-2 pi i k p / N)
-//   dir = +1 : X[k] = sum_p x[p] exp(+2 pi i k p / N)     (unnormalised)
+//   DIR = -1 : X[k] = sum_p x[p] exp(-2 pi i k p / N)
+//   DIR = +1 : X[k] = sum_p x[p] exp(+2 pi i k p / N)     (unnormalised)
 //
-// Twiddles come from a table tw[i] = exp(-2 pi i i / TW_N) computed in FP64
-// on the host (TW_N a power of two >= N).
+// Twiddles come from a table computed in FP64 on the host that holds, for
+// every power of two N <= TW_N, the N values exp(-2 pi i k / N) contiguously
+// at tw[N + k] (so a transform of length N touches N consecutive entries).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,71 +34,172 @@ __device__ __forceinline__ float2 mul_i(float2 a, int dir) {
     return dir < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
 }
 
+// log2 of a power of two
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
 // exp(dir * 2 pi i * q / N) for 0 <= q < N
 __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int q, int N, int dir) {
-    float2 t = __ldg(&tw[q * (TW_N / N)]);
+    float2 t = __ldg(&tw[N + q]);
     return dir < 0 ? t : cconj(t);
 }
 
-// One Stockham pass of radix R over all columns: src -> dst.
+// ---------------------------------------------------------------------------
+// small DFTs in registers
+// ---------------------------------------------------------------------------
+template <int DIR>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    const float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+    const float2 a0 = cadd(v0, v2), a1 = csub(v0, v2);
+    const float2 a2 = cadd(v1, v3), a3 = mul_i(csub(v1, v3), DIR);
+    v0 = cadd(a0, a2);
+    v2 = csub(a0, a2);
+    v1 = cadd(a1, a3);
+    v3 = csub(a1, a3);
+}
+
+// exp(DIR 2 pi i q / 16), q = 0..15, from the exact values of cos/sin at multiples of pi/8
+template <int DIR>
+__device__ __forceinline__ float2 w16(int q) {
+    const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+    float cr, si;
+    switch (q & 15) {
+        case 0: cr = 1.f; si = 0.f; break;
+        case 1: cr = c1; si = s1; break;
+        case 2: cr = h; si = h; break;
+        case 3: cr = s1; si = c1; break;
+        case 4: cr = 0.f; si = 1.f; break;
+        case 5: cr = -s1; si = c1; break;
+        case 6: cr = -h; si = h; break;
+        case 7: cr = -c1; si = s1; break;
+        case 8: cr = -1.f; si = 0.f; break;
+        case 9: cr = -c1; si = -s1; break;
+        case 10: cr = -h; si = -h; break;
+        case 11: cr = -s1; si = -c1; break;
+        case 12: cr = 0.f; si = -1.f; break;
+        case 13: cr = s1; si = -c1; break;
+        case 14: cr = h; si = -h; break;
+        default: cr = c1; si = -s1; break;
+    }
+    return make_float2(cr, DIR * si);
+}
+
+// DFT of R points in registers; X[k] ends up in v[out_index<R>(k)].
+template <int R, int DIR>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+    if constexpr (R == 2) {
+        dft2<DIR>(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        dft4<DIR>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8) {
+        // n = 4 n1 + n2 (n1 < 2, n2 < 4), k = k1 + 2 k2: 4 DFT2 over n1, twiddle W8^(n2 k1), 2 DFT4 over n2
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) dft2<DIR>(v[n2], v[4 + n2]);
+#pragma unroll
+        for (int n2 = 1; n2 < 4; ++n2) v[4 + n2] = cmul(v[4 + n2], w16<DIR>(2 * n2));
+#pragma unroll
+        for (int k1 = 0; k1 < 2; ++k1) dft4<DIR>(v[4 * k1 + 0], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    } else {
+        // R = 16: n = 4 n1 + n2, k = k1 + 4 k2: 4 DFT4 over n1, twiddle W16^(n2 k1), 4 DFT4 over n2
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) dft4<DIR>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+            for (int n2 = 1; n2 < 4; ++n2) v[4 * k1 + n2] = cmul(v[4 * k1 + n2], w16<DIR>(n2 * k1));
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) dft4<DIR>(v[4 * k1 + 0], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    }
+}
+
+// position in v of output X[k] after dft_reg
 template <int R>
+__device__ __forceinline__ constexpr int out_index(int k) {
+    return R == 8 ? 4 * (k & 1) + (k >> 1) : R == 16 ? 4 * (k & 3) + (k >> 2) : k;
+}
+
+// One Stockham pass of radix R over all columns: src -> dst (nb a power of two).
+template <int R, int DIR>
 __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2* __restrict__ dst, int N,
-                                         int Ns, int nb, int ld, int dir, const float2* __restrict__ tw) {
+                                         int Ns, int nb, int ld, const float2* __restrict__ tw) {
     const int stride = N / R;
-    const int items = stride * nb;
+    const int lnb = ilog2(nb);
+    const int items = stride << lnb;
+    const int step = N / (Ns * R);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int j = it / nb;
-        const int b = it - j * nb;
+        const int j = it >> lnb;
+        const int b = it & (nb - 1);
         const int k = j & (Ns - 1);
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[(j + r * stride) * ld + b];
         if (Ns > 1) {
-            const int step = N / (Ns * R);
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, k * r * step, N, dir));
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, k * r * step, N, DIR));
         }
-        if (R == 2) {
-            float2 a = v[0], c = v[1];
-            v[0] = cadd(a, c);
-            v[1] = csub(a, c);
-        } else {
-            float2 a0 = cadd(v[0], v[2]);
-            float2 a1 = csub(v[0], v[2]);
-            float2 a2 = cadd(v[1], v[3]);
-            float2 a3 = mul_i(csub(v[1], v[3]), dir);
-            v[0] = cadd(a0, a2);
-            v[2] = csub(a0, a2);
-            v[1] = cadd(a1, a3);
-            v[3] = csub(a1, a3);
-        }
+        dft_reg<R, DIR>(v);
         const int i0 = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[(i0 + r * Ns) * ld + b] = v[r];
+        for (int r = 0; r < R; ++r) dst[(i0 + r * Ns) * ld + b] = v[out_index<R>(r)];
     }
+}
+
+template <int DIR>
+__device__ __forceinline__ float2* block_fft_dir(float2* a, float2* b, int N, int nb, int ld,
+                                                 const float2* __restrict__ tw) {
+    __syncthreads();
+    float2* src = a;
+    float2* dst = b;
+    int Ns = 1;
+    int rem = ilog2(N);
+    // first pass: radix 2^(rem mod 4); a single-column transform starts with
+    // radix 4 at most, so that neighbouring threads' first-pass stores
+    // (stride R) stay within few banks
+    int first = rem & 3;
+    if (nb == 1 && first == 0 && rem >= 4) first = 2;
+    if (nb == 1 && first == 3) first = 1;
+    if (first) {
+        if (first == 1) fft_pass<2, DIR>(src, dst, N, Ns, nb, ld, tw);
+        else if (first == 2) fft_pass<4, DIR>(src, dst, N, Ns, nb, ld, tw);
+        else fft_pass<8, DIR>(src, dst, N, Ns, nb, ld, tw);
+        Ns <<= first;
+        rem -= first;
+        __syncthreads();
+        float2* t = src; src = dst; dst = t;
+    }
+    while (rem > 0) {
+        if (rem >= 4) {
+            fft_pass<16, DIR>(src, dst, N, Ns, nb, ld, tw);
+            Ns <<= 4;
+            rem -= 4;
+        } else if (rem == 3) {
+            fft_pass<8, DIR>(src, dst, N, Ns, nb, ld, tw);
+            Ns <<= 3;
+            rem -= 3;
+        } else if (rem == 2) {
+            fft_pass<4, DIR>(src, dst, N, Ns, nb, ld, tw);
+            Ns <<= 2;
+            rem -= 2;
+        } else {
+            fft_pass<2, DIR>(src, dst, N, Ns, nb, ld, tw);
+            Ns <<= 1;
+            rem -= 1;
+        }
+        __syncthreads();
+        float2* t = src; src = dst; dst = t;
+    }
+    return src;
 }
 
 // Transform; returns the buffer (a or b) that holds the result.
 __device__ __forceinline__ float2* block_fft(float2* a, float2* b, int N, int nb, int ld, int dir,
                                              const float2* __restrict__ tw) {
-    __syncthreads();
-    float2* src = a;
-    float2* dst = b;
-    int Ns = 1;
-    int logN = 31 - __clz(N);
-    if (logN & 1) {
-        fft_pass<2>(src, dst, N, Ns, nb, ld, dir, tw);
-        Ns = 2;
-        __syncthreads();
-        float2* t = src; src = dst; dst = t;
-    }
-    while (Ns < N) {
-        fft_pass<4>(src, dst, N, Ns, nb, ld, dir, tw);
-        Ns *= 4;
-        __syncthreads();
-        float2* t = src; src = dst; dst = t;
-    }
-    return src;
+    return dir < 0 ? block_fft_dir<-1>(a, b, N, nb, ld, tw) : block_fft_dir<+1>(a, b, N, nb, ld, tw);
 }
 
 }  // namespace nedner

@@ -30,12 +30,28 @@ struct Chunks {
     int c2;   // time samples per CTA in the y-FFT stage
     int c4;   // depth planes per CTA in the y-IFFT stage
     int c5;   // image rows per CTA in the x-c2r stage
+    int groups1;   // lane groups (column segments) per CTA in the spread stage
+    int threads1;  // threads per CTA in the spread stage
+    int ca;        // time samples per CTA in the transposed interpolation stage
+    int smax;      // sensors per task in the transposed interpolation stage
     size_t smem1, smem2, smem3, smem4, smem5;
+    size_t smem_interp, smem_grad, smem3a;
 };
+
+constexpr int kRowBlock = 16;   // grid rows per block of the transposed interpolation
+
+// Monomial coefficients of the NER interpolation taps, passed by value to the
+// NER kernels so that they are read as constant-bank operands.
+struct TapPoly {
+    float c[16 * 13];   // [k][d], k < w <= 16, d <= D <= 12
+};
+
+// Register window of the spreading sweep: the window width w rounded up to 4, 8, 12 or 16.
+inline int spread_taps(int w) { return w <= 4 ? 4 : w <= 8 ? 8 : w <= 12 ? 12 : 16; }
 
 // Device-side tables owned by a plan.
 struct DevTables {
-    float2* tw = nullptr;         // [TW_N] exp(-2 pi i k / TW_N)
+    float2* tw = nullptr;         // [2 TW_N] exp(-2 pi i k / N) at [N + k], N = 1, 2, 4, .., TW_N
     float* deconv_x = nullptr;    // [nx/2+1]   1/phihat(jx / Lx)
     float* deconv_y = nullptr;    // [ny+1]     1/phihat(jy / Ly), jy = -ny/2..ny/2
     float* deconv_t = nullptr;    // [Nt]       1/phihat((n - Nt/2) / Lt)
@@ -51,6 +67,20 @@ struct DevTables {
     int* row_ptr = nullptr;       // [Ly+1] CSR of (sensor, y tap) entries by grid row
     int* row_m = nullptr;         // [M w] sensor of each entry
     float* row_w = nullptr;       // [M w] y tap times sensor factor
+    float* row_dw = nullptr;      // [M w] y-tap derivative (per metre) times sensor factor
+    int* row_local = nullptr;     // [M w] index of the entry's sensor in its row block's band
+    // spreading: per row, entries sorted by first x column, wrapped ones repeated at bx - Lx
+    int* xrow_ptr = nullptr;      // [Ly+1]
+    int* xent_m = nullptr;        // [E'] sensor
+    float* xent_wx = nullptr;     // [E'][spread_taps(w)] x taps times y tap times sensor factor (zero padded)
+    int* xent_bx = nullptr;       // [E'] first x column, in (-w, Lx)
+    int4* seg = nullptr;          // [Ly][groups1] column range [x, y) and entry range [z, w)
+    // transposed interpolation: sensors touching each block of kRowBlock rows
+    int* band_m = nullptr;        // [B] sensor
+    int* band_slot = nullptr;     // [B] 0 = block of the sensor's first row, 1 = the next block
+    int4* tasks = nullptr;        // [ntasks] (block, band begin, band end, first band index of block)
+    unsigned char* two_blocks = nullptr;  // [M] 1 if the sensor's rows span two blocks
+    int ntasks = 0;
 };
 
 }  // namespace nedner
@@ -65,6 +95,7 @@ struct nedner_plan_s {
     nedner_grid grid{};
     std::vector<double> xy, h;
     nedner::DevTables t;
+    nedner::TapPoly tap{};
     void* ws = nullptr;           // device workspace
     size_t ws_bytes = 0;
     size_t region_a = 0;          // bytes of region A (R / V), region B follows (Ghat / Y)
@@ -80,5 +111,16 @@ cudaError_t launch_ner_lines(const nedner_plan_s& p, const float2* Ghat, float2*
 cudaError_t launch_img_yifft(const nedner_plan_s& p, const float2* V, float2* Y, cudaStream_t s);
 cudaError_t launch_img_xc2r(const nedner_plan_s& p, const float2* Y, float* p0, cudaStream_t s);
 cudaError_t configure_fwd_kernels(const nedner_plan_s& p);
+
+// transposed-stage launchers (kernels_adj.cu)
+cudaError_t launch_img_xr2c_adj(const nedner_plan_s& p, const float* p0, float2* Y, cudaStream_t s);
+cudaError_t launch_img_yfft_adj(const nedner_plan_s& p, const float2* Y, float2* V, cudaStream_t s);
+cudaError_t launch_ner_lines_adj(const nedner_plan_s& p, const float2* V, float2* Ghat, cudaStream_t s);
+cudaError_t launch_ned_yfft_adj(const nedner_plan_s& p, const float2* Ghat, float2* R, cudaStream_t s);
+cudaError_t launch_ned_interp_adj(const nedner_plan_s& p, const float2* R, float* P, cudaStream_t s);
+cudaError_t launch_adj_finish(const nedner_plan_s& p, const float* P, float* g, cudaStream_t s);
+cudaError_t launch_ned_grad(const nedner_plan_s& p, const float2* R, const float* g, float2* Q, cudaStream_t s);
+cudaError_t launch_grad_finish(const nedner_plan_s& p, const float2* Q, float* dxy, cudaStream_t s);
+cudaError_t configure_adj_kernels(const nedner_plan_s& p);
 
 }  // namespace nedner

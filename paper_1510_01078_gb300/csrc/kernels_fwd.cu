@@ -16,17 +16,61 @@ namespace nedner {
 
 // ---------------------------------------------------------------------------
 // Stage (a), part 1: NED spreading (Eq. NED_NUFFT) fused with the x-FFT.
-// One CTA owns grid row gy and C consecutive time samples.  It spreads every
-// (sensor, y tap) entry of that row into a shared-memory row [Lx][C] (window
-// taps w along x), then transforms the row along x (two real columns packed
-// into one complex FFT) and keeps jx = 0..nx/2, divided by phihat(jx/Lx).
+// One CTA owns grid row gy and C consecutive time samples.  Its threads form
+// lane groups of C (lane = time sample); group q owns the column segment
+// seg[gy][q] = [c0, c1) of the shared-memory row [Lx][C].  The row's entries
+// (sensor, y tap) are sorted by their first x column bx; the group sweeps the
+// ones whose taps reach into its segment, keeping 2 WT columns
+// [base, base + 2 WT) in registers.  An entry at bx >= base + WT first moves
+// the window up by WT columns (the lower WT are final: stored once if inside
+// the segment), then its taps (already multiplied by the y tap and the sensor
+// factor) are added at offset bx - base in [0, WT), chosen by a switch that
+// is uniform across the group.  No atomics and no shared-memory
+// read-modify-write; every column of the row is written exactly once.
+// Entries are taken sixteen at a time: their indices, taps and samples of g
+// are loaded together (independent loads in flight) and staged in shared
+// memory, then swept.
+// The row is then transformed along x (two real columns packed into one
+// complex FFT) and jx = 0..nx/2 is kept, divided by phihat(jx/Lx).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ned_spread_xfft(Geo G, int C, const float* __restrict__ g,
-                                                         const int* __restrict__ row_ptr,
-                                                         const int* __restrict__ row_m,
-                                                         const float* __restrict__ row_w,
-                                                         const int* __restrict__ sens_bx,
-                                                         const float* __restrict__ sens_wx,
+template <int WT>
+__device__ __forceinline__ void flush_lower(float (&acc)[2 * WT], float* S, int C, int ln, int base, int c0, int c1) {
+#pragma unroll
+    for (int k = 0; k < WT; ++k) {
+        const int col = base + k;
+        if (col >= c0 && col < c1) S[col * C + ln] = acc[k];
+        acc[k] = acc[k + WT];
+        acc[k + WT] = 0.f;
+    }
+}
+
+template <int WT, int D>
+__device__ __forceinline__ void add_taps(float (&acc)[2 * WT], const float (&wv)[WT], float gval) {
+#pragma unroll
+    for (int k = 0; k < WT; ++k) acc[D + k] = fmaf(wv[k], gval, acc[D + k]);
+}
+
+template <int WT>
+__device__ __forceinline__ void add_at(float (&acc)[2 * WT], const float (&wv)[WT], float gval, int d) {
+    switch (d) {
+#define NEDNER_CASE(D) \
+    case D:            \
+        if (D < WT) add_taps<WT, (D < WT ? D : 0)>(acc, wv, gval); \
+        break;
+        NEDNER_CASE(0) NEDNER_CASE(1) NEDNER_CASE(2) NEDNER_CASE(3) NEDNER_CASE(4) NEDNER_CASE(5)
+        NEDNER_CASE(6) NEDNER_CASE(7) NEDNER_CASE(8) NEDNER_CASE(9) NEDNER_CASE(10) NEDNER_CASE(11)
+        NEDNER_CASE(12) NEDNER_CASE(13) NEDNER_CASE(14) NEDNER_CASE(15)
+#undef NEDNER_CASE
+        default: break;
+    }
+}
+
+template <int WT>
+__global__ void __launch_bounds__(512) k_ned_spread_xfft(Geo G, int C, const float* __restrict__ g,
+                                                         const int4* __restrict__ seg,
+                                                         const int* __restrict__ xent_m,
+                                                         const float* __restrict__ xent_wx,
+                                                         const int* __restrict__ xent_bx,
                                                          const float* __restrict__ deconv_x,
                                                          const float2* __restrict__ tw, float2* __restrict__ R) {
     extern __shared__ float4 smem4[];
@@ -35,25 +79,83 @@ __global__ void __launch_bounds__(256) k_ned_spread_xfft(Geo G, int C, const flo
     const int gy = blockIdx.x;
     const int n0 = blockIdx.y * C;
     const int Lx = G.Lx;
+    const int lc = ilog2(C);
+    const int groups = blockDim.x >> lc;
+    const int q = threadIdx.x >> lc;
+    const int ln = threadIdx.x & (C - 1);
 
-    for (int i = threadIdx.x; i < Lx * C; i += blockDim.x) S[i] = 0.f;
-    __syncthreads();
+    const int4 sg = seg[(size_t)gy * groups + q];      // c0, c1, first entry, end entry
+    float acc[2 * WT];
+#pragma unroll
+    for (int k = 0; k < 2 * WT; ++k) acc[k] = 0.f;
+    int base = sg.x - WT;
 
+    // per-group staging area for one batch, carved out of the FFT scratch
+    // (unused until the sweep is over): bx[B], taps[B][WT], g[B][C]
+    constexpr int B = 16;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int per_warp = 32 / C;                 // entries handled side by side in a warp
-    const int sub = lane / C;
-    const int ln = lane - sub * C;
-    const int groups = (blockDim.x >> 5) * per_warp;
-    const int e_end = row_ptr[gy + 1];
-    if (sub < per_warp) {
-        for (int e = row_ptr[gy] + warp * per_warp + sub; e < e_end; e += groups) {
-            const int m = row_m[e];
-            const float val = row_w[e] * __ldg(&g[(size_t)m * G.Nt + n0 + ln]);
-            const int bx = sens_bx[m];
-            const float* wx = sens_wx + (size_t)m * G.w;
-            for (int k = 0; k < G.w; ++k) atomicAdd(&S[((bx + k) & (Lx - 1)) * C + ln], __ldg(&wx[k]) * val);
+    const int gbase = lane - ln;
+    const unsigned gmask = (C == 32) ? 0xffffffffu : (((1u << C) - 1u) << gbase);
+    int* st_bx = reinterpret_cast<int*>(B2) + (size_t)q * (B + B * WT + B * C);
+    float* st_w = reinterpret_cast<float*>(st_bx + B);
+    float* st_g = st_w + B * WT;
+
+    for (int e0 = sg.z; e0 < sg.w; e0 += B) {
+        const int nbat = min(B, sg.w - e0);
+        // indices of the batch, one entry per lane (lanes >= nbat idle)
+        const int m_l = (ln < nbat) ? __ldg(&xent_m[e0 + ln]) : 0;    // entries 0..C-1 of the batch
+        for (int j = ln; j < nbat; j += C) st_bx[j] = __ldg(&xent_bx[e0 + j]);
+        // taps of the batch (contiguous, zero padded to WT)
+        const float* wsrc = xent_wx + (size_t)e0 * WT;
+        for (int i = ln; i < nbat * WT; i += C) st_w[i] = __ldg(&wsrc[i]);
+        // samples of g of the batch: B independent loads per lane
+        float gl[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int src_lane = gbase + (j & (C - 1));
+            const int mj = __shfl_sync(gmask, m_l, src_lane);
+            gl[j] = (j < nbat && j < C) ? __ldg(&g[(size_t)mj * G.Nt + n0 + ln]) : 0.f;
         }
+        if (C < B) {
+            // batches larger than the group: indices of entries C.. come from a second round
+            for (int j0 = C; j0 < nbat; j0 += C) {
+                int m2 = (ln + j0 < nbat) ? __ldg(&xent_m[e0 + j0 + ln]) : 0;
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    if (j >= j0 && j < j0 + C) {
+                        const int mj = __shfl_sync(gmask, m2, gbase + (j - j0));
+                        if (j < nbat) gl[j] = __ldg(&g[(size_t)mj * G.Nt + n0 + ln]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) st_g[j * C + ln] = gl[j];
+        __syncwarp(gmask);
+        for (int j = 0; j < nbat; ++j) {
+            const int bx = st_bx[j];
+            const float gval = st_g[j * C + ln];
+            while (bx >= base + WT) {
+                flush_lower<WT>(acc, S, C, ln, base, sg.x, sg.y);
+                base += WT;
+            }
+            float wv[WT];
+            const float4* wp = reinterpret_cast<const float4*>(st_w + j * WT);
+#pragma unroll
+            for (int k4 = 0; k4 < WT / 4; ++k4) {
+                const float4 t = wp[k4];
+                wv[4 * k4 + 0] = t.x;
+                wv[4 * k4 + 1] = t.y;
+                wv[4 * k4 + 2] = t.z;
+                wv[4 * k4 + 3] = t.w;
+            }
+            add_at<WT>(acc, wv, gval, bx - base);
+        }
+        __syncwarp(gmask);
+    }
+    while (base < sg.y) {
+        flush_lower<WT>(acc, S, C, ln, base, sg.x, sg.y);
+        base += WT;
     }
 
     const int nb = C / 2;
@@ -61,8 +163,8 @@ __global__ void __launch_bounds__(256) k_ned_spread_xfft(Geo G, int C, const flo
 
     const int items = G.nxh * C;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int jx = it / C;
-        const int c = it - jx * C;
+        const int jx = it >> lc;
+        const int c = it & (C - 1);
         const int b = c >> 1;
         const float2 zk = res[jx * nb + b];
         const float2 zm = cconj(res[((Lx - jx) & (Lx - 1)) * nb + b]);
@@ -85,16 +187,18 @@ __global__ void __launch_bounds__(256) k_ned_yfft(Geo G, int C, const float2* __
     float2* B = A + (size_t)G.Ly * C;
     const int jx = blockIdx.x;
     const int n0 = blockIdx.y * C;
+    const int lc = ilog2(C);
+#pragma unroll 8
     for (int it = threadIdx.x; it < G.Ly * C; it += blockDim.x) {
-        const int gy = it / C;
-        const int c = it - gy * C;
+        const int gy = it >> lc;
+        const int c = it & (C - 1);
         A[it] = R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c];
     }
     float2* res = block_fft(A, B, G.Ly, C, C, -1, tw);
     const int items = G.nyp * C;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int b = it / C;                  // jy = b - ny/2
-        const int c = it - b * C;
+        const int b = it >> lc;                // jy = b - ny/2
+        const int c = it & (C - 1);
         const int q = (b - G.ny / 2 + G.Ly) & (G.Ly - 1);
         Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c] = cscale(res[q * C + c], __ldg(&deconv_y[b]));
     }
@@ -149,16 +253,27 @@ __device__ __forceinline__ FF nu_abs(const Geo& G, float2 axy, int l) {
     return quick_two_sum(r, resid * (0.5f / r));
 }
 
-__device__ __forceinline__ float tap_poly(const float* __restrict__ cf, int D, float s) {
-    float p = cf[D];
-    for (int d = D - 1; d >= 0; --d) p = fmaf(p, s, cf[d]);
-    return p;
+// sum_k P_k(s) B[(mu0 + k) mod Lt] with the tap polynomials unrolled (Horner)
+template <int W, int D>
+__device__ __forceinline__ float2 ner_gather(const TapPoly& P, const float2* Bf, int mu0, float s, int Lt) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        float p = P.c[k * (D + 1) + D];
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) p = fmaf(p, s, P.c[k * (D + 1) + d]);
+        const float2 b = Bf[(mu0 + k) & (Lt - 1)];
+        acc.x = fmaf(p, b.x, acc.x);
+        acc.y = fmaf(p, b.y, acc.y);
+    }
+    return acc;
 }
 
-__global__ void __launch_bounds__(256) k_ner_lines(Geo G, const float2* __restrict__ Ghat,
+template <int W, int D>
+__global__ void __launch_bounds__(256) k_ner_lines(Geo G, const __grid_constant__ TapPoly P,
+                                                   const float2* __restrict__ Ghat,
                                                    const float2* __restrict__ axy_tab,
                                                    const float* __restrict__ deconv_t,
-                                                   const float* __restrict__ tapcoef,
                                                    const float2* __restrict__ tw, float2* __restrict__ V) {
     extern __shared__ float4 smem4[];
     float2* LA = reinterpret_cast<float2*>(smem4);   // [Lt]
@@ -166,19 +281,16 @@ __global__ void __launch_bounds__(256) k_ner_lines(Geo G, const float2* __restri
     float2* T = LB + G.Lt;                           // [nz + 1] values at l = -nz/2..nz/2
     float2* UA = T + (G.nz + 1);                     // [nz]
     float2* UB = UA + G.nz;                          // [nz]
-    float* cf = reinterpret_cast<float*>(UB + G.nz); // [w][D+1]
 
     const int grp = blockIdx.x;
-    const int kx = grp / G.ny;
-    const int ky = grp - kx * G.ny - G.ny / 2;       // -ny/2..ny/2-1
+    const int kx = grp >> ilog2(G.ny);
+    const int ky = (grp & (G.ny - 1)) - G.ny / 2;    // -ny/2..ny/2-1
     const int kyb = (ky == -G.ny / 2) ? G.ny / 2 : ky;
     const bool nyq_x = (kx == G.nx / 2);
     const float ca = nyq_x ? 0.f : 0.5f;
     const float cb = nyq_x ? 1.f : 0.5f;
     const int half_nz = G.nz / 2;
-    const int ncf = G.w * (G.D + 1);
 
-    for (int i = threadIdx.x; i < ncf; i += blockDim.x) cf[i] = tapcoef[i];
     for (int i = threadIdx.x; i < G.nz; i += blockDim.x) UA[i] = make_float2(0.f, 0.f);
 
     // lines to evaluate: a = (kx, ky) unless its coefficient is zero, b = (kx, kyb)
@@ -195,6 +307,7 @@ __global__ void __launch_bounds__(256) k_ner_lines(Geo G, const float2* __restri
         for (int p = threadIdx.x; p < G.Lt; p += blockDim.x) LA[p] = make_float2(0.f, 0.f);
         __syncthreads();
         const float2* src = Ghat + line * G.Nt;
+#pragma unroll 4
         for (int n = threadIdx.x; n < G.Nt; n += blockDim.x)
             LA[(n - G.Nt / 2) & (G.Lt - 1)] = cscale(src[n], __ldg(&deconv_t[n]));
         float2* Bf = block_fft(LA, LB, G.Lt, 1, 1, -1, tw);
@@ -204,15 +317,15 @@ __global__ void __launch_bounds__(256) k_ner_lines(Geo G, const float2* __restri
             const int l = e - half_nz;
             float2 val = make_float2(0.f, 0.f);
             FF nu = nu_abs(G, axy, l);
-            float W;
+            float Wj;
             if (l == 0) {
-                W = (kx == 0 && lky == 0) ? 2.f : 0.f;
+                Wj = (kx == 0 && lky == 0) ? 2.f : 0.f;
                 nu = {0.f, 0.f};
             } else {
-                W = 2.f * G.sqrt_az * (float)abs(l) / nu.hi;
+                Wj = 2.f * G.sqrt_az * (float)abs(l) / nu.hi;
                 if (l < 0) nu = {-nu.hi, -nu.lo};
             }
-            float cl = G.apply_weights ? W * G.scale : G.scale;
+            float cl = G.apply_weights ? Wj * G.scale : G.scale;
             if (G.band_mask) {
                 const double nd = (double)nu.hi + (double)nu.lo;
                 if (!(nd >= -0.5 * G.Nt - 1e-9 && nd < 0.5 * G.Nt - 1e-9)) cl = 0.f;
@@ -225,15 +338,8 @@ __global__ void __launch_bounds__(256) k_ner_lines(Geo G, const float2* __restri
                 if (t < 0.f) { t += 1.f; fl -= 1.f; }
                 if (t >= 1.f) { t -= 1.f; fl += 1.f; }
                 const int ifl = (int)fl;
-                const int mu0 = ifl - G.w / 2 + 1;
-                const float s = 2.f * t - 1.f;
-                float2 acc = make_float2(0.f, 0.f);
-                for (int k = 0; k < G.w; ++k) {
-                    const float wk = tap_poly(cf + k * (G.D + 1), G.D, s);
-                    const float2 b = Bf[(mu0 + k) & (G.Lt - 1)];
-                    acc.x = fmaf(wk, b.x, acc.x);
-                    acc.y = fmaf(wk, b.y, acc.y);
-                }
+                const int mu0 = ifl - W / 2 + 1;
+                const float2 acc = ner_gather<W, D>(P, Bf, mu0, 2.f * t - 1.f, G.Lt);
                 // exp(-i pi nu) = exp(-i pi v/2) = (-i)^floor(v) exp(-i pi t / 2)
                 float sn, cs;
                 sincospif(0.5f * t, &sn, &cs);
@@ -278,15 +384,17 @@ __global__ void __launch_bounds__(256) k_img_yifft(Geo G, int C, const float2* _
     float2* B = A + (size_t)G.ny * ld;
     const int kx = blockIdx.x;
     const int z0 = blockIdx.y * C;
+    const int lc = ilog2(C), lny = ilog2(G.ny);
+#pragma unroll 8
     for (int it = threadIdx.x; it < G.ny * C; it += blockDim.x) {
-        const int ky = it / C;
-        const int c = it - ky * C;
+        const int ky = it >> lc;
+        const int c = it & (C - 1);
         A[ky * ld + c] = V[((size_t)kx * G.ny + ky) * G.nz + z0 + c];
     }
     float2* res = block_fft(A, B, G.ny, C, ld, +1, tw);
     for (int it = threadIdx.x; it < G.ny * C; it += blockDim.x) {
-        const int c = it / G.ny;
-        const int qy = it - c * G.ny;
+        const int c = it >> lny;
+        const int qy = it & (G.ny - 1);
         Y[((size_t)kx * G.nz + z0 + c) * G.ny + qy] = res[qy * ld + c];
     }
 }
@@ -309,15 +417,17 @@ __global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, const float2* __
     float2* B = A + (size_t)H * ld;                 // [H][ld]
     const int qz = blockIdx.x;
     const int y0 = blockIdx.y * C;
+    const int lc = ilog2(C), lh = ilog2(H);
+#pragma unroll 8
     for (int it = threadIdx.x; it < (H + 1) * C; it += blockDim.x) {
-        const int kx = it / C;
-        const int c = it - kx * C;
+        const int kx = it >> lc;
+        const int c = it & (C - 1);
         X[kx * ld + c] = Y[((size_t)kx * G.nz + qz) * G.ny + y0 + c];
     }
     __syncthreads();
     for (int it = threadIdx.x; it < H * C; it += blockDim.x) {
-        const int k = it / C;
-        const int c = it - k * C;
+        const int k = it >> lc;
+        const int c = it & (C - 1);
         float2 xk = X[k * ld + c];
         float2 xm = X[(H - k) * ld + c];
         if (k == 0) {
@@ -331,8 +441,8 @@ __global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, const float2* __
     }
     float2* res = block_fft(A, B, H, C, ld, +1, tw);
     for (int it = threadIdx.x; it < H * C; it += blockDim.x) {
-        const int c = it / H;
-        const int pp = it - c * H;
+        const int c = it >> lh;
+        const int pp = it & (H - 1);
         const float2 z = res[pp * ld + c];
         reinterpret_cast<float2*>(p0 + ((size_t)qz * G.ny + y0 + c) * G.nx)[pp] = z;
     }
@@ -343,9 +453,17 @@ __global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, const float2* __
 // ---------------------------------------------------------------------------
 cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem1))) return e;
+    const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<4>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<8>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<12>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<16>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
     if ((e = cudaFuncSetAttribute(k_ned_yfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2))) return e;
-    if ((e = cudaFuncSetAttribute(k_ner_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem3))) return e;
+#define NEDNER_ATTR_NER(W, D) \
+    if ((e = cudaFuncSetAttribute(k_ner_lines<W, D>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e;
+    NEDNER_ATTR_NER(4, 10) NEDNER_ATTR_NER(6, 10) NEDNER_ATTR_NER(8, 10) NEDNER_ATTR_NER(10, 10)
+    NEDNER_ATTR_NER(12, 10) NEDNER_ATTR_NER(14, 12) NEDNER_ATTR_NER(16, 12)
+#undef NEDNER_ATTR_NER
     if ((e = cudaFuncSetAttribute(k_img_yifft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem4))) return e;
     if ((e = cudaFuncSetAttribute(k_img_xc2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem5))) return e;
     return cudaSuccess;
@@ -354,8 +472,16 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
 cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float2* R, cudaStream_t s) {
     const Geo& G = p.geo;
     dim3 grid(G.Ly, G.Nt / p.ch.c1);
-    k_ned_spread_xfft<<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.row_ptr, p.t.row_m, p.t.row_w,
-                                                    p.t.sens_bx, p.t.sens_wx, p.t.deconv_x, p.t.tw, R);
+#define NEDNER_SPREAD(WT)                                                                                 \
+    k_ned_spread_xfft<WT><<<grid, p.ch.threads1, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m,       \
+                                                                 p.t.xent_wx, p.t.xent_bx, p.t.deconv_x, p.t.tw, R)
+    switch (spread_taps(G.w)) {
+        case 4: NEDNER_SPREAD(4); break;
+        case 8: NEDNER_SPREAD(8); break;
+        case 12: NEDNER_SPREAD(12); break;
+        default: NEDNER_SPREAD(16); break;
+    }
+#undef NEDNER_SPREAD
     return cudaGetLastError();
 }
 
@@ -369,7 +495,17 @@ cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Gha
 cudaError_t launch_ner_lines(const nedner_plan_s& p, const float2* Ghat, float2* V, cudaStream_t s) {
     const Geo& G = p.geo;
     dim3 grid(G.nxh * G.ny);
-    k_ner_lines<<<grid, 256, p.ch.smem3, s>>>(G, Ghat, p.t.axy, p.t.deconv_t, p.t.tapcoef, p.t.tw, V);
+#define NEDNER_NER(W, D) k_ner_lines<W, D><<<grid, 256, p.ch.smem3, s>>>(G, p.tap, Ghat, p.t.axy, p.t.deconv_t, p.t.tw, V)
+    switch (G.w) {
+        case 4: NEDNER_NER(4, 10); break;
+        case 6: NEDNER_NER(6, 10); break;
+        case 8: NEDNER_NER(8, 10); break;
+        case 10: NEDNER_NER(10, 10); break;
+        case 12: NEDNER_NER(12, 10); break;
+        case 14: NEDNER_NER(14, 12); break;
+        default: NEDNER_NER(16, 12); break;
+    }
+#undef NEDNER_NER
     return cudaGetLastError();
 }
 

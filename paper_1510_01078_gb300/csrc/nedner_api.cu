@@ -40,11 +40,20 @@ cudaError_t upload(T** dptr, const std::vector<T>& h, cudaStream_t s) {
 void free_sensor_tables(DevTables& t) {
     cudaFree(t.sens_bx); cudaFree(t.sens_by); cudaFree(t.sens_wx); cudaFree(t.sens_wy);
     cudaFree(t.sens_dwx); cudaFree(t.sens_dwy); cudaFree(t.sens_fac);
-    cudaFree(t.row_ptr); cudaFree(t.row_m); cudaFree(t.row_w);
+    cudaFree(t.row_ptr); cudaFree(t.row_m); cudaFree(t.row_w); cudaFree(t.row_dw); cudaFree(t.row_local);
+    cudaFree(t.xrow_ptr); cudaFree(t.xent_m); cudaFree(t.xent_wx); cudaFree(t.xent_bx); cudaFree(t.seg);
+    cudaFree(t.band_m); cudaFree(t.band_slot); cudaFree(t.tasks); cudaFree(t.two_blocks);
     t.sens_bx = t.sens_by = nullptr;
     t.sens_wx = t.sens_wy = t.sens_dwx = t.sens_dwy = t.sens_fac = nullptr;
-    t.row_ptr = t.row_m = nullptr;
-    t.row_w = nullptr;
+    t.row_ptr = t.row_m = t.row_local = nullptr;
+    t.row_w = t.row_dw = nullptr;
+    t.xrow_ptr = t.xent_m = t.xent_bx = nullptr;
+    t.xent_wx = nullptr;
+    t.seg = nullptr;
+    t.band_m = t.band_slot = nullptr;
+    t.tasks = nullptr;
+    t.two_blocks = nullptr;
+    t.ntasks = 0;
 }
 
 void free_tables(DevTables& t) {
@@ -66,8 +75,18 @@ nedner_status check_positions(const nedner_plan_s& p, const double* xy) {
 
 // Per-sensor taps and the row lists (Sec. 3.2: mu_{m,k} are the w grid
 // points nearest u_m = x_m Lx / X, the weights phi(u_m - mu)).
+//
+// Three views of the (sensor, y tap) entries are built:
+//  - row CSR: the entries of each grid row (transposed interpolation);
+//  - per row, the entries sorted by their first x column, entries that wrap
+//    around x = Lx repeated at bx - Lx, and each row cut into groups1 column
+//    segments of about equal entry count (spreading: every lane group of a CTA
+//    owns one segment and writes it without atomics);
+//  - per block of kRowBlock rows, the sensors touching it (at most two blocks
+//    per sensor since w <= kRowBlock), split into tasks of at most smax sensors.
 nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     const Geo& G = p.geo;
+    const Chunks& C = p.ch;
     const int64_t M = p.M;
     const int w = G.w;
     const double X = p.grid.nx * p.grid.dx, Y = p.grid.ny * p.grid.dy;
@@ -88,22 +107,120 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
         }
         fac[m] = (float)(G.apply_weights ? p.h[m] / (p.grid.dx * p.grid.dy) : 1.0);
     }
-    // CSR by grid row: entry (m, ky) lands in row (by_m + ky) mod Ly
+    // row CSR: entry (m, k) lands in row (by_m + k) mod Ly
     std::vector<int> row_ptr(G.Ly + 1, 0);
     for (int64_t m = 0; m < M; ++m)
         for (int k = 0; k < w; ++k) row_ptr[((by[m] + k) & (G.Ly - 1)) + 1]++;
     for (int r = 0; r < G.Ly; ++r) row_ptr[r + 1] += row_ptr[r];
     std::vector<int> fill(row_ptr.begin(), row_ptr.end() - 1);
-    std::vector<int> row_m((size_t)M * w);
-    std::vector<float> row_w((size_t)M * w);
+    const size_t E = (size_t)M * w;
+    std::vector<int> row_m(E);
+    std::vector<float> row_w(E), row_dw(E);
     for (int64_t m = 0; m < M; ++m)
         for (int k = 0; k < w; ++k) {
             int r = (by[m] + k) & (G.Ly - 1);
             int e = fill[r]++;
             row_m[e] = (int)m;
             row_w[e] = wy[m * w + k] * fac[m];
+            row_dw[e] = dwy[m * w + k] * fac[m];
         }
+
+    // spreading view: sorted by first x column, wrapped entries repeated
+    struct XE { int bx, m; float w; };
+    std::vector<int> xrow_ptr(G.Ly + 1, 0);
+    std::vector<int> xent_m, xent_bx;
+    std::vector<float> xent_wx;
+    std::vector<int4> seg((size_t)G.Ly * C.groups1);
+    std::vector<XE> tmp;
+    for (int r = 0; r < G.Ly; ++r) {
+        tmp.clear();
+        for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+            int m = row_m[e];
+            tmp.push_back({bx[m], m, row_w[e]});
+            if (bx[m] > G.Lx - w) tmp.push_back({bx[m] - G.Lx, m, row_w[e]});
+        }
+        std::stable_sort(tmp.begin(), tmp.end(), [](const XE& a, const XE& b) { return a.bx < b.bx; });
+        const int base = (int)xent_m.size();
+        for (const XE& x : tmp) {
+            xent_m.push_back(x.m);
+            xent_bx.push_back(x.bx);
+            for (int k = 0; k < spread_taps(w); ++k) xent_wx.push_back(k < w ? x.w * wx[(size_t)x.m * w + k] : 0.f);
+        }
+        xrow_ptr[r + 1] = (int)xent_m.size();
+        const int Er = (int)tmp.size();
+        // cut the columns so that each lane group's sweep costs about the same:
+        // an entry costs about as much as 1.5 columns of window sliding
+        std::vector<int> cut(C.groups1 + 1);
+        cut[0] = 0;
+        cut[C.groups1] = G.Lx;
+        {
+            std::vector<double> cum(G.Lx + 1, 0.0);     // cost of columns < c
+            size_t i = 0;
+            for (int c = 0; c < G.Lx; ++c) {
+                double add = 1.0;
+                while (i < tmp.size() && tmp[i].bx <= c) { add += 1.5; ++i; }
+                cum[c + 1] = cum[c] + add;
+            }
+            int c = 0;
+            for (int q = 1; q < C.groups1; ++q) {
+                const double target = cum[G.Lx] * q / C.groups1;
+                while (c < G.Lx && cum[c] < target) ++c;
+                cut[q] = std::max(cut[q - 1], c);
+            }
+        }
+        for (int q = 0; q < C.groups1; ++q) {
+            const int c0 = cut[q], c1 = cut[q + 1];
+            int lo = 0, hi = 0;
+            while (lo < Er && tmp[lo].bx < c0 - w + 1) ++lo;
+            hi = lo;
+            while (hi < Er && tmp[hi].bx < c1) ++hi;
+            seg[(size_t)r * C.groups1 + q] = make_int4(c0, c1, base + lo, base + hi);
+        }
+    }
+
+    // transposed-interpolation view: row blocks, bands and tasks
+    const int nblk = G.Ly / kRowBlock;
+    std::vector<int> b0(M), b1(M);
+    std::vector<unsigned char> two(M);
+    for (int64_t m = 0; m < M; ++m) {
+        b0[m] = by[m] / kRowBlock;
+        b1[m] = ((by[m] + w - 1) & (G.Ly - 1)) / kRowBlock;
+        two[m] = (unsigned char)(b1[m] != b0[m]);
+    }
+    std::vector<int> band_ptr(nblk + 1, 0);
+    for (int64_t m = 0; m < M; ++m) {
+        band_ptr[b0[m] + 1]++;
+        if (two[m]) band_ptr[b1[m] + 1]++;
+    }
+    for (int b = 0; b < nblk; ++b) band_ptr[b + 1] += band_ptr[b];
+    std::vector<int> bfill(band_ptr.begin(), band_ptr.end() - 1);
+    std::vector<int> band_m(band_ptr[nblk]), band_slot(band_ptr[nblk]);
+    std::vector<int> pos0(M, -1), pos1(M, -1);
+    for (int64_t m = 0; m < M; ++m) {
+        int i = bfill[b0[m]]++;
+        band_m[i] = (int)m;
+        band_slot[i] = 0;
+        pos0[m] = i - band_ptr[b0[m]];
+        if (two[m]) {
+            int j = bfill[b1[m]]++;
+            band_m[j] = (int)m;
+            band_slot[j] = 1;
+            pos1[m] = j - band_ptr[b1[m]];
+        }
+    }
+    std::vector<int> row_local(E);
+    for (int r = 0; r < G.Ly; ++r)
+        for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+            int m = row_m[e];
+            row_local[e] = (r / kRowBlock == b0[m]) ? pos0[m] : pos1[m];
+        }
+    std::vector<int4> tasks;
+    for (int b = 0; b < nblk; ++b)
+        for (int s0 = band_ptr[b]; s0 < band_ptr[b + 1]; s0 += C.smax)
+            tasks.push_back(make_int4(b, s0, std::min(band_ptr[b + 1], s0 + C.smax), band_ptr[b]));
+
     free_sensor_tables(p.t);
+    p.t.ntasks = (int)tasks.size();
     cudaError_t e = cudaSuccess;
     if (!e) e = upload(&p.t.sens_bx, bx, s);
     if (!e) e = upload(&p.t.sens_by, by, s);
@@ -115,6 +232,17 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = upload(&p.t.row_ptr, row_ptr, s);
     if (!e) e = upload(&p.t.row_m, row_m, s);
     if (!e) e = upload(&p.t.row_w, row_w, s);
+    if (!e) e = upload(&p.t.row_dw, row_dw, s);
+    if (!e) e = upload(&p.t.row_local, row_local, s);
+    if (!e) e = upload(&p.t.xrow_ptr, xrow_ptr, s);
+    if (!e) e = upload(&p.t.xent_m, xent_m, s);
+    if (!e) e = upload(&p.t.xent_wx, xent_wx, s);
+    if (!e) e = upload(&p.t.xent_bx, xent_bx, s);
+    if (!e) e = upload(&p.t.seg, seg, s);
+    if (!e) e = upload(&p.t.band_m, band_m, s);
+    if (!e) e = upload(&p.t.band_slot, band_slot, s);
+    if (!e) e = upload(&p.t.tasks, tasks, s);
+    if (!e) e = upload(&p.t.two_blocks, two, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e == cudaErrorMemoryAllocation) return NEDNER_ENOMEM;
     return e ? NEDNER_ECUDA : NEDNER_OK;
@@ -122,11 +250,13 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
 
 nedner_status build_static_tables(nedner_plan_s& p, cudaStream_t s) {
     const Geo& G = p.geo;
-    std::vector<float2> tw(TW_N);
-    for (int k = 0; k < TW_N; ++k) {
-        double a = 2.0 * kPi * (double)k / (double)TW_N;
-        tw[k] = make_float2((float)std::cos(a), (float)-std::sin(a));
-    }
+    // twiddles exp(-2 pi i k / N) for every power of two N <= TW_N, at [N + k]
+    std::vector<float2> tw(2 * TW_N, make_float2(0.f, 0.f));
+    for (int N = 1; N <= TW_N; N *= 2)
+        for (int k = 0; k < N; ++k) {
+            double a = 2.0 * kPi * (double)k / (double)N;
+            tw[N + k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+        }
     std::vector<float> dx(G.nxh), dy(G.nyp), dt(G.Nt);
     for (int j = 0; j < G.nxh; ++j) dx[j] = (float)(1.0 / win_phihat(p.win, (double)j / G.Lx));
     for (int b = 0; b < G.nyp; ++b) dy[b] = (float)(1.0 / win_phihat(p.win, (double)(b - G.ny / 2) / G.Ly));
@@ -134,6 +264,7 @@ nedner_status build_static_tables(nedner_plan_s& p, cudaStream_t s) {
     std::vector<double> cd;
     win_tap_polys(p.win, G.D, cd);
     std::vector<float> cf(cd.begin(), cd.end());
+    for (size_t i = 0; i < cf.size() && i < sizeof(p.tap.c) / sizeof(float); ++i) p.tap.c[i] = cf[i];
     // lateral part of nu^2: (c Nt dt)^2 ((jx/X)^2 + (jy/Y)^2), jx = 0..nx/2, jy = -ny/2..ny/2
     const double X = p.grid.nx * p.grid.dx, Y = p.grid.ny * p.grid.dy;
     const double T = p.c * p.Nt * p.dt;
@@ -167,13 +298,27 @@ void choose_chunks(nedner_plan_s& p) {
     Geo& G = p.geo;
     Chunks& c = p.ch;
     const long budget = 64 * 1024;                     // bytes of shared memory per CTA
-    c.c1 = std::min<long>(32, std::max<long>(2, pow2_floor(budget / (8L * G.Lx))));
+    // spread + x-FFT: lane groups of a full warp (32 time samples) while the
+    // row fits in 128 KB of shared memory, smaller groups beyond
+    c.c1 = std::min<long>(32, std::max<long>(2, pow2_floor((128L * 1024) / (8L * G.Lx))));
     c.c1 = std::min(c.c1, G.Nt);
+    c.threads1 = G.Lx >= 512 ? 512 : 256;
+    c.groups1 = c.threads1 / c.c1;
     c.smem1 = (size_t)G.Lx * c.c1 * 8;                 // real row + complex scratch
+    {
+        // the spread's batch staging (16 entries per lane group) lives in the scratch half
+        const size_t staging = (size_t)c.groups1 * 16 * (1 + spread_taps(G.w) + c.c1) * 4;
+        c.smem1 = std::max(c.smem1, (size_t)G.Lx * c.c1 * 4 + staging);
+    }
+    c.ca = c.c1;
+    c.smax = (int)std::max<long>(32, budget / (4L * c.ca));
+    c.smem_interp = (size_t)G.Lx * c.ca * 8 + (size_t)c.smax * c.ca * 4;
+    c.smem_grad = (size_t)G.Lx * c.ca * 8 + (size_t)c.smax * 8;
     c.c2 = std::min<long>(16, std::max<long>(1, pow2_floor(budget / (16L * G.Ly))));
     c.c2 = std::min(c.c2, G.Nt);
     c.smem2 = (size_t)G.Ly * c.c2 * 16;
-    c.smem3 = (size_t)(2 * G.Lt + (G.nz + 1) + 2 * G.nz) * 8 + (size_t)G.w * (G.D + 1) * 4;
+    c.smem3 = (size_t)(2 * G.Lt + (G.nz + 1) + 2 * G.nz) * 8;
+    c.smem3a = c.smem3;
     c.c4 = 1;
     while (c.c4 * 2 <= 16 && c.c4 * 2 <= G.nz && 2L * G.ny * (c.c4 * 2 + 1) * 8 <= 96 * 1024) c.c4 *= 2;
     c.smem4 = (size_t)2 * G.ny * (c.c4 + 1) * 8;
@@ -269,8 +414,11 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     size_t r_bytes = (size_t)G.nxh * G.Ly * Nt * 8;
     size_t v_bytes = (size_t)G.nxh * G.ny * G.nz * 8;
     size_t gh_bytes = (size_t)G.nxh * G.nyp * Nt * 8;
+    // region B also holds the transposed stage's per-slot partial sums
+    size_t pa_bytes = (size_t)2 * M * Nt * 4;
+    size_t q_bytes = (size_t)2 * (Nt / p->ch.ca) * M * 8;
     p->region_a = (std::max(r_bytes, v_bytes) + 255) / 256 * 256;
-    p->ws_bytes = p->region_a + std::max(gh_bytes, v_bytes);
+    p->ws_bytes = p->region_a + std::max(std::max(gh_bytes, v_bytes), std::max(pa_bytes, q_bytes));
     if (o.max_workspace_bytes && p->ws_bytes > o.max_workspace_bytes) { delete p; return NEDNER_ENOMEM; }
     cudaError_t e = cudaMalloc(&p->ws, p->ws_bytes);
     if (e != cudaSuccess) {
@@ -281,6 +429,7 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     st = build_static_tables(*p, s);
     if (st == NEDNER_OK) st = build_sensor_tables(*p, s);
     if (st == NEDNER_OK && configure_fwd_kernels(*p) != cudaSuccess) st = NEDNER_ECUDA;
+    if (st == NEDNER_OK && configure_adj_kernels(*p) != cudaSuccess) st = NEDNER_ECUDA;
     if (st != NEDNER_OK) {
         cudaGetLastError();
         free_tables(p->t);
@@ -353,15 +502,43 @@ nedner_status nedner_ned_stage(nedner_plan_t p, const float* g, void* Ghat, void
     return run(launch_ned_yfft(*p, A, (float2*)Ghat, s));
 }
 
+// Transposed stages shared by the adjoint and the position gradient:
+// p0-shaped input -> R-bar in region A.
+static cudaError_t transposed_to_R(nedner_plan_t p, const float* p0, cudaStream_t s) {
+    float2* A = (float2*)p->ws;
+    float2* B = (float2*)((char*)p->ws + p->region_a);
+    cudaError_t e;
+    if ((e = launch_img_xr2c_adj(*p, p0, B, s))) return e;
+    if ((e = launch_img_yfft_adj(*p, B, A, s))) return e;
+    if ((e = launch_ner_lines_adj(*p, A, B, s))) return e;
+    return launch_ned_yfft_adj(*p, B, A, s);
+}
+
 nedner_status nedner_adjoint(nedner_plan_t p, const float* p0, float* g, void* stream) {
-    (void)p; (void)p0; (void)g; (void)stream;
-    return NEDNER_EINVAL;
+    if (!p || !p0 || (p->M > 0 && !g)) return NEDNER_EINVAL;
+    if (((uintptr_t)p0 & 7) != 0) return NEDNER_EINVAL;
+    if (p->M == 0) return NEDNER_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = transposed_to_R(p, p0, s))) return run(e);
+    float2* A = (float2*)p->ws;
+    float* P = (float*)((char*)p->ws + p->region_a);
+    if ((e = launch_ned_interp_adj(*p, A, P, s))) return run(e);
+    return run(launch_adj_finish(*p, P, g, s));
 }
 
 nedner_status nedner_grad_positions(nedner_plan_t p, const float* g, const float* dL_dp0, float* dL_dxy,
                                     void* stream) {
-    (void)p; (void)g; (void)dL_dp0; (void)dL_dxy; (void)stream;
-    return NEDNER_EINVAL;
+    if (!p || !dL_dp0 || (p->M > 0 && (!g || !dL_dxy))) return NEDNER_EINVAL;
+    if (((uintptr_t)dL_dp0 & 7) != 0) return NEDNER_EINVAL;
+    if (p->M == 0) return NEDNER_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = transposed_to_R(p, dL_dp0, s))) return run(e);
+    float2* A = (float2*)p->ws;
+    float2* Q = (float2*)((char*)p->ws + p->region_a);
+    if ((e = launch_ned_grad(*p, A, g, Q, s))) return run(e);
+    return run(launch_grad_finish(*p, Q, dL_dxy, s));
 }
 
 size_t nedner_workspace_bytes(nedner_plan_t p) { return p ? p->ws_bytes : 0; }

@@ -228,6 +228,57 @@ def ned_stage_static(plan: Plan, g, out=None, stream=None):
     return out
 
 
+def _autograd():
+    import torch
+
+    class ReconFunction(torch.autograd.Function):
+        """p0 = R(x) g as a differentiable op: backward gives dL/dg = R^T dL/dp0
+        (nedner_adjoint) and dL/d(sensor_xy) (nedner_grad_positions, areas
+        held fixed).  The plan's sensor positions must equal sensor_xy."""
+
+        @staticmethod
+        def forward(ctx, g, sensor_xy, plan):
+            ctx.plan = plan
+            ctx.xy_like = (sensor_xy.device, sensor_xy.dtype)
+            ctx.save_for_backward(g)
+            return plan.forward(g.contiguous())
+
+        @staticmethod
+        def backward(ctx, dL_dp0):
+            (g,) = ctx.saved_tensors
+            plan = ctx.plan
+            dL_dp0 = dL_dp0.contiguous()
+            dg = plan.adjoint(dL_dp0) if ctx.needs_input_grad[0] else None
+            dxy = None
+            if ctx.needs_input_grad[1]:
+                dxy = plan.grad_positions(g.contiguous(), dL_dp0).to(device=ctx.xy_like[0],
+                                                                      dtype=ctx.xy_like[1])
+            return dg, dxy, None
+
+    return ReconFunction
+
+
+_RECON = None
+
+
+def reconstruct(plan: Plan, g, sensor_xy=None):
+    """Differentiable reconstruction.  ``sensor_xy``: optional (M, 2) float64
+    tensor of positions (metres); if given and different from the plan's, the
+    plan is moved there first (nedner_set_positions), and gradients with
+    respect to it are available through autograd."""
+    global _RECON
+    if _RECON is None:
+        _RECON = _autograd()
+    import torch
+    if sensor_xy is not None:
+        xy = sensor_xy.detach().to("cpu", torch.float64).numpy()
+        if not np.array_equal(xy, plan._xy):
+            plan.set_positions(xy)
+    else:
+        sensor_xy = torch.as_tensor(plan._xy)
+    return _RECON.apply(g, sensor_xy, plan)
+
+
 def plan_from_config(cfg, **kw) -> Plan:
     """Plan for a workload dict as produced by ``inputs.make_config``/``small_case``."""
     return Plan(cfg["sensor_xy"], cfg["Nt"], cfg["dt"], cfg["c"],
@@ -235,5 +286,5 @@ def plan_from_config(cfg, **kw) -> Plan:
                 sensor_w=kw.pop("sensor_w", cfg.get("h")), **kw)
 
 
-__all__ = ["Plan", "plan_from_config", "ned_stage_static", "NednerError", "library", "LIB_PATH", "SIGNATURES",
+__all__ = ["Plan", "plan_from_config", "ned_stage_static", "reconstruct", "NednerError", "library", "LIB_PATH", "SIGNATURES",
            "WINDOW_KB", "WINDOW_GAUSS"]
