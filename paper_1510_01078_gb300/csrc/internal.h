@@ -46,8 +46,9 @@ struct TapPoly {
     float c[16 * 13];   // [k][d], k < w <= 16, d <= D <= 12
 };
 
-// Register window of the spreading sweep: the window width w rounded up to 4, 8, 12 or 16.
-inline int spread_taps(int w) { return w <= 4 ? 4 : w <= 8 ? 8 : w <= 12 ? 12 : 16; }
+// Taps stored per spreading entry: w taps placed after up to 3 leading zeros
+// (first column aligned to 4), rounded up to a multiple of 4.
+inline int spread_taps(int w) { return ((w + 3) + 3) / 4 * 4; }
 
 // Device-side tables owned by a plan.
 struct DevTables {
@@ -72,8 +73,8 @@ struct DevTables {
     // spreading: per row, entries sorted by first x column, wrapped ones repeated at bx - Lx
     int* xrow_ptr = nullptr;      // [Ly+1]
     int* xent_m = nullptr;        // [E'] sensor
-    float* xent_wx = nullptr;     // [E'][spread_taps(w)] x taps times y tap times sensor factor (zero padded)
-    int* xent_bx = nullptr;       // [E'] first x column, in (-w, Lx)
+    float* xent_wx = nullptr;     // [E'][spread_taps(w)] taps from column xent_bx on (x tap times y tap times sensor factor)
+    int* xent_bx = nullptr;       // [E'] first x column rounded down to a multiple of 4
     int4* seg = nullptr;          // [Ly][groups1] column range [x, y) and entry range [z, w)
     // transposed interpolation: sensors touching each block of kRowBlock rows
     int* band_m = nullptr;        // [B] sensor

@@ -19,17 +19,18 @@ namespace nedner {
 // One CTA owns grid row gy and C consecutive time samples.  Its threads form
 // lane groups of C (lane = time sample); group q owns the column segment
 // seg[gy][q] = [c0, c1) of the shared-memory row [Lx][C].  The row's entries
-// (sensor, y tap) are sorted by their first x column bx; the group sweeps the
-// ones whose taps reach into its segment, keeping 2 WT columns
-// [base, base + 2 WT) in registers.  An entry at bx >= base + WT first moves
-// the window up by WT columns (the lower WT are final: stored once if inside
-// the segment), then its taps (already multiplied by the y tap and the sensor
-// factor) are added at offset bx - base in [0, WT), chosen by a switch that
-// is uniform across the group.  No atomics and no shared-memory
-// read-modify-write; every column of the row is written exactly once.
-// Entries are taken sixteen at a time: their indices, taps and samples of g
-// are loaded together (independent loads in flight) and staged in shared
-// memory, then swept.
+// (sensor, y tap) are sorted by their first x column; each entry's w taps
+// (already multiplied by the y tap and the sensor factor) are stored as WT
+// values starting at a column bx4 that is a multiple of 4 (leading zeros
+// absorb bx - bx4).  The group sweeps the entries whose taps reach into its
+// segment, keeping the 2 WT columns [base, base + 2 WT) in registers: an
+// entry with bx4 - base > WT first moves the window up by WT columns (the
+// lower WT are final: stored once if inside the segment), then its taps are
+// added at offset d = bx4 - base, a multiple of 4 in [0, WT], with WT FMAs
+// (a branch on d with WT/4 + 1 cases, uniform across the group).  No atomics,
+// no shared-memory read-modify-write; every column is written exactly once.
+// Entries are staged sixteen at a time (indices, taps, samples of g loaded
+// together) and then swept.
 // The row is then transformed along x (two real columns packed into one
 // complex FFT) and jx = 0..nx/2 is kept, divided by phihat(jx/Lx).
 // ---------------------------------------------------------------------------
@@ -45,28 +46,35 @@ __device__ __forceinline__ void flush_lower(float (&acc)[2 * WT], float* S, int 
 }
 
 template <int WT, int D>
-__device__ __forceinline__ void add_taps(float (&acc)[2 * WT], const float (&wv)[WT], float gval) {
+__device__ __forceinline__ void add_taps(float (&acc)[2 * WT], const float4 (&wv)[WT / 4], float gval) {
 #pragma unroll
-    for (int k = 0; k < WT; ++k) acc[D + k] = fmaf(wv[k], gval, acc[D + k]);
-}
-
-template <int WT>
-__device__ __forceinline__ void add_at(float (&acc)[2 * WT], const float (&wv)[WT], float gval, int d) {
-    switch (d) {
-#define NEDNER_CASE(D) \
-    case D:            \
-        if (D < WT) add_taps<WT, (D < WT ? D : 0)>(acc, wv, gval); \
-        break;
-        NEDNER_CASE(0) NEDNER_CASE(1) NEDNER_CASE(2) NEDNER_CASE(3) NEDNER_CASE(4) NEDNER_CASE(5)
-        NEDNER_CASE(6) NEDNER_CASE(7) NEDNER_CASE(8) NEDNER_CASE(9) NEDNER_CASE(10) NEDNER_CASE(11)
-        NEDNER_CASE(12) NEDNER_CASE(13) NEDNER_CASE(14) NEDNER_CASE(15)
-#undef NEDNER_CASE
-        default: break;
+    for (int k4 = 0; k4 < WT / 4; ++k4) {
+        acc[D + 4 * k4 + 0] = fmaf(wv[k4].x, gval, acc[D + 4 * k4 + 0]);
+        acc[D + 4 * k4 + 1] = fmaf(wv[k4].y, gval, acc[D + 4 * k4 + 1]);
+        acc[D + 4 * k4 + 2] = fmaf(wv[k4].z, gval, acc[D + 4 * k4 + 2]);
+        acc[D + 4 * k4 + 3] = fmaf(wv[k4].w, gval, acc[D + 4 * k4 + 3]);
     }
 }
 
+// one entry: slide the window to bx4, then add its taps at d = bx4 - base
 template <int WT>
-__global__ void __launch_bounds__(512) k_ned_spread_xfft(Geo G, int C, const float* __restrict__ g,
+__device__ __forceinline__ void sweep_entry(float (&acc)[2 * WT], float* S, int C, int ln, int& base, int c0,
+                                            int c1, int bx4, const float4 (&wv)[WT / 4], float gval) {
+    while (bx4 - base > WT) {
+        flush_lower<WT>(acc, S, C, ln, base, c0, c1);
+        base += WT;
+    }
+    const int d = (bx4 - base) >> 2;
+    if (d == 0) add_taps<WT, 0>(acc, wv, gval);
+    else if (d == 1) add_taps<WT, 4>(acc, wv, gval);
+    else if (d == 2) add_taps<WT, (WT >= 8 ? 8 : 0)>(acc, wv, gval);
+    else if (WT >= 12 && d == 3) add_taps<WT, (WT >= 12 ? 12 : 0)>(acc, wv, gval);
+    else if (WT >= 16 && d == 4) add_taps<WT, (WT >= 16 ? 16 : 0)>(acc, wv, gval);
+    else if (WT >= 20 && d == 5) add_taps<WT, (WT >= 20 ? 20 : 0)>(acc, wv, gval);
+}
+
+template <int WT, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ned_spread_xfft(Geo G, int C, const float* __restrict__ g,
                                                          const int4* __restrict__ seg,
                                                          const int* __restrict__ xent_m,
                                                          const float* __restrict__ xent_wx,
@@ -88,10 +96,10 @@ __global__ void __launch_bounds__(512) k_ned_spread_xfft(Geo G, int C, const flo
     float acc[2 * WT];
 #pragma unroll
     for (int k = 0; k < 2 * WT; ++k) acc[k] = 0.f;
-    int base = sg.x - WT;
+    int base = (sg.x - WT) & ~3;
 
     // per-group staging area for one batch, carved out of the FFT scratch
-    // (unused until the sweep is over): bx[B], taps[B][WT], g[B][C]
+    // (unused until the sweep is over): bx4[B], taps[B][WT], g[B][C]
     constexpr int B = 16;
     const int lane = threadIdx.x & 31;
     const int gbase = lane - ln;
@@ -102,24 +110,21 @@ __global__ void __launch_bounds__(512) k_ned_spread_xfft(Geo G, int C, const flo
 
     for (int e0 = sg.z; e0 < sg.w; e0 += B) {
         const int nbat = min(B, sg.w - e0);
-        // indices of the batch, one entry per lane (lanes >= nbat idle)
         const int m_l = (ln < nbat) ? __ldg(&xent_m[e0 + ln]) : 0;    // entries 0..C-1 of the batch
         for (int j = ln; j < nbat; j += C) st_bx[j] = __ldg(&xent_bx[e0 + j]);
-        // taps of the batch (contiguous, zero padded to WT)
-        const float* wsrc = xent_wx + (size_t)e0 * WT;
-        for (int i = ln; i < nbat * WT; i += C) st_w[i] = __ldg(&wsrc[i]);
-        // samples of g of the batch: B independent loads per lane
+        const float4* wsrc = reinterpret_cast<const float4*>(xent_wx + (size_t)e0 * WT);
+        float4* wdst = reinterpret_cast<float4*>(st_w);
+        for (int i = ln; i < nbat * (WT / 4); i += C) wdst[i] = __ldg(&wsrc[i]);
         float gl[B];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
-            const int src_lane = gbase + (j & (C - 1));
-            const int mj = __shfl_sync(gmask, m_l, src_lane);
+            const int mj = __shfl_sync(gmask, m_l, gbase + (j & (C - 1)));
             gl[j] = (j < nbat && j < C) ? __ldg(&g[(size_t)mj * G.Nt + n0 + ln]) : 0.f;
         }
         if (C < B) {
-            // batches larger than the group: indices of entries C.. come from a second round
+            // batches larger than the group: indices of entries C.. come in further rounds
             for (int j0 = C; j0 < nbat; j0 += C) {
-                int m2 = (ln + j0 < nbat) ? __ldg(&xent_m[e0 + j0 + ln]) : 0;
+                const int m2 = (ln + j0 < nbat) ? __ldg(&xent_m[e0 + j0 + ln]) : 0;
 #pragma unroll
                 for (int j = 0; j < B; ++j) {
                     if (j >= j0 && j < j0 + C) {
@@ -132,24 +137,14 @@ __global__ void __launch_bounds__(512) k_ned_spread_xfft(Geo G, int C, const flo
 #pragma unroll
         for (int j = 0; j < B; ++j) st_g[j * C + ln] = gl[j];
         __syncwarp(gmask);
+#pragma unroll 1
         for (int j = 0; j < nbat; ++j) {
-            const int bx = st_bx[j];
-            const float gval = st_g[j * C + ln];
-            while (bx >= base + WT) {
-                flush_lower<WT>(acc, S, C, ln, base, sg.x, sg.y);
-                base += WT;
-            }
-            float wv[WT];
-            const float4* wp = reinterpret_cast<const float4*>(st_w + j * WT);
+            const int bxa = st_bx[j];
+            const float ga = st_g[j * C + ln];
+            float4 wa[WT / 4];
 #pragma unroll
-            for (int k4 = 0; k4 < WT / 4; ++k4) {
-                const float4 t = wp[k4];
-                wv[4 * k4 + 0] = t.x;
-                wv[4 * k4 + 1] = t.y;
-                wv[4 * k4 + 2] = t.z;
-                wv[4 * k4 + 3] = t.w;
-            }
-            add_at<WT>(acc, wv, gval, bx - base);
+            for (int k4 = 0; k4 < WT / 4; ++k4) wa[k4] = wdst[j * (WT / 4) + k4];
+            sweep_entry<WT>(acc, S, C, ln, base, sg.x, sg.y, bxa, wa, ga);
         }
         __syncwarp(gmask);
     }
@@ -454,10 +449,11 @@ __global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, const float2* __
 cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     cudaError_t e;
     const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<4>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
-    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<8>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
-    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<12>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
-    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<16>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+#define NEDNER_ATTR_SPREAD(WT)                                                                              \
+    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 256>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 512>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+    NEDNER_ATTR_SPREAD(8) NEDNER_ATTR_SPREAD(12) NEDNER_ATTR_SPREAD(16) NEDNER_ATTR_SPREAD(20)
+#undef NEDNER_ATTR_SPREAD
     if ((e = cudaFuncSetAttribute(k_ned_yfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2))) return e;
 #define NEDNER_ATTR_NER(W, D) \
     if ((e = cudaFuncSetAttribute(k_ner_lines<W, D>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e;
@@ -472,14 +468,18 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
 cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float2* R, cudaStream_t s) {
     const Geo& G = p.geo;
     dim3 grid(G.Ly, G.Nt / p.ch.c1);
-#define NEDNER_SPREAD(WT)                                                                                 \
-    k_ned_spread_xfft<WT><<<grid, p.ch.threads1, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m,       \
-                                                                 p.t.xent_wx, p.t.xent_bx, p.t.deconv_x, p.t.tw, R)
+#define NEDNER_SPREAD(WT)                                                                                    \
+    if (p.ch.threads1 <= 256)                                                                                \
+        k_ned_spread_xfft<WT, 256><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
+                                                                 p.t.xent_bx, p.t.deconv_x, p.t.tw, R);      \
+    else                                                                                                     \
+        k_ned_spread_xfft<WT, 512><<<grid, 512, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
+                                                                 p.t.xent_bx, p.t.deconv_x, p.t.tw, R)
     switch (spread_taps(G.w)) {
-        case 4: NEDNER_SPREAD(4); break;
         case 8: NEDNER_SPREAD(8); break;
         case 12: NEDNER_SPREAD(12); break;
-        default: NEDNER_SPREAD(16); break;
+        case 16: NEDNER_SPREAD(16); break;
+        default: NEDNER_SPREAD(20); break;
     }
 #undef NEDNER_SPREAD
     return cudaGetLastError();

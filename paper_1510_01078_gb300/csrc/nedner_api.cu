@@ -141,10 +141,16 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
         }
         std::stable_sort(tmp.begin(), tmp.end(), [](const XE& a, const XE& b) { return a.bx < b.bx; });
         const int base = (int)xent_m.size();
+        const int WT = spread_taps(w);
         for (const XE& x : tmp) {
+            const int bx4 = x.bx & ~3;                  // floor to a multiple of 4 (also for negative bx)
+            const int off = x.bx - bx4;
             xent_m.push_back(x.m);
-            xent_bx.push_back(x.bx);
-            for (int k = 0; k < spread_taps(w); ++k) xent_wx.push_back(k < w ? x.w * wx[(size_t)x.m * w + k] : 0.f);
+            xent_bx.push_back(bx4);
+            for (int k = 0; k < WT; ++k) {
+                const int t = k - off;
+                xent_wx.push_back(t >= 0 && t < w ? x.w * wx[(size_t)x.m * w + t] : 0.f);
+            }
         }
         xrow_ptr[r + 1] = (int)xent_m.size();
         const int Er = (int)tmp.size();
