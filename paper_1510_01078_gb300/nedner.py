@@ -259,6 +259,35 @@ def _autograd():
 
 
 _RECON = None
+_MODEL = None
+
+
+def _model_autograd():
+    import torch
+
+    class ModelFunction(torch.autograd.Function):
+        """g = R^T p0 (nedner_adjoint) as a differentiable op; its backward is
+        nedner_forward.  With an unweighted plan this is the physical forward
+        model A (data from an initial pressure), A^T being the unweighted R."""
+
+        @staticmethod
+        def forward(ctx, p0, plan):
+            ctx.plan = plan
+            return plan.adjoint(p0.contiguous())
+
+        @staticmethod
+        def backward(ctx, dL_dg):
+            return ctx.plan.forward(dL_dg.contiguous()), None
+
+    return ModelFunction
+
+
+def model(plan: Plan, p0):
+    """Differentiable g = R^T p0 (see ``ModelFunction``)."""
+    global _MODEL
+    if _MODEL is None:
+        _MODEL = _model_autograd()
+    return _MODEL.apply(p0, plan)
 
 
 def reconstruct(plan: Plan, g, sensor_xy=None):
@@ -286,5 +315,5 @@ def plan_from_config(cfg, **kw) -> Plan:
                 sensor_w=kw.pop("sensor_w", cfg.get("h")), **kw)
 
 
-__all__ = ["Plan", "plan_from_config", "ned_stage_static", "reconstruct", "NednerError", "library", "LIB_PATH", "SIGNATURES",
+__all__ = ["Plan", "plan_from_config", "ned_stage_static", "reconstruct", "model", "NednerError", "library", "LIB_PATH", "SIGNATURES",
            "WINDOW_KB", "WINDOW_GAUSS"]
