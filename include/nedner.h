@@ -78,7 +78,23 @@ typedef struct {
     int band_mask;                /* 1: zero F where nu is outside [-Nt/2, Nt/2) */
     size_t max_workspace_bytes;   /* 0 = no limit; plan fails with ENOMEM above it */
     const double* sensor_w;       /* host [M] detector areas h_m (m^2), or NULL for X Y / M */
+    int ned_mode;                 /* NEDNER_NED_NUFFT (default) or NEDNER_NED_TENSOR_BF16, see below */
 } nedner_opts;
+
+/*
+ * ned_mode selects how nedner_forward and nedner_ned_stage evaluate stage (a):
+ *   NEDNER_NED_NUFFT        the NED-NUFFT of Sec. 3.2 (any sensor layout);
+ *   NEDNER_NED_TENSOR_BF16  sensors on a tensor product x_m = xs[a], y_m = ys[b],
+ *                           m = b * 128 + a, 128 x 128 of them, output grid
+ *                           nx = ny = 256: the NED sum (Eq. NUDFT2 with a separable
+ *                           exponent) evaluated exactly as two complex GEMMs per time
+ *                           sample on the tensor cores, BF16 operands with a hi + lo
+ *                           split of every factor and FP32 accumulation.  Other
+ *                           layouts give NEDNER_EINVAL.  The transposed entry points
+ *                           (nedner_adjoint, nedner_grad_positions) always use the
+ *                           NUFFT formulation.
+ */
+enum { NEDNER_NED_NUFFT = 0, NEDNER_NED_TENSOR_BF16 = 1 };
 
 /*
  * Build a plan (host tables, device tables, device workspace).
@@ -89,7 +105,7 @@ typedef struct {
  *   out_grid   output grid (see nedner_grid).
  *   window     interpolation window of both NUFFTs (Sec. 3.1-3.2).
  *   sigma      oversampling factor (the paper's c > 1); this build supports 2.0.
- *   opts       NULL for defaults {1, 0, 0, NULL}.
+ *   opts       NULL for defaults {1, 0, 0, NULL, NEDNER_NED_NUFFT}.
  *   stream     stream used for the table uploads (synchronised before return).
  *   out        receives the plan; untouched on error.
  * Returns NEDNER_OK, NEDNER_EINVAL, NEDNER_ERANGE, NEDNER_ENOMEM or NEDNER_ECUDA.

@@ -84,6 +84,19 @@ struct DevTables {
     int ntasks = 0;
 };
 
+// Tensor-product NED state (tcgen05 GEMM path).
+struct TPState {
+    int enabled = 0;
+    int sms = 0;                  // multiprocessors of the device
+    void* work = nullptr;         // device: operand matrices of the data, GEMM 1 output, Nyquist line
+    size_t work_bytes = 0;
+    void* ex = nullptr;           // device BF16: 4 matrices (Re hi, Re lo, Im hi, Im lo), rows jx < nx/2, K = a
+    void* ey = nullptr;           // device BF16: 3 tiles x 6 matrices (Re hi/lo, Im hi/lo, -Im hi/lo), rows jy, K = b
+    float2* exn = nullptr;        // device FP32: Ex row jx = nx/2
+    float2* eyf = nullptr;        // device FP32: Ey [ny+1][nys]
+    int* err = nullptr;           // device flag: a bounded wait ran out
+};
+
 }  // namespace nedner
 
 struct nedner_plan_s {
@@ -97,6 +110,7 @@ struct nedner_plan_s {
     std::vector<double> xy, h;
     nedner::DevTables t;
     nedner::TapPoly tap{};
+    nedner::TPState tp;
     void* ws = nullptr;           // device workspace
     size_t ws_bytes = 0;
     size_t region_a = 0;          // bytes of region A (R / V), region B follows (Ghat / Y)
@@ -123,5 +137,11 @@ cudaError_t launch_adj_finish(const nedner_plan_s& p, const float* P, float* g, 
 cudaError_t launch_ned_grad(const nedner_plan_s& p, const float2* R, const float* g, float2* Q, cudaStream_t s);
 cudaError_t launch_grad_finish(const nedner_plan_s& p, const float2* Q, float* dxy, cudaStream_t s);
 cudaError_t configure_adj_kernels(const nedner_plan_s& p);
+
+// tensor-product NED (kernels_tp.cu)
+cudaError_t configure_tp_kernels();
+cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, cudaStream_t s);
+size_t tp_work_bytes(int Nt);
+constexpr int TP_SENSORS = 128;   // sensors per axis the tensor-core path is built for
 
 }  // namespace nedner

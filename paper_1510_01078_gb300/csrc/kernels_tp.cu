@@ -1,0 +1,445 @@
+// Tensor-product NED stage on the tcgen05 tensor cores.
+//
+// When the sensors form a tensor product x_m = xs[a], y_m = ys[b]
+// (m = b * nxs + a), the NED sum of Eq. disc_rec factorises (Eq. NUDFT2 with a
+// separable exponent):
+//   G[jx, jy, n] = sum_b Ey[jy, b] sum_a Ex[jx, a] A[b, a, n],
+//   Ex[jx, a] = exp(-2 pi i jx xs[a] / X), Ey[jy, b] = exp(-2 pi i jy ys[b] / Y),
+//   A[b, a, n] = w_m g[m, n],
+// i.e. two dense complex contractions per time sample, evaluated exactly (no
+// window, no oversampled grid) on the tensor cores:
+//   GEMM 1 (per n):  D[jx, b] = sum_a Ex[jx, a] A[b, a, n]        M = jx, N = b, K = a
+//   GEMM 2 (per n):  G[jx, jy] = sum_b D[jx, b] Ey[jy, b]         M = jx, N = jy, K = b
+// Operands are BF16 with a hi + lo split of every real factor
+// (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)); each real product is
+// formed as hi*hi + lo*hi + hi*lo with FP32 accumulation in tensor memory.
+// Shapes handled: nxs = nys = 128 sensors per axis, nx = ny = 256 output
+// grid (jx = 0..127 from GEMM tiles of M = 128; jy in three N tiles:
+// -128..-1, 0..127 and +128 padded to 16).  The line jx = 128 is evaluated on
+// the CUDA cores in FP32 (k_tp_nyq_t, k_tp_nyq_g).
+//
+// Operand tiles live in global memory already in the tensor cores'
+// K-major, unswizzled shared-memory layout, split in K chunks of 64 so that
+// every (matrix, chunk) is one contiguous block moved by a single bulk copy
+// (cp.async.bulk, completion on an mbarrier).  Within a chunk, element
+// (row r, k) is at ((r/8) * 8 + k/8) * 64 + (r%8) * 8 + k%8 (core matrices
+// of 8 rows x 16 bytes; 128 bytes between core matrices along K, 1024 bytes
+// between 8-row groups).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace nedner {
+namespace tp {
+
+constexpr int K = 128;                 // contraction length (sensors per axis)
+constexpr int KC = 64;                 // K chunk
+constexpr int ROWS = 128;              // M and N of the main tiles
+constexpr uint32_t CHUNK = ROWS * KC * 2;          // 16 KB per (128-row matrix, chunk)
+constexpr uint32_t MAT = ROWS * K * 2;             // 32 KB per 128-row matrix
+constexpr uint32_t SMALL_ROWS = 16;                // rows of the jy = +128 tile
+constexpr uint32_t SMALL_CHUNK = SMALL_ROWS * KC * 2;  // 2 KB
+constexpr uint32_t SMALL_MAT = SMALL_ROWS * K * 2;     // 4 KB
+constexpr int WAIT_LIMIT = 1 << 26;    // iterations of a bounded mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// element offset of (r, k) inside a chunked K-major matrix with `rows` rows
+__device__ __forceinline__ int tile_off(int r, int k, int rows) {
+    const int c = k >> 6, kk = k & 63;
+    return c * rows * KC + (((r >> 3) * (KC >> 3) + (kk >> 3)) << 6) + ((r & 7) << 3) + (kk & 7);
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle, LBO 128 B (along K), SBO 1024 B (8-row groups)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// bounded wait for the phase of parity `parity`; false if it did not complete
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < WAIT_LIMIT && !done; ++it) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(parity)
+                     : "memory");
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// ---------------------------------------------------------------------------
+// prep: A[b][a][n] = w_m g[m][n] -> per n, matrices (hi, lo) with rows b, K = a
+// (256 threads; CTA = 16 time samples x 4 rows b)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __restrict__ g,
+                                                 const float* __restrict__ fac, __nv_bfloat16* __restrict__ At) {
+    __shared__ float tile[4 * K][17];
+    const int n0 = blockIdx.x * 16;
+    const int b0 = blockIdx.y * 4;
+    for (int i = threadIdx.x; i < 4 * K * 16; i += blockDim.x) {
+        const int r = i >> 4, c = i & 15;                   // r = (b - b0) * K + a
+        const int m = (b0 + (r >> 7)) * K + (r & 127);
+        tile[r][c] = (n0 + c < G.Nt) ? fac[m] * g[(size_t)m * G.Nt + n0 + c] : 0.f;
+    }
+    __syncthreads();
+    // items: 16 n x 4 b x 16 groups of 8 a
+    for (int it = threadIdx.x; it < 16 * 4 * 16; it += blockDim.x) {
+        const int c = it >> 6, rb = (it >> 4) & 3, ag = it & 15;
+        const int n = n0 + c;
+        if (n >= G.Nt) continue;
+        __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) split_bf16(tile[rb * K + ag * 8 + j][c], hi[j], lo[j]);
+        const int off = tile_off(b0 + rb, ag * 8, ROWS);
+        __nv_bfloat16* base = At + (size_t)n * 2 * (ROWS * K);
+        *reinterpret_cast<uint4*>(base + off) = *reinterpret_cast<uint4*>(hi);
+        *reinterpret_cast<uint4*>(base + ROWS * K + off) = *reinterpret_cast<uint4*>(lo);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// GEMM 1: persistent over n.  Ex (4 matrices: Re hi, Re lo, Im hi, Im lo;
+// rows jx = 0..127, K = a) stays in shared memory; per n the two matrices of
+// A (hi, lo; rows b) are loaded, 12 MMAs per K step of 16 accumulate
+// D_re, D_im (128 x 128 each) in tensor memory, and the epilogue writes D as
+// BF16 hi/lo matrices (rows jx, K = b) for GEMM 2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, 1) k_tp_gemm1(const Geo G, const __nv_bfloat16* __restrict__ Ex,
+                                                     const __nv_bfloat16* __restrict__ At,
+                                                     __nv_bfloat16* __restrict__ Dt, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __nv_bfloat16* sEx = reinterpret_cast<__nv_bfloat16*>(smem);             // 4 x 32 KB
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem + 4 * MAT);    // 2 x 32 KB
+    __shared__ __align__(8) uint64_t load_bar, mma_bar;
+    __shared__ uint32_t taddr_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        bar_init(&load_bar, 1);
+        bar_init(&mma_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tD = taddr_s;                 // columns [0,128): Re, [128,256): Im
+    uint32_t lphase = 0, mphase = 0;
+    bool ok = true;
+
+    if (tid == 0) {
+        expect_tx(&load_bar, 4 * MAT);
+        for (int q = 0; q < 4; ++q) bulk_load(sEx + q * (MAT / 2), Ex + q * (MAT / 2), MAT, &load_bar);
+    }
+    ok = __syncthreads_and(bar_wait(&load_bar, lphase));
+    lphase ^= 1;
+
+    const uint32_t idesc = idesc_bf16(128);
+    for (int n = blockIdx.x; n < G.Nt && ok; n += gridDim.x) {
+        if (tid == 0) {
+            expect_tx(&load_bar, 2 * MAT);
+            bulk_load(sA, At + (size_t)n * 2 * (ROWS * K), 2 * MAT, &load_bar);
+        }
+        ok = __syncthreads_and(bar_wait(&load_bar, lphase));
+        lphase ^= 1;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t ex = smem_u32(sEx), a = smem_u32(sA);
+            for (int c = 0; c < 2; ++c)
+                for (int s = 0; s < KC / 16; ++s) {
+                    const uint32_t off = c * CHUNK + s * 256;
+                    const uint64_t rh = sdesc(ex + 0 * MAT + off), rl = sdesc(ex + 1 * MAT + off);
+                    const uint64_t ih = sdesc(ex + 2 * MAT + off), il = sdesc(ex + 3 * MAT + off);
+                    const uint64_t ah = sdesc(a + 0 * MAT + off), al = sdesc(a + 1 * MAT + off);
+                    const uint32_t acc = (c | s) ? 1u : 0u;
+                    mma(tD, rh, ah, idesc, acc);
+                    mma(tD, rl, ah, idesc, 1u);
+                    mma(tD, rh, al, idesc, 1u);
+                    mma(tD + 128, ih, ah, idesc, acc);
+                    mma(tD + 128, il, ah, idesc, 1u);
+                    mma(tD + 128, ih, al, idesc, 1u);
+                }
+            mma_commit(&mma_bar);
+        }
+        ok = __syncthreads_and(bar_wait(&mma_bar, mphase));
+        mphase ^= 1;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: row jx = 32 warp + lane; columns b
+        const int jx = warp * 32 + lane;
+        __nv_bfloat16* out = Dt + (size_t)n * 4 * (ROWS * K);      // matrices Re hi, Re lo, Im hi, Im lo
+        for (int part = 0; part < 2; ++part) {
+            for (int c0 = 0; c0 < 128; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tD + ((uint32_t)(warp * 32) << 16) + part * 128 + c0, v);
+#pragma unroll
+                for (int g8 = 0; g8 < 4; ++g8) {
+                    __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) split_bf16(__uint_as_float(v[g8 * 8 + j]), hi[j], lo[j]);
+                    const int off = tile_off(jx, c0 + g8 * 8, ROWS);
+                    *reinterpret_cast<uint4*>(out + (2 * part) * (ROWS * K) + off) = *reinterpret_cast<uint4*>(hi);
+                    *reinterpret_cast<uint4*>(out + (2 * part + 1) * (ROWS * K) + off) =
+                        *reinterpret_cast<uint4*>(lo);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (!ok) {
+        // a wait ran out: flag it, give the copies and MMAs in flight one more bounded wait
+        if (lane == 0) atomicExch(err, 1);
+        bar_wait(&load_bar, lphase);
+        bar_wait(&mma_bar, mphase);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tD), "r"(256));
+}
+
+// ---------------------------------------------------------------------------
+// GEMM 2: CTA per (n, jy tile).  Per K chunk: D (4 matrices, rows jx, K = b)
+// and the tile of Ey (6 matrices: Re hi/lo, Im hi/lo, -Im hi/lo; rows jy);
+// 24 MMAs per K step of 16:
+//   G_re = D_re Ey_re - D_im Ey_im,  G_im = D_re Ey_im + D_im Ey_re.
+// Epilogue writes G[jx][jy + ny/2][n] (complex64) for the tile's real rows.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, 1) k_tp_gemm2(const Geo G, const __nv_bfloat16* __restrict__ Dt,
+                                                     const __nv_bfloat16* __restrict__ Ey,
+                                                     float2* __restrict__ Ghat, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t load_bar, mma_bar;
+    __shared__ uint32_t taddr_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n = blockIdx.x;
+    const int tile = blockIdx.y;                                  // 0: jy -128..-1, 1: 0..127, 2: +128
+    const int ntile = (tile == 2) ? (int)SMALL_ROWS : ROWS;
+    const uint32_t bchunk = (tile == 2) ? SMALL_CHUNK : CHUNK;
+    const uint32_t bmat = (tile == 2) ? SMALL_MAT : MAT;
+    // Ey global layout: tile 0 (6 matrices of 32 KB), tile 1 (6 x 32 KB), tile 2 (6 x 4 KB)
+    const __nv_bfloat16* eyt = Ey + (size_t)tile * 6 * (MAT / 2);
+    __nv_bfloat16* sD = reinterpret_cast<__nv_bfloat16*>(smem);                   // 4 x 16 KB (one chunk)
+    __nv_bfloat16* sE = reinterpret_cast<__nv_bfloat16*>(smem + 4 * CHUNK);       // 6 x bchunk
+
+    if (tid == 0) {
+        bar_init(&load_bar, 1);
+        bar_init(&mma_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tG = taddr_s;                  // Re at [0, ntile), Im at [128, 128 + ntile)
+    const uint32_t idesc = idesc_bf16(ntile);
+    bool ok = true;
+    uint32_t lphase = 0, mphase = 0;
+    const __nv_bfloat16* dsrc = Dt + (size_t)n * 4 * (ROWS * K);
+    for (int c = 0; c < 2 && ok; ++c) {
+        if (tid == 0) {
+            expect_tx(&load_bar, 4 * CHUNK + 6 * bchunk);
+            for (int q = 0; q < 4; ++q)
+                bulk_load(sD + q * (CHUNK / 2), dsrc + q * (ROWS * K) + c * (ROWS * KC), CHUNK, &load_bar);
+            for (int q = 0; q < 6; ++q)
+                bulk_load(sE + q * (bchunk / 2), eyt + q * (bmat / 2) + c * (ntile * KC), bchunk, &load_bar);
+        }
+        ok = __syncthreads_and(bar_wait(&load_bar, lphase));
+        lphase ^= 1;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t d = smem_u32(sD), e = smem_u32(sE);
+            for (int s = 0; s < KC / 16; ++s) {
+                const uint32_t off = s * 256;
+                const uint64_t drh = sdesc(d + 0 * CHUNK + off), drl = sdesc(d + 1 * CHUNK + off);
+                const uint64_t dih = sdesc(d + 2 * CHUNK + off), dil = sdesc(d + 3 * CHUNK + off);
+                const uint64_t erh = sdesc(e + 0 * bchunk + off), erl = sdesc(e + 1 * bchunk + off);
+                const uint64_t eih = sdesc(e + 2 * bchunk + off), eil = sdesc(e + 3 * bchunk + off);
+                const uint64_t nih = sdesc(e + 4 * bchunk + off), nil = sdesc(e + 5 * bchunk + off);
+                const uint32_t acc = (c | s) ? 1u : 0u;
+                // G_re = D_re Ey_re + D_im (-Ey_im)
+                mma(tG, drh, erh, idesc, acc);
+                mma(tG, drl, erh, idesc, 1u);
+                mma(tG, drh, erl, idesc, 1u);
+                mma(tG, dih, nih, idesc, 1u);
+                mma(tG, dil, nih, idesc, 1u);
+                mma(tG, dih, nil, idesc, 1u);
+                // G_im = D_re Ey_im + D_im Ey_re
+                mma(tG + 128, drh, eih, idesc, acc);
+                mma(tG + 128, drl, eih, idesc, 1u);
+                mma(tG + 128, drh, eil, idesc, 1u);
+                mma(tG + 128, dih, erh, idesc, 1u);
+                mma(tG + 128, dil, erh, idesc, 1u);
+                mma(tG + 128, dih, erl, idesc, 1u);
+            }
+            mma_commit(&mma_bar);
+        }
+        ok = __syncthreads_and(bar_wait(&mma_bar, mphase));
+        mphase ^= 1;
+    }
+    if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int jx = warp * 32 + lane;
+        const int jy0 = (tile == 0) ? -G.ny / 2 : (tile == 1 ? 0 : G.ny / 2);
+        const int nreal = (tile == 2) ? 1 : ROWS;
+        for (int c0 = 0; c0 < ntile; c0 += 32) {
+            uint32_t vr[32], vi[32];
+            if (c0 + 32 <= ntile) {
+                tmem_ld32(tG + ((uint32_t)(warp * 32) << 16) + c0, vr);
+                tmem_ld32(tG + ((uint32_t)(warp * 32) << 16) + 128 + c0, vi);
+            } else {
+                // a 16-column tile: read 32 columns (the upper 16 hold no data of ours) and use the first
+                tmem_ld32(tG + ((uint32_t)(warp * 32) << 16) + c0, vr);
+                tmem_ld32(tG + ((uint32_t)(warp * 32) << 16) + 128 + c0, vi);
+            }
+            for (int j = 0; j < 32 && c0 + j < nreal; ++j) {
+                const int b = jy0 + c0 + j + G.ny / 2;
+                Ghat[((size_t)jx * G.nyp + b) * G.Nt + n] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+            }
+        }
+    }
+    if (!ok) {
+        if (lane == 0) atomicExch(err, 1);
+        bar_wait(&load_bar, lphase);
+        bar_wait(&mma_bar, mphase);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tG), "r"(256));
+}
+
+// ---------------------------------------------------------------------------
+// The line jx = nx/2 for every jy and n, on the CUDA cores in FP32:
+//   t[b][n] = sum_a Ex[nx/2, a] A[b, a, n]            (k_tp_nyq_t: CTA = 32 n, one b)
+//   G[nx/2, jy, n] = sum_b Ey[jy, b] t[b][n]          (k_tp_nyq_g: CTA = 32 n, one jy)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_tp_nyq_t(const Geo G, const float* __restrict__ g,
+                                                 const float* __restrict__ fac, const float2* __restrict__ exn,
+                                                 float2* __restrict__ t) {
+    const int n = blockIdx.x * 32 + threadIdx.x;
+    const int b = blockIdx.y;
+    if (n >= G.Nt) return;
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int a = 0; a < K; ++a) {
+        const int m = b * K + a;
+        const float v = __ldg(&fac[m]) * __ldg(&g[(size_t)m * G.Nt + n]);
+        const float2 e = __ldg(&exn[a]);
+        s.x = fmaf(e.x, v, s.x);
+        s.y = fmaf(e.y, v, s.y);
+    }
+    t[(size_t)b * G.Nt + n] = s;
+}
+
+__global__ void __launch_bounds__(32) k_tp_nyq_g(const Geo G, const float2* __restrict__ t,
+                                                 const float2* __restrict__ eyf, float2* __restrict__ Ghat) {
+    const int n = blockIdx.x * 32 + threadIdx.x;
+    const int bj = blockIdx.y;                       // jy = bj - ny/2
+    if (n >= G.Nt) return;
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int b = 0; b < K; ++b) {
+        const float2 e = __ldg(&eyf[(size_t)bj * K + b]);
+        const float2 v = __ldg(&t[(size_t)b * G.Nt + n]);
+        s.x = fmaf(e.x, v.x, fmaf(-e.y, v.y, s.x));
+        s.y = fmaf(e.x, v.y, fmaf(e.y, v.x, s.y));
+    }
+    Ghat[((size_t)(G.nx / 2) * G.nyp + bj) * G.Nt + n] = s;
+}
+
+}  // namespace tp
+
+size_t tp_work_bytes(int Nt) {
+    // data operands (hi, lo) + GEMM 1 output (4 matrices) per n, plus the Nyquist-line partial sums
+    return (size_t)Nt * (2 + 4) * tp::MAT + (size_t)Nt * tp::K * sizeof(float2);
+}
+
+size_t tp_gemm1_smem() { return 6 * tp::MAT; }
+size_t tp_gemm2_smem() { return 4 * tp::CHUNK + 6 * tp::CHUNK; }
+
+cudaError_t configure_tp_kernels() {
+    cudaError_t e;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(tp::k_tp_gemm1, a, (int)tp_gemm1_smem()))) return e;
+    if ((e = cudaFuncSetAttribute(tp::k_tp_gemm2, a, (int)tp_gemm2_smem()))) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, cudaStream_t s) {
+    const Geo& G = p.geo;
+    __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(p.tp.work);
+    __nv_bfloat16* Dt = At + (size_t)G.Nt * 2 * (tp::ROWS * tp::K);
+    tp::k_tp_prep<<<dim3((G.Nt + 15) / 16, tp::K / 4), 256, 0, s>>>(G, g, p.t.sens_fac, At);
+    tp::k_tp_gemm1<<<std::min(G.Nt, p.tp.sms), 128, tp_gemm1_smem(), s>>>(G, reinterpret_cast<const __nv_bfloat16*>(p.tp.ex),
+                                                                          At, Dt, p.tp.err);
+    tp::k_tp_gemm2<<<dim3(G.Nt, 3), 128, tp_gemm2_smem(), s>>>(G, Dt, reinterpret_cast<const __nv_bfloat16*>(p.tp.ey),
+                                                               Ghat, p.tp.err);
+    float2* tl = reinterpret_cast<float2*>(Dt + (size_t)G.Nt * 4 * (tp::ROWS * tp::K));
+    tp::k_tp_nyq_t<<<dim3((G.Nt + 31) / 32, tp::K), 32, 0, s>>>(G, g, p.t.sens_fac, p.tp.exn, tl);
+    tp::k_tp_nyq_g<<<dim3((G.Nt + 31) / 32, G.nyp), 32, 0, s>>>(G, tl, p.tp.eyf, Ghat);
+    return cudaGetLastError();
+}
+
+}  // namespace nedner

@@ -56,6 +56,118 @@ void free_sensor_tables(DevTables& t) {
     t.ntasks = 0;
 }
 
+void free_tp(TPState& tp) {
+    cudaFree(tp.work); cudaFree(tp.ex); cudaFree(tp.ey); cudaFree(tp.exn); cudaFree(tp.eyf); cudaFree(tp.err);
+    tp = TPState();
+}
+
+// host BF16 (round to nearest even) and the hi + lo split of a float
+uint16_t f2bf(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf2f(uint16_t h) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// element offset of (r, k) in a chunked K-major operand matrix (K chunks of 64)
+size_t tp_off(int r, int k, int rows) {
+    const int c = k >> 6, kk = k & 63;
+    return (size_t)c * rows * 64 + (size_t)(((r >> 3) * 8 + (kk >> 3)) << 6) + ((r & 7) << 3) + (kk & 7);
+}
+
+// Tensor-product path: check the layout and build the exponent operands.
+nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
+    const int NS = TP_SENSORS;
+    const Geo& G = p.geo;
+    if (p.M != (int64_t)NS * NS || G.nx != 2 * NS || G.ny != 2 * NS) return NEDNER_EINVAL;
+    const double X = p.grid.nx * p.grid.dx, Y = p.grid.ny * p.grid.dy;
+    std::vector<double> xs(NS), ys(NS);
+    for (int a = 0; a < NS; ++a) xs[a] = p.xy[2 * a];
+    for (int b = 0; b < NS; ++b) ys[b] = p.xy[2 * (size_t)b * NS + 1];
+    for (int b = 0; b < NS; ++b)
+        for (int a = 0; a < NS; ++a) {
+            const size_t m = (size_t)b * NS + a;
+            if (std::fabs(p.xy[2 * m] - xs[a]) > 1e-12 * X || std::fabs(p.xy[2 * m + 1] - ys[b]) > 1e-12 * Y)
+                return NEDNER_EINVAL;
+        }
+    const size_t MATE = (size_t)NS * NS;               // elements of a 128-row matrix
+    std::vector<uint16_t> ex(4 * MATE), ey(2 * 6 * MATE + 6 * 16 * NS, 0);
+    for (int jx = 0; jx < NS; ++jx)
+        for (int a = 0; a < NS; ++a) {
+            const double ph = -2.0 * kPi * (double)jx * xs[a] / X;
+            const float re = (float)std::cos(ph), im = (float)std::sin(ph);
+            const size_t o = tp_off(jx, a, NS);
+            const uint16_t rh = f2bf(re), ih = f2bf(im);
+            ex[0 * MATE + o] = rh;
+            ex[1 * MATE + o] = f2bf(re - bf2f(rh));
+            ex[2 * MATE + o] = ih;
+            ex[3 * MATE + o] = f2bf(im - bf2f(ih));
+        }
+    for (int t = 0; t < 3; ++t) {
+        const int rows = (t == 2) ? 16 : NS;
+        const size_t mat = (size_t)rows * NS;
+        const size_t tbase = (size_t)t * 6 * MATE;
+        for (int r = 0; r < rows; ++r) {
+            if (t == 2 && r > 0) continue;                 // padding rows stay zero
+            const int jy = (t == 0) ? r - NS : (t == 1 ? r : NS);
+            for (int b = 0; b < NS; ++b) {
+                const double ph = -2.0 * kPi * (double)jy * ys[b] / Y;
+                const float re = (float)std::cos(ph), im = (float)std::sin(ph);
+                const size_t o = tp_off(r, b, rows);
+                const uint16_t rh = f2bf(re), ih = f2bf(im), nh = f2bf(-im);
+                ey[tbase + 0 * mat + o] = rh;
+                ey[tbase + 1 * mat + o] = f2bf(re - bf2f(rh));
+                ey[tbase + 2 * mat + o] = ih;
+                ey[tbase + 3 * mat + o] = f2bf(im - bf2f(ih));
+                ey[tbase + 4 * mat + o] = nh;
+                ey[tbase + 5 * mat + o] = f2bf(-im - bf2f(nh));
+            }
+        }
+    }
+    std::vector<float2> exn(NS), eyf((size_t)G.nyp * NS);
+    for (int a = 0; a < NS; ++a) {
+        const double ph = -2.0 * kPi * (double)(G.nx / 2) * xs[a] / X;
+        exn[a] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+    }
+    for (int bj = 0; bj < G.nyp; ++bj)
+        for (int b = 0; b < NS; ++b) {
+            const double ph = -2.0 * kPi * (double)(bj - G.ny / 2) * ys[b] / Y;
+            eyf[(size_t)bj * NS + b] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+        }
+    TPState& tp = p.tp;
+    cudaError_t e = cudaSuccess;
+    int dev = 0;
+    if (!e) e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&tp.sms, cudaDevAttrMultiProcessorCount, dev);
+    uint16_t* dex = nullptr;
+    uint16_t* dey = nullptr;
+    if (!e) e = upload(&dex, ex, s);
+    if (!e) e = upload(&dey, ey, s);
+    tp.ex = dex;
+    tp.ey = dey;
+    if (!e) e = upload(&tp.exn, exn, s);
+    if (!e) e = upload(&tp.eyf, eyf, s);
+    tp.work_bytes = tp_work_bytes(G.Nt);
+    if (!e) e = cudaMalloc(&tp.work, tp.work_bytes);
+    if (!e) e = cudaMalloc((void**)&tp.err, sizeof(int));
+    if (!e) e = cudaMemsetAsync(tp.err, 0, sizeof(int), s);
+    if (!e) e = configure_tp_kernels();
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) {
+        cudaGetLastError();
+        free_tp(tp);
+        return e == cudaErrorMemoryAllocation ? NEDNER_ENOMEM : NEDNER_ECUDA;
+    }
+    tp.enabled = 1;
+    return NEDNER_OK;
+}
+
 void free_tables(DevTables& t) {
     cudaFree(t.tw); cudaFree(t.deconv_x); cudaFree(t.deconv_y); cudaFree(t.deconv_t);
     cudaFree(t.tapcoef); cudaFree(t.axy);
@@ -370,8 +482,9 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     if (sigma != 2.0) return NEDNER_EINVAL;
     if (window.kind != NEDNER_WINDOW_KB && window.kind != NEDNER_WINDOW_GAUSS) return NEDNER_EINVAL;
     if (window.width < 4 || window.width > 16 || (window.width & 1)) return NEDNER_EINVAL;
-    nedner_opts o = {1, 0, 0, nullptr};
+    nedner_opts o = {1, 0, 0, nullptr, NEDNER_NED_NUFFT};
     if (opts) o = *opts;
+    if (o.ned_mode != NEDNER_NED_NUFFT && o.ned_mode != NEDNER_NED_TENSOR_BF16) return NEDNER_EINVAL;
 
     nedner_plan_s* p = new (std::nothrow) nedner_plan_s();
     if (!p) return NEDNER_ENOMEM;
@@ -436,9 +549,11 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     if (st == NEDNER_OK) st = build_sensor_tables(*p, s);
     if (st == NEDNER_OK && configure_fwd_kernels(*p) != cudaSuccess) st = NEDNER_ECUDA;
     if (st == NEDNER_OK && configure_adj_kernels(*p) != cudaSuccess) st = NEDNER_ECUDA;
+    if (st == NEDNER_OK && o.ned_mode == NEDNER_NED_TENSOR_BF16) st = build_tp(*p, s);
     if (st != NEDNER_OK) {
         cudaGetLastError();
         free_tables(p->t);
+        free_tp(p->tp);
         cudaFree(p->ws);
         delete p;
         return st;
@@ -464,8 +579,12 @@ nedner_status nedner_forward(nedner_plan_t p, const float* g, float* p0, void* s
     float2* A = (float2*)p->ws;
     float2* B = (float2*)((char*)p->ws + p->region_a);
     cudaError_t e;
-    if ((e = launch_ned_spread_xfft(*p, g, A, s))) return run(e);
-    if ((e = launch_ned_yfft(*p, A, B, s))) return run(e);
+    if (p->tp.enabled) {
+        if ((e = launch_tp_ned(*p, g, B, s))) return run(e);
+    } else {
+        if ((e = launch_ned_spread_xfft(*p, g, A, s))) return run(e);
+        if ((e = launch_ned_yfft(*p, A, B, s))) return run(e);
+    }
     if ((e = launch_ner_lines(*p, B, A, s))) return run(e);
     if ((e = launch_img_yifft(*p, A, B, s))) return run(e);
     return run(launch_img_xc2r(*p, B, p0, s));
@@ -483,9 +602,15 @@ nedner_status nedner_forward_profiled(nedner_plan_t p, const float* g, float* p0
     cudaError_t e = cudaSuccess;
     for (; made <= NEDNER_FORWARD_KERNELS && !e; ++made) e = cudaEventCreate(&ev[made]);
     if (!e) e = cudaEventRecord(ev[0], s);
-    if (!e) e = launch_ned_spread_xfft(*p, g, A, s);
-    if (!e) e = cudaEventRecord(ev[1], s);
-    if (!e) e = launch_ned_yfft(*p, A, B, s);
+    if (p->tp.enabled) {
+        // tensor-product NED: all of stage (a) is reported as the first kernel group
+        if (!e) e = launch_tp_ned(*p, g, B, s);
+        if (!e) e = cudaEventRecord(ev[1], s);
+    } else {
+        if (!e) e = launch_ned_spread_xfft(*p, g, A, s);
+        if (!e) e = cudaEventRecord(ev[1], s);
+        if (!e) e = launch_ned_yfft(*p, A, B, s);
+    }
     if (!e) e = cudaEventRecord(ev[2], s);
     if (!e) e = launch_ner_lines(*p, B, A, s);
     if (!e) e = cudaEventRecord(ev[3], s);
@@ -504,6 +629,7 @@ nedner_status nedner_ned_stage(nedner_plan_t p, const float* g, void* Ghat, void
     cudaStream_t s = (cudaStream_t)stream;
     float2* A = (float2*)p->ws;
     cudaError_t e;
+    if (p->tp.enabled) return run(launch_tp_ned(*p, g, (float2*)Ghat, s));
     if ((e = launch_ned_spread_xfft(*p, g, A, s))) return run(e);
     return run(launch_ned_yfft(*p, A, (float2*)Ghat, s));
 }
@@ -554,6 +680,7 @@ nedner_status nedner_destroy(nedner_plan_t p) {
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
     free_tables(p->t);
+    free_tp(p->tp);
     cudaFree(p->ws);
     delete p;
     return NEDNER_OK;

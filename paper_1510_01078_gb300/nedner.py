@@ -40,7 +40,11 @@ class _Window(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("apply_weights", ctypes.c_int), ("band_mask", ctypes.c_int),
-                ("max_workspace_bytes", ctypes.c_size_t), ("sensor_w", ctypes.c_void_p)]
+                ("max_workspace_bytes", ctypes.c_size_t), ("sensor_w", ctypes.c_void_p),
+                ("ned_mode", ctypes.c_int)]
+
+
+NED_NUFFT, NED_TENSOR_BF16 = 0, 1
 
 
 # symbol -> (restype, argtypes); mirrors include/nedner.h
@@ -112,7 +116,7 @@ class Plan:
 
     def __init__(self, sensor_xy, Nt: int, dt: float, c: float, grid, window=("kb", 12), sigma: float = 2.0,
                  apply_weights: bool = True, band_mask: bool = False, sensor_w=None,
-                 max_workspace_bytes: int = 0, stream=None):
+                 max_workspace_bytes: int = 0, stream=None, ned_mode: str = "nufft"):
         lib = _load()
         self._xy = np.ascontiguousarray(np.asarray(sensor_xy, dtype=np.float64).reshape(-1, 2))
         self.M = int(self._xy.shape[0])
@@ -123,8 +127,9 @@ class Plan:
         kind = {"kb": WINDOW_KB, "gauss": WINDOW_GAUSS}[window[0]] if isinstance(window[0], str) else int(window[0])
         w = _Window(kind, int(window[1]))
         self._h = None if sensor_w is None else np.ascontiguousarray(np.asarray(sensor_w, dtype=np.float64))
+        mode = {"nufft": NED_NUFFT, "tensor_bf16": NED_TENSOR_BF16}[ned_mode]
         opts = _Opts(int(bool(apply_weights)), int(bool(band_mask)), int(max_workspace_bytes),
-                     None if self._h is None else self._h.ctypes.data)
+                     None if self._h is None else self._h.ctypes.data, mode)
         handle = ctypes.c_void_p()
         st = lib.nedner_plan(self._xy.ctypes.data if self.M else None, self.M, self.Nt, float(dt), float(c),
                              ctypes.byref(g), w, float(sigma), ctypes.byref(opts), _stream_ptr(stream),
