@@ -170,6 +170,8 @@ def main():
     ap.add_argument("--impl", default="nedner", choices=["nedner", "reference"])
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ned-mode", default="nufft", choices=["nufft", "tensor_bf16"],
+                    help="stage (a) as NUFFT (any layout) or tensor-core GEMMs (128x128 tensor grids)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -202,7 +204,7 @@ def main():
     from paper_1510_01078_gb300 import nedner
 
     stream = torch.cuda.current_stream(dev)
-    plan = nedner.plan_from_config(cfg)
+    plan = nedner.plan_from_config(cfg, ned_mode=args.ned_mode)
     g = torch.as_tensor(np.asarray(cfg["g"], dtype=np.float32), device=dev).contiguous()
     p0 = torch.empty((cfg["nz"], cfg["ny"], cfg["nx"]), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -267,6 +269,11 @@ def main():
     # roofline of the dominant kernel
     abytes = algorithmic_bytes(cfg)
     avg = {k: sum(v) / len(v) for k, v in per_kernel.items()}
+    if args.ned_mode != "nufft":
+        # stage (a) is one group of tensor-core kernels, reported under the first name
+        avg = {("tp_ned_gemm" if k == "ned_spread_xfft" else k): v for k, v in avg.items() if k != "ned_yfft"}
+        M, Nt = cfg["sensor_xy"].shape[0], cfg["Nt"]
+        abytes = dict(abytes, tp_ned_gemm=M * Nt * 4 + (cfg["nx"] // 2 + 1) * (cfg["ny"] + 1) * Nt * 8)
     dom = max(avg, key=avg.get)
     peak, peak_kind = peaks()
     kernels = {k: {"ms": round(avg[k], 5), "share": round(avg[k] / sum(avg.values()), 4),
@@ -275,7 +282,8 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic_for(dom), "peak_source": peak_kind}
     # the spread kernel's own fraction (the metric names spread/interp)
-    spread_frac = round(abytes["ned_spread_xfft"] / (avg["ned_spread_xfft"] * 1e-3) / 1e9 / peak, 4)
+    spread_frac = (round(abytes["ned_spread_xfft"] / (avg["ned_spread_xfft"] * 1e-3) / 1e9 / peak, 4)
+                   if "ned_spread_xfft" in avg else None)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -294,7 +302,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded balls + 20 dB noise)",
                 "config": {"workload": describe(cfg), "l2": "flushed between timed steps (256 MB write)",
-                           "parallelism": "independent reconstruction per GPU"},
+                           "parallelism": "independent reconstruction per GPU", "ned_mode": args.ned_mode},
                 "roofline": roofline, "spread_frac_of_peak": spread_frac, "kernels": kernels,
                 "cpu_baseline": cpu, "clocks": clk,
                 "e2e": {"value": voxels * world / (e2e_step / 1e3), "unit": "voxels/s",
