@@ -200,6 +200,18 @@ nedner_status nedner_forward_profiled(nedner_plan_t plan, const float* g, float*
 #define NEDNER_STATIC_SCRATCH_BYTES (16u << 20)
 nedner_status nedner_ned_stage_static(nedner_plan_t plan, const float* g, void* Ghat, void* stream);
 
+/*
+ * Device-side status of the plan's tensor-core kernels (NEDNER_NED_TENSOR_BF16).
+ * Those kernels bound every wait on an mbarrier (bulk copies, MMA
+ * completion); when one runs out the kernel sets a flag and returns early,
+ * leaving its output incomplete, instead of hanging.  Waits for the device,
+ * stores 1 in *flags if such a wait ran out since the last call (0 otherwise,
+ * and always 0 for plans without the tensor-core stage) and clears the flag.
+ * Synchronous.  Returns NEDNER_EINVAL for a null argument, NEDNER_ECUDA if
+ * the device reports an error.
+ */
+nedner_status nedner_device_status(nedner_plan_t plan, int* flags);
+
 /* Bytes of device workspace held by the plan. */
 size_t nedner_workspace_bytes(nedner_plan_t plan);
 

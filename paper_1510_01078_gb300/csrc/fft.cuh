@@ -202,4 +202,71 @@ __device__ __forceinline__ float2* block_fft(float2* a, float2* b, int N, int nb
     return dir < 0 ? block_fft_dir<-1>(a, b, N, nb, ld, tw) : block_fft_dir<+1>(a, b, N, nb, ld, tw);
 }
 
+// ---------------------------------------------------------------------------
+// In-place variant.  Every thread keeps its share of a pass in registers, so
+// one buffer holds the data throughout; the caller guarantees
+// N * nb <= PER * blockDim.x (PER a multiple of 16).  The buffer is padded:
+// linear index a = p * nb + b (point p, column b) lives at padx(a), one spare
+// slot after every 16 values.  With the radix-16 passes first and the
+// remaining radix-2/4/8 pass last, the 16 lanes of a half-warp then touch 16
+// distinct 8-byte bank pairs on every load and store, for every nb.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int padx(int a) { return a + (a >> 4); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
+
+template <int R, int DIR, int PER>
+__device__ __forceinline__ void fft_pass_ip(float2* buf, int N, int Ns, int nb, const float2* __restrict__ tw) {
+    constexpr int IT = PER / R;
+    const int stride = N / R;
+    const int lnb = ilog2(nb);
+    const int items = stride << lnb;
+    const int step = N / (Ns * R);
+    float2 v[IT][R];
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int it = threadIdx.x + i * blockDim.x;
+        if (it < items) {
+            const int j = it >> lnb, b = it & (nb - 1);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[i][r] = buf[padx(((j + r * stride) << lnb) + b)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int it = threadIdx.x + i * blockDim.x;
+        if (it < items) {
+            const int j = it >> lnb, b = it & (nb - 1);
+            const int k = j & (Ns - 1);
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], twiddle(tw, k * r * step, N, DIR));
+            }
+            dft_reg<R, DIR>(v[i]);
+            const int i0 = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[padx(((i0 + r * Ns) << lnb) + b)] = v[i][out_index<R>(r)];
+        }
+    }
+    __syncthreads();
+}
+
+template <int PER, int DIR>
+__device__ __forceinline__ void block_fft_ip_dir(float2* buf, int N, int nb, const float2* __restrict__ tw) {
+    __syncthreads();
+    int Ns = 1;
+    int rem = ilog2(N);
+    for (; rem >= 4; rem -= 4, Ns <<= 4) fft_pass_ip<16, DIR, PER>(buf, N, Ns, nb, tw);
+    if (rem == 3) fft_pass_ip<8, DIR, PER>(buf, N, Ns, nb, tw);
+    else if (rem == 2) fft_pass_ip<4, DIR, PER>(buf, N, Ns, nb, tw);
+    else if (rem == 1) fft_pass_ip<2, DIR, PER>(buf, N, Ns, nb, tw);
+}
+
+// In-place transform of nb columns of length N in a padded buffer.
+template <int PER>
+__device__ __forceinline__ void block_fft_ip(float2* buf, int N, int nb, int dir, const float2* __restrict__ tw) {
+    if (dir < 0) block_fft_ip_dir<PER, -1>(buf, N, nb, tw);
+    else block_fft_ip_dir<PER, +1>(buf, N, nb, tw);
+}
+
 }  // namespace nedner

@@ -34,6 +34,8 @@ struct Chunks {
     int threads1;  // threads per CTA in the spread stage
     int ca;        // time samples per CTA in the transposed interpolation stage
     int smax;      // sensors per task in the transposed interpolation stage
+    int lpc;       // line groups per CTA in the NER stage
+    int threads3;  // threads per CTA in the NER stage
     size_t smem1, smem2, smem3, smem4, smem5;
     size_t smem_interp, smem_grad, smem3a;
 };

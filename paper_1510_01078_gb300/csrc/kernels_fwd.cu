@@ -9,6 +9,7 @@
 //     -- img_xc2r         -->  p0   [nz][ny][nx]       x complex-to-real IFFT
 #include <cuda_runtime.h>
 
+
 #include "fft.cuh"
 #include "internal.h"
 
@@ -248,123 +249,148 @@ __device__ __forceinline__ FF nu_abs(const Geo& G, float2 axy, int l) {
     return quick_two_sum(r, resid * (0.5f / r));
 }
 
-// sum_k P_k(s) B[(mu0 + k) mod Lt] with the tap polynomials unrolled (Horner)
+// sum_k P_k(s) B[((mu0 + k) mod Lt) * 2^lld + col] (padded buffer) with the tap polynomials unrolled (Horner)
 template <int W, int D>
-__device__ __forceinline__ float2 ner_gather(const TapPoly& P, const float2* Bf, int mu0, float s, int Lt) {
+__device__ __forceinline__ float2 ner_gather(const TapPoly& P, const float2* Bf, int mu0, float s, int Lt, int lld,
+                                             int col) {
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < W; ++k) {
         float p = P.c[k * (D + 1) + D];
 #pragma unroll
         for (int d = D - 1; d >= 0; --d) p = fmaf(p, s, P.c[k * (D + 1) + d]);
-        const float2 b = Bf[(mu0 + k) & (Lt - 1)];
+        const float2 b = Bf[padx((((mu0 + k) & (Lt - 1)) << lld) + col)];
         acc.x = fmaf(p, b.x, acc.x);
         acc.y = fmaf(p, b.y, acc.y);
     }
     return acc;
 }
 
+// coefficient(l) * F(nu_l) for one line whose oversampled spectrum is column
+// `col` of the padded buffer Bf with 2^lld columns; j0: the line is j = 0
 template <int W, int D>
-__global__ void __launch_bounds__(256) k_ner_lines(Geo G, const __grid_constant__ TapPoly P,
-                                                   const float2* __restrict__ Ghat,
-                                                   const float2* __restrict__ axy_tab,
-                                                   const float* __restrict__ deconv_t,
-                                                   const float2* __restrict__ tw, float2* __restrict__ V) {
+__device__ __forceinline__ float2 ner_value(const Geo& G, const TapPoly& P, float2 axy, bool j0, int l,
+                                            const float2* Bf, int lld, int col) {
+    FF nu = nu_abs(G, axy, l);
+    float Wj;
+    if (l == 0) {
+        Wj = j0 ? 2.f : 0.f;
+        nu = {0.f, 0.f};
+    } else {
+        Wj = 2.f * G.sqrt_az * (float)abs(l) / nu.hi;
+        if (l < 0) nu = {-nu.hi, -nu.lo};
+    }
+    float cl = G.apply_weights ? Wj * G.scale : G.scale;
+    if (G.band_mask) {
+        const double nd = (double)nu.hi + (double)nu.lo;
+        if (!(nd >= -0.5 * G.Nt - 1e-9 && nd < 0.5 * G.Nt - 1e-9)) cl = 0.f;
+    }
+    if (cl == 0.f) return make_float2(0.f, 0.f);
+    // v = sigma nu (sigma = 2): exact scaling of the pair
+    const float vh = 2.f * nu.hi, vl = 2.f * nu.lo;
+    float fl = floorf(vh);
+    float t = (vh - fl) + vl;
+    if (t < 0.f) { t += 1.f; fl -= 1.f; }
+    if (t >= 1.f) { t -= 1.f; fl += 1.f; }
+    const int ifl = (int)fl;
+    const float2 acc = ner_gather<W, D>(P, Bf, ifl - W / 2 + 1, 2.f * t - 1.f, G.Lt, lld, col);
+    // exp(-i pi nu) = exp(-i pi v/2) = (-i)^floor(v) exp(-i pi t / 2)
+    float sn, cs;
+    sincospif(0.5f * t, &sn, &cs);
+    float2 ph = make_float2(cs, -sn);
+    const int q = ifl & 3;
+    if (q == 1) ph = make_float2(ph.y, -ph.x);
+    else if (q == 2) ph = make_float2(-ph.x, -ph.y);
+    else if (q == 3) ph = make_float2(-ph.y, ph.x);
+    return cscale(cmul(ph, acc), cl);
+}
+
+// One CTA per LPC consecutive line groups (kx, k0..k0+LPC-1).  The LPC lines
+// (kx, ky) are transformed together (a batched FFT, one column per line); the
+// CTA whose first group is ky = -ny/2 also needs the line (kx, +ny/2), which
+// it transforms and evaluates first in the same buffer.  The FFTs run in
+// place in padded buffers (see block_fft_ip), NT threads holding 16 values
+// each, so Lt * LPC and nz * LPC are at most 16 NT.
+template <int W, int D, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, const __grid_constant__ TapPoly P, int LPC,
+                                                                   const float2* __restrict__ Ghat,
+                                                                   const float2* __restrict__ axy_tab,
+                                                                   const float* __restrict__ deconv_t,
+                                                                   const float2* __restrict__ tw,
+                                                                   float2* __restrict__ V) {
+    constexpr int PER = 16;
     extern __shared__ float4 smem4[];
-    float2* LA = reinterpret_cast<float2*>(smem4);   // [Lt]
-    float2* LB = LA + G.Lt;                          // [Lt]
-    float2* T = LB + G.Lt;                           // [nz + 1] values at l = -nz/2..nz/2
-    float2* UA = T + (G.nz + 1);                     // [nz]
-    float2* UB = UA + G.nz;                          // [nz]
+    const int nz1 = G.nz + 1;
+    float2* LA = reinterpret_cast<float2*>(smem4);                 // [Lt][LPC], padded
+    float2* T = LA + padded_len(G.Lt * LPC);                       // [LPC + 1][nz + 1] values at l = -nz/2..nz/2
+    float2* UA = T + (size_t)(LPC + 1) * nz1;                      // [nz][LPC], padded
 
-    const int grp = blockIdx.x;
-    const int kx = grp >> ilog2(G.ny);
-    const int ky = (grp & (G.ny - 1)) - G.ny / 2;    // -ny/2..ny/2-1
-    const int kyb = (ky == -G.ny / 2) ? G.ny / 2 : ky;
+    const int llpc = ilog2(LPC), lnz = ilog2(G.nz);
+    const int cpk = G.ny >> llpc;                    // CTAs per kx
+    const int kx = blockIdx.x / cpk;
+    const int k0 = (blockIdx.x - kx * cpk) * LPC - G.ny / 2;
     const bool nyq_x = (kx == G.nx / 2);
-    const float ca = nyq_x ? 0.f : 0.5f;
-    const float cb = nyq_x ? 1.f : 0.5f;
     const int half_nz = G.nz / 2;
+    const size_t line0 = (size_t)kx * G.nyp + (k0 + G.ny / 2);
 
-    for (int i = threadIdx.x; i < G.nz; i += blockDim.x) UA[i] = make_float2(0.f, 0.f);
-
-    // lines to evaluate: a = (kx, ky) unless its coefficient is zero, b = (kx, kyb)
-    const int nlines = (nyq_x || ky == kyb) ? 1 : 2;
-    for (int li = 0; li < nlines; ++li) {
-        const int lky = (li == 0 && nlines == 2) ? ky : kyb;
-        const size_t line = (size_t)kx * G.nyp + (lky + G.ny / 2);
-        const float2 axy = __ldg(&axy_tab[line]);
-        const bool is_a = !nyq_x && (lky == ky);
-        const bool is_b = (lky == kyb);
-
-        // centred, deconvolved, zero-padded line
-        __syncthreads();
-        for (int p = threadIdx.x; p < G.Lt; p += blockDim.x) LA[p] = make_float2(0.f, 0.f);
-        __syncthreads();
-        const float2* src = Ghat + line * G.Nt;
+    if (k0 == -G.ny / 2) {
+        // the line (kx, +ny/2): centred, deconvolved, zero-padded, in column 0
+        const size_t lx = (size_t)kx * G.nyp + G.ny;
+        const float2* src = Ghat + lx * G.Nt;
 #pragma unroll 4
-        for (int n = threadIdx.x; n < G.Nt; n += blockDim.x)
-            LA[(n - G.Nt / 2) & (G.Lt - 1)] = cscale(src[n], __ldg(&deconv_t[n]));
-        float2* Bf = block_fft(LA, LB, G.Lt, 1, 1, -1, tw);
-
-        // NER values at l = -nz/2..nz/2
-        for (int e = threadIdx.x; e <= G.nz; e += blockDim.x) {
-            const int l = e - half_nz;
-            float2 val = make_float2(0.f, 0.f);
-            FF nu = nu_abs(G, axy, l);
-            float Wj;
-            if (l == 0) {
-                Wj = (kx == 0 && lky == 0) ? 2.f : 0.f;
-                nu = {0.f, 0.f};
-            } else {
-                Wj = 2.f * G.sqrt_az * (float)abs(l) / nu.hi;
-                if (l < 0) nu = {-nu.hi, -nu.lo};
-            }
-            float cl = G.apply_weights ? Wj * G.scale : G.scale;
-            if (G.band_mask) {
-                const double nd = (double)nu.hi + (double)nu.lo;
-                if (!(nd >= -0.5 * G.Nt - 1e-9 && nd < 0.5 * G.Nt - 1e-9)) cl = 0.f;
-            }
-            if (cl != 0.f) {
-                // v = sigma nu (sigma = 2): exact scaling of the pair
-                const float vh = 2.f * nu.hi, vl = 2.f * nu.lo;
-                float fl = floorf(vh);
-                float t = (vh - fl) + vl;
-                if (t < 0.f) { t += 1.f; fl -= 1.f; }
-                if (t >= 1.f) { t -= 1.f; fl += 1.f; }
-                const int ifl = (int)fl;
-                const int mu0 = ifl - W / 2 + 1;
-                const float2 acc = ner_gather<W, D>(P, Bf, mu0, 2.f * t - 1.f, G.Lt);
-                // exp(-i pi nu) = exp(-i pi v/2) = (-i)^floor(v) exp(-i pi t / 2)
-                float sn, cs;
-                sincospif(0.5f * t, &sn, &cs);
-                float2 ph = make_float2(cs, -sn);
-                const int q = ifl & 3;
-                if (q == 1) ph = make_float2(ph.y, -ph.x);
-                else if (q == 2) ph = make_float2(-ph.x, -ph.y);
-                else if (q == 3) ph = make_float2(-ph.y, ph.x);
-                val = cscale(cmul(ph, acc), cl);
-            }
-            T[e] = val;
+        for (int p = threadIdx.x; p < G.Lt; p += NT) {
+            const int n = (p + G.Nt / 2) & (G.Lt - 1);
+            LA[padx(p)] = (n < G.Nt) ? cscale(src[n], __ldg(&deconv_t[n])) : make_float2(0.f, 0.f);
         }
+        block_fft_ip<PER>(LA, G.Lt, 1, -1, tw);
+        const float2 axy = __ldg(&axy_tab[lx]);
+        for (int e = threadIdx.x; e < nz1; e += NT)
+            T[LPC * nz1 + e] = ner_value<W, D>(G, P, axy, false, e - half_nz, LA, 0, 0);
         __syncthreads();
-        // fold into U (slot l mod nz, l = -nz/2..nz/2-1)
-        for (int l0 = threadIdx.x; l0 < G.nz; l0 += blockDim.x) {
-            const int l = l0 - half_nz;
-            float2 u = UA[l & (G.nz - 1)];
-            if (is_a) u = cadd(u, cscale(T[l0], ca));
-            if (is_b) {
-                const int estar = (l == -half_nz) ? G.nz : l0;    // l* = +nz/2 for l = -nz/2
-                u = cadd(u, cscale(T[estar], cb));
-            }
-            UA[l & (G.nz - 1)] = u;
+    }
+    // the LPC lines (theta = 2 pi n/N - pi of Sec. 3.1): centred, deconvolved, zero-padded
+    {
+        const float2* src = Ghat + line0 * G.Nt;
+#pragma unroll 4
+        for (int i = threadIdx.x; i < (G.Lt << llpc); i += NT) {
+            const int p = i >> llpc, c = i & (LPC - 1);
+            const int n = (p + G.Nt / 2) & (G.Lt - 1);
+            LA[padx(i)] = (n < G.Nt) ? cscale(src[(size_t)c * G.Nt + n], __ldg(&deconv_t[n])) : make_float2(0.f, 0.f);
         }
     }
+    block_fft_ip<PER>(LA, G.Lt, LPC, -1, tw);
 
-    float2* Uz = block_fft(UA, UB, G.nz, 1, 1, +1, tw);
-    const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
-    float2* dst = V + ((size_t)kx * G.ny + (ky & (G.ny - 1))) * G.nz;
-    for (int q = threadIdx.x; q < G.nz; q += blockDim.x) dst[q] = cscale(Uz[q], sg);
+    // NER values of the LPC lines at l = -nz/2..nz/2
+    for (int i = threadIdx.x; i < (G.nz << llpc) + LPC; i += NT) {
+        int c, e;
+        if (i < (G.nz << llpc)) { c = i >> lnz; e = i & (G.nz - 1); }
+        else { c = i - (G.nz << llpc); e = G.nz; }
+        const float2 axy = __ldg(&axy_tab[line0 + c]);
+        T[c * nz1 + e] = ner_value<W, D>(G, P, axy, kx == 0 && k0 + c == 0, e - half_nz, LA, llpc, c);
+    }
+    __syncthreads();
+
+    // real part over the half lattice (see the comment above FF):
+    //   kx < nx/2 : U[l] = (F(kx, ky, l) + F(kx, ky*, l*)) / 2,   kx = nx/2 : U[l] = F(kx, ky*, l*)
+    const float ca = nyq_x ? 0.f : 0.5f;
+    const float cb = nyq_x ? 1.f : 0.5f;
+    for (int i = threadIdx.x; i < (G.nz << llpc); i += NT) {
+        const int c = i >> lnz, l0 = i & (G.nz - 1);
+        const int l = l0 - half_nz;
+        const int ky = k0 + c;
+        const int bcol = (ky == -G.ny / 2) ? LPC : c;
+        const int estar = (l == -half_nz) ? G.nz : l0;      // l* = +nz/2 for l = -nz/2
+        float2 u = cscale(T[bcol * nz1 + estar], cb);
+        if (!nyq_x) u = cadd(u, cscale(T[c * nz1 + l0], ca));
+        UA[padx(((l & (G.nz - 1)) << llpc) + c)] = u;
+    }
+    block_fft_ip<PER>(UA, G.nz, LPC, +1, tw);
+    for (int i = threadIdx.x; i < (G.nz << llpc); i += NT) {
+        const int c = i >> lnz, q = i & (G.nz - 1);
+        const int ky = k0 + c;
+        const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
+        V[((size_t)kx * G.ny + (ky & (G.ny - 1))) * G.nz + q] = cscale(UA[padx((q << llpc) + c)], sg);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -455,8 +481,9 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     NEDNER_ATTR_SPREAD(8) NEDNER_ATTR_SPREAD(12) NEDNER_ATTR_SPREAD(16) NEDNER_ATTR_SPREAD(20)
 #undef NEDNER_ATTR_SPREAD
     if ((e = cudaFuncSetAttribute(k_ned_yfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2))) return e;
-#define NEDNER_ATTR_NER(W, D) \
-    if ((e = cudaFuncSetAttribute(k_ner_lines<W, D>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e;
+#define NEDNER_ATTR_NER(W, D)                                                                                   \
+    if ((e = cudaFuncSetAttribute(k_ner_lines<W, D, 256>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ner_lines<W, D, 512>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e;
     NEDNER_ATTR_NER(4, 10) NEDNER_ATTR_NER(6, 10) NEDNER_ATTR_NER(8, 10) NEDNER_ATTR_NER(10, 10)
     NEDNER_ATTR_NER(12, 10) NEDNER_ATTR_NER(14, 12) NEDNER_ATTR_NER(16, 12)
 #undef NEDNER_ATTR_NER
@@ -494,8 +521,14 @@ cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Gha
 
 cudaError_t launch_ner_lines(const nedner_plan_s& p, const float2* Ghat, float2* V, cudaStream_t s) {
     const Geo& G = p.geo;
-    dim3 grid(G.nxh * G.ny);
-#define NEDNER_NER(W, D) k_ner_lines<W, D><<<grid, 256, p.ch.smem3, s>>>(G, p.tap, Ghat, p.t.axy, p.t.deconv_t, p.t.tw, V)
+    dim3 grid(G.nxh * (G.ny / p.ch.lpc));
+#define NEDNER_NER(W, D)                                                                                      \
+    if (p.ch.threads3 <= 256)                                                                                 \
+        k_ner_lines<W, D, 256><<<grid, 256, p.ch.smem3, s>>>(G, p.tap, p.ch.lpc, Ghat, p.t.axy, p.t.deconv_t, \
+                                                             p.t.tw, V);                                      \
+    else                                                                                                      \
+        k_ner_lines<W, D, 512><<<grid, 512, p.ch.smem3, s>>>(G, p.tap, p.ch.lpc, Ghat, p.t.axy, p.t.deconv_t, \
+                                                             p.t.tw, V)
     switch (G.w) {
         case 4: NEDNER_NER(4, 10); break;
         case 6: NEDNER_NER(6, 10); break;

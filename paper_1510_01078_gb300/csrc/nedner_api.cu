@@ -406,6 +406,9 @@ nedner_status build_static_tables(nedner_plan_s& p, cudaStream_t s) {
     return e ? NEDNER_ECUDA : NEDNER_OK;
 }
 
+// length of a padded FFT buffer (one spare slot after every 16 values)
+long padded(long n) { return n + (n >> 4); }
+
 int pow2_floor(long v) {
     int r = 1;
     while ((long)r * 2 <= v) r *= 2;
@@ -435,8 +438,15 @@ void choose_chunks(nedner_plan_s& p) {
     c.c2 = std::min<long>(16, std::max<long>(1, pow2_floor(budget / (16L * G.Ly))));
     c.c2 = std::min(c.c2, G.Nt);
     c.smem2 = (size_t)G.Ly * c.c2 * 16;
-    c.smem3 = (size_t)(2 * G.Lt + (G.nz + 1) + 2 * G.nz) * 8;
-    c.smem3a = c.smem3;
+    // NER: lines per CTA such that the batched line FFT has Lt * lpc = 4096 points
+    // (16 per thread of 256; 512 threads for Lt = 8192), within nz * lpc <= 4096
+    c.threads3 = G.Lt > 4096 ? 512 : 256;
+    c.lpc = 1;
+    while (c.lpc * 2 <= G.ny && (long)G.Lt * c.lpc * 2 <= 16L * c.threads3 &&
+           (long)G.nz * c.lpc * 2 <= 16L * c.threads3)
+        c.lpc *= 2;
+    c.smem3 = (size_t)(padded(G.Lt * c.lpc) + (c.lpc + 1) * (G.nz + 1) + padded(G.nz * c.lpc)) * 8;
+    c.smem3a = (size_t)(2 * G.Lt + (G.nz + 1) + 2 * G.nz) * 8;
     c.c4 = 1;
     while (c.c4 * 2 <= 16 && c.c4 * 2 <= G.nz && 2L * G.ny * (c.c4 * 2 + 1) * 8 <= 96 * 1024) c.c4 *= 2;
     c.smem4 = (size_t)2 * G.ny * (c.c4 + 1) * 8;
@@ -671,6 +681,19 @@ nedner_status nedner_grad_positions(nedner_plan_t p, const float* g, const float
     float2* Q = (float2*)((char*)p->ws + p->region_a);
     if ((e = launch_ned_grad(*p, A, g, Q, s))) return run(e);
     return run(launch_grad_finish(*p, Q, dL_dxy, s));
+}
+
+nedner_status nedner_device_status(nedner_plan_t p, int* flags) {
+    if (!p || !flags) return NEDNER_EINVAL;
+    *flags = 0;
+    if (!p->tp.err) return NEDNER_OK;
+    if (cudaSetDevice(p->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return NEDNER_ECUDA;
+    int f = 0;
+    const int zero = 0;
+    if (cudaMemcpy(&f, p->tp.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NEDNER_ECUDA;
+    if (cudaMemcpy(p->tp.err, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return NEDNER_ECUDA;
+    *flags = f ? 1 : 0;
+    return NEDNER_OK;
 }
 
 size_t nedner_workspace_bytes(nedner_plan_t p) { return p ? p->ws_bytes : 0; }

@@ -61,6 +61,7 @@ SIGNATURES = {
     "nedner_forward_profiled": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
     "nedner_ned_stage_static": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "nedner_device_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "nedner_destroy": (ctypes.c_int, [_P]),
     "nedner_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -148,6 +149,12 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def device_status(self) -> int:
+        """Flags of kernels whose bounded waits ran out since the last call (0 = none); synchronous."""
+        f = ctypes.c_int(0)
+        _check(_load().nedner_device_status(self._handle, ctypes.byref(f)), "nedner_device_status")
+        return int(f.value)
 
     @property
     def workspace_bytes(self) -> int:
