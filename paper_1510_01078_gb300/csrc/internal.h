@@ -27,16 +27,18 @@ struct Geo {
 // Work-split choices made once per plan.
 struct Chunks {
     int c1;   // time samples per CTA in the spread + x-FFT stage
-    int c2;   // time samples per CTA in the y-FFT stage
+    int c2;   // time samples per CTA in the transposed y-FFT stage
+    int c2f;  // time samples per CTA in the y-FFT stage
     int c4;   // depth planes per CTA in the y-IFFT stage
     int c5;   // image rows per CTA in the x-c2r stage
     int groups1;   // lane groups (column segments) per CTA in the spread stage
     int threads1;  // threads per CTA in the spread stage
+    int per1;      // values per thread in the spread stage's in-place x-FFT (16 or 32)
     int ca;        // time samples per CTA in the transposed interpolation stage
     int smax;      // sensors per task in the transposed interpolation stage
     int lpc;       // line groups per CTA in the NER stage
     int threads3;  // threads per CTA in the NER stage
-    size_t smem1, smem2, smem3, smem4, smem5;
+    size_t smem1, smem2, smem2f, smem3, smem4, smem5;
     size_t smem_interp, smem_grad, smem3a;
 };
 

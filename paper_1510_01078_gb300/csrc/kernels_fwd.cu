@@ -15,11 +15,22 @@
 
 namespace nedner {
 
+// asynchronous global -> shared copies (cp.async), completed per thread by
+// cp.async.wait_group; both addresses aligned to the copy size
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Stage (a), part 1: NED spreading (Eq. NED_NUFFT) fused with the x-FFT.
-// One CTA owns grid row gy and C consecutive time samples.  Its threads form
-// lane groups of C (lane = time sample); group q owns the column segment
-// seg[gy][q] = [c0, c1) of the shared-memory row [Lx][C].  The row's entries
+// One CTA of 256 threads owns grid row gy and C consecutive time samples.
+// Its threads form lane groups of C (lane = time sample); group q owns the
+// column segment seg[gy][q] = [c0, c1) of the row.  The row's entries
 // (sensor, y tap) are sorted by their first x column; each entry's w taps
 // (already multiplied by the y tap and the sensor factor) are stored as WT
 // values starting at a column bx4 that is a multiple of 4 (leading zeros
@@ -30,17 +41,19 @@ namespace nedner {
 // added at offset d = bx4 - base, a multiple of 4 in [0, WT], with WT FMAs
 // (a branch on d with WT/4 + 1 cases, uniform across the group).  No atomics,
 // no shared-memory read-modify-write; every column is written exactly once.
-// Entries are staged sixteen at a time (indices, taps, samples of g loaded
-// together) and then swept.
-// The row is then transformed along x (two real columns packed into one
-// complex FFT) and jx = 0..nx/2 is kept, divided by phihat(jx/Lx).
+// Entries are staged eight at a time (indices, taps, samples of g), the next
+// batch arriving by asynchronous copies while the current one is swept.
+// The row is held as C/2 complex columns (time samples 2b, 2b+1 packed as
+// real and imaginary part) in a padded buffer, transformed in place along x
+// (PER values per thread), and jx = 0..nx/2 is kept, divided by phihat(jx/Lx).
 // ---------------------------------------------------------------------------
 template <int WT>
-__device__ __forceinline__ void flush_lower(float (&acc)[2 * WT], float* S, int C, int ln, int base, int c0, int c1) {
+__device__ __forceinline__ void flush_lower(float (&acc)[2 * WT], float* Zf, int lnb, int hl, int base, int c0,
+                                            int c1) {
 #pragma unroll
     for (int k = 0; k < WT; ++k) {
         const int col = base + k;
-        if (col >= c0 && col < c1) S[col * C + ln] = acc[k];
+        if (col >= c0 && col < c1) Zf[2 * padx((col << lnb) + (hl >> 1)) + (hl & 1)] = acc[k];
         acc[k] = acc[k + WT];
         acc[k + WT] = 0.f;
     }
@@ -59,10 +72,10 @@ __device__ __forceinline__ void add_taps(float (&acc)[2 * WT], const float4 (&wv
 
 // one entry: slide the window to bx4, then add its taps at d = bx4 - base
 template <int WT>
-__device__ __forceinline__ void sweep_entry(float (&acc)[2 * WT], float* S, int C, int ln, int& base, int c0,
+__device__ __forceinline__ void sweep_entry(float (&acc)[2 * WT], float* Zf, int lnb, int hl, int& base, int c0,
                                             int c1, int bx4, const float4 (&wv)[WT / 4], float gval) {
     while (bx4 - base > WT) {
-        flush_lower<WT>(acc, S, C, ln, base, c0, c1);
+        flush_lower<WT>(acc, Zf, lnb, hl, base, c0, c1);
         base += WT;
     }
     const int d = (bx4 - base) >> 2;
@@ -74,22 +87,28 @@ __device__ __forceinline__ void sweep_entry(float (&acc)[2 * WT], float* S, int 
     else if (WT >= 20 && d == 5) add_taps<WT, (WT >= 20 ? 20 : 0)>(acc, wv, gval);
 }
 
-template <int WT, int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ned_spread_xfft(Geo G, int C, const float* __restrict__ g,
-                                                         const int4* __restrict__ seg,
-                                                         const int* __restrict__ xent_m,
-                                                         const float* __restrict__ xent_wx,
-                                                         const int* __restrict__ xent_bx,
-                                                         const float* __restrict__ deconv_x,
-                                                         const float2* __restrict__ tw, float2* __restrict__ R) {
+template <int WT, int PER>
+__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_spread_xfft(Geo G, int C, const float* __restrict__ g,
+                                                                          const int4* __restrict__ seg,
+                                                                          const int* __restrict__ xent_m,
+                                                                          const float* __restrict__ xent_wx,
+                                                                          const int* __restrict__ xent_bx,
+                                                                          const float* __restrict__ deconv_x,
+                                                                          const float2* __restrict__ tw,
+                                                                          float2* __restrict__ R) {
+    constexpr int NT = 256;
+    constexpr int B = 8;                                           // entries per staged batch
     extern __shared__ float4 smem4[];
-    float* S = reinterpret_cast<float*>(smem4);                  // [Lx][C] real row
-    float2* B2 = reinterpret_cast<float2*>(S + (size_t)G.Lx * C);  // [Lx][C/2] scratch
+    const int Lx = G.Lx;
+    const int nb = C / 2;
+    const int lnb = ilog2(nb);
+    float2* Z = reinterpret_cast<float2*>(smem4);                  // [Lx][C/2] complex row, padded
+    float* Zf = reinterpret_cast<float*>(Z);
+    const int zlen = (padded_len(Lx * nb) + 1) & ~1;
     const int gy = blockIdx.x;
     const int n0 = blockIdx.y * C;
-    const int Lx = G.Lx;
     const int lc = ilog2(C);
-    const int groups = blockDim.x >> lc;
+    const int groups = NT >> lc;
     const int q = threadIdx.x >> lc;
     const int ln = threadIdx.x & (C - 1);
 
@@ -99,71 +118,78 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ned_spread_xfft(Geo G
     for (int k = 0; k < 2 * WT; ++k) acc[k] = 0.f;
     int base = (sg.x - WT) & ~3;
 
-    // per-group staging area for one batch, carved out of the FFT scratch
-    // (unused until the sweep is over): bx4[B], taps[B][WT], g[B][C]
-    constexpr int B = 16;
-    const int lane = threadIdx.x & 31;
-    const int gbase = lane - ln;
-    const unsigned gmask = (C == 32) ? 0xffffffffu : (((1u << C) - 1u) << gbase);
-    int* st_bx = reinterpret_cast<int*>(B2) + (size_t)q * (B + B * WT + B * C);
-    float* st_w = reinterpret_cast<float*>(st_bx + B);
-    float* st_g = st_w + B * WT;
-
-    for (int e0 = sg.z; e0 < sg.w; e0 += B) {
-        const int nbat = min(B, sg.w - e0);
-        const int m_l = (ln < nbat) ? __ldg(&xent_m[e0 + ln]) : 0;    // entries 0..C-1 of the batch
-        for (int j = ln; j < nbat; j += C) st_bx[j] = __ldg(&xent_bx[e0 + j]);
-        const float4* wsrc = reinterpret_cast<const float4*>(xent_wx + (size_t)e0 * WT);
-        float4* wdst = reinterpret_cast<float4*>(st_w);
-        for (int i = ln; i < nbat * (WT / 4); i += C) wdst[i] = __ldg(&wsrc[i]);
-        float gl[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            const int mj = __shfl_sync(gmask, m_l, gbase + (j & (C - 1)));
-            gl[j] = (j < nbat && j < C) ? __ldg(&g[(size_t)mj * G.Nt + n0 + ln]) : 0.f;
+    // Per-group staging, double-buffered: the entries' sensor indices one batch
+    // ahead, and bx4[B], taps[B][WT], g[B][C] of the next batch, arrive by
+    // cp.async while the current batch is swept.
+    const unsigned gmask = (C >= 32) ? 0xffffffffu : (((1u << C) - 1u) << ((threadIdx.x & 31) - ln));
+    constexpr int DB = B + B * WT;                                 // ints + floats before the g block
+    const int dsz = DB + B * C;                                    // one data buffer (4-byte words)
+    int* st_m = reinterpret_cast<int*>(Z + zlen) + (size_t)q * (2 * B + 2 * dsz);   // [2][B]
+    int* st_d = st_m + 2 * B;                                      // [2][dsz]
+    const int nent = sg.w - sg.z;
+    const int nbt = (nent + B - 1) / B;
+    const int cw = C >= 4 ? 4 : C;                                 // floats per copy of g
+    auto issue_m = [&](int b) {
+        const int e0 = sg.z + b * B, nb_ = min(B, sg.w - e0);
+        for (int j = ln; j < nb_; j += C) cp_async(st_m + (b & 1) * B + j, xent_m + e0 + j, 4);
+    };
+    auto issue_data = [&](int b) {
+        const int e0 = sg.z + b * B, nb_ = min(B, sg.w - e0);
+        int* d = st_d + (b & 1) * dsz;
+        const int* mm = st_m + (b & 1) * B;
+        for (int j = ln; j < nb_; j += C) cp_async(d + j, xent_bx + e0 + j, 4);
+        const float* wsrc = xent_wx + (size_t)e0 * WT;
+        for (int i = ln; i < nb_ * (WT / 4); i += C) cp_async(d + B + 4 * i, wsrc + 4 * i, 16);
+        const int per = C / cw;                                    // copies per entry
+        for (int i = ln; i < nb_ * per; i += C) {
+            const int j = i / per, c = i - j * per;
+            cp_async(d + DB + j * C + c * cw, g + (size_t)mm[j] * G.Nt + n0 + c * cw, cw * 4);
         }
-        if (C < B) {
-            // batches larger than the group: indices of entries C.. come in further rounds
-            for (int j0 = C; j0 < nbat; j0 += C) {
-                const int m2 = (ln + j0 < nbat) ? __ldg(&xent_m[e0 + j0 + ln]) : 0;
-#pragma unroll
-                for (int j = 0; j < B; ++j) {
-                    if (j >= j0 && j < j0 + C) {
-                        const int mj = __shfl_sync(gmask, m2, gbase + (j - j0));
-                        if (j < nbat) gl[j] = __ldg(&g[(size_t)mj * G.Nt + n0 + ln]);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < B; ++j) st_g[j * C + ln] = gl[j];
+    };
+    if (nbt > 0) {
+        issue_m(0);
+        cp_async_commit();
+        cp_async_wait_all();
         __syncwarp(gmask);
+        issue_data(0);
+        if (nbt > 1) issue_m(1);
+        cp_async_commit();
+    }
+    for (int b = 0; b < nbt; ++b) {
+        cp_async_wait_all();
+        __syncwarp(gmask);
+        if (b + 1 < nbt) issue_data(b + 1);
+        if (b + 2 < nbt) issue_m(b + 2);
+        cp_async_commit();
+        const int nbat = min(B, nent - b * B);
+        const int* st_bx = st_d + (b & 1) * dsz;
+        const float4* wst = reinterpret_cast<const float4*>(st_bx + B);
+        const float* st_g = reinterpret_cast<const float*>(st_bx + DB);
 #pragma unroll 1
         for (int j = 0; j < nbat; ++j) {
             const int bxa = st_bx[j];
             const float ga = st_g[j * C + ln];
             float4 wa[WT / 4];
 #pragma unroll
-            for (int k4 = 0; k4 < WT / 4; ++k4) wa[k4] = wdst[j * (WT / 4) + k4];
-            sweep_entry<WT>(acc, S, C, ln, base, sg.x, sg.y, bxa, wa, ga);
+            for (int k4 = 0; k4 < WT / 4; ++k4) wa[k4] = wst[j * (WT / 4) + k4];
+            sweep_entry<WT>(acc, Zf, lnb, ln, base, sg.x, sg.y, bxa, wa, ga);
         }
         __syncwarp(gmask);
     }
     while (base < sg.y) {
-        flush_lower<WT>(acc, S, C, ln, base, sg.x, sg.y);
+        flush_lower<WT>(acc, Zf, lnb, ln, base, sg.x, sg.y);
         base += WT;
     }
 
-    const int nb = C / 2;
-    float2* res = block_fft(reinterpret_cast<float2*>(S), B2, Lx, nb, nb, -1, tw);
+    block_fft_ip<PER>(Z, Lx, nb, -1, tw);
 
     const int items = G.nxh * C;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    for (int it = threadIdx.x; it < items; it += NT) {
         const int jx = it >> lc;
         const int c = it & (C - 1);
         const int b = c >> 1;
-        const float2 zk = res[jx * nb + b];
-        const float2 zm = cconj(res[((Lx - jx) & (Lx - 1)) * nb + b]);
+        const float2 zk = Z[padx((jx << lnb) + b)];
+        const float2 zm = cconj(Z[padx((((Lx - jx) & (Lx - 1)) << lnb) + b)]);
         // column 2b = (Z[k] + conj Z[-k]) / 2, column 2b+1 = -i (Z[k] - conj Z[-k]) / 2
         float2 x = (c & 1) ? mul_i(csub(zk, zm), -1) : cadd(zk, zm);
         x = cscale(x, 0.5f * __ldg(&deconv_x[jx]));
@@ -173,30 +199,30 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ned_spread_xfft(Geo G
 
 // ---------------------------------------------------------------------------
 // Stage (a), part 2: y-FFT of length Ly for one jx and C time samples; keeps
-// jy = -ny/2..ny/2 (both Nyquist rows) divided by phihat(jy/Ly).
+// jy = -ny/2..ny/2 (both Nyquist rows) divided by phihat(jy/Ly).  The FFT
+// runs in place in a padded buffer, Ly * C <= 4096 (16 values per thread).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ned_yfft(Geo G, int C, const float2* __restrict__ R,
-                                                  const float* __restrict__ deconv_y,
-                                                  const float2* __restrict__ tw, float2* __restrict__ Ghat) {
+__global__ void __launch_bounds__(256, 3) k_ned_yfft(Geo G, int C, const float2* __restrict__ R,
+                                                     const float* __restrict__ deconv_y,
+                                                     const float2* __restrict__ tw, float2* __restrict__ Ghat) {
     extern __shared__ float4 smem4[];
-    float2* A = reinterpret_cast<float2*>(smem4);
-    float2* B = A + (size_t)G.Ly * C;
+    float2* A = reinterpret_cast<float2*>(smem4);   // [Ly][C], padded
     const int jx = blockIdx.x;
     const int n0 = blockIdx.y * C;
     const int lc = ilog2(C);
 #pragma unroll 8
-    for (int it = threadIdx.x; it < G.Ly * C; it += blockDim.x) {
+    for (int it = threadIdx.x; it < G.Ly * C; it += 256) {
         const int gy = it >> lc;
         const int c = it & (C - 1);
-        A[it] = R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c];
+        A[padx(it)] = R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c];
     }
-    float2* res = block_fft(A, B, G.Ly, C, C, -1, tw);
+    block_fft_ip<16>(A, G.Ly, C, -1, tw);
     const int items = G.nyp * C;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    for (int it = threadIdx.x; it < items; it += 256) {
         const int b = it >> lc;                // jy = b - ny/2
         const int c = it & (C - 1);
         const int q = (b - G.ny / 2 + G.Ly) & (G.Ly - 1);
-        Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c] = cscale(res[q * C + c], __ldg(&deconv_y[b]));
+        Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c] = cscale(A[padx(q * C + c)], __ldg(&deconv_y[b]));
     }
 }
 
@@ -476,11 +502,11 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     cudaError_t e;
     const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
 #define NEDNER_ATTR_SPREAD(WT)                                                                              \
-    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 256>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e; \
-    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 512>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 16>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 32>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
     NEDNER_ATTR_SPREAD(8) NEDNER_ATTR_SPREAD(12) NEDNER_ATTR_SPREAD(16) NEDNER_ATTR_SPREAD(20)
 #undef NEDNER_ATTR_SPREAD
-    if ((e = cudaFuncSetAttribute(k_ned_yfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_yfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2f))) return e;
 #define NEDNER_ATTR_NER(W, D)                                                                                   \
     if ((e = cudaFuncSetAttribute(k_ner_lines<W, D, 256>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e; \
     if ((e = cudaFuncSetAttribute(k_ner_lines<W, D, 512>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e;
@@ -495,13 +521,13 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
 cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float2* R, cudaStream_t s) {
     const Geo& G = p.geo;
     dim3 grid(G.Ly, G.Nt / p.ch.c1);
-#define NEDNER_SPREAD(WT)                                                                                    \
-    if (p.ch.threads1 <= 256)                                                                                \
-        k_ned_spread_xfft<WT, 256><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
-                                                                 p.t.xent_bx, p.t.deconv_x, p.t.tw, R);      \
-    else                                                                                                     \
-        k_ned_spread_xfft<WT, 512><<<grid, 512, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
-                                                                 p.t.xent_bx, p.t.deconv_x, p.t.tw, R)
+#define NEDNER_SPREAD(WT)                                                                                   \
+    if (p.ch.per1 <= 16)                                                                                    \
+        k_ned_spread_xfft<WT, 16><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
+                                                                p.t.xent_bx, p.t.deconv_x, p.t.tw, R);      \
+    else                                                                                                    \
+        k_ned_spread_xfft<WT, 32><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
+                                                                p.t.xent_bx, p.t.deconv_x, p.t.tw, R)
     switch (spread_taps(G.w)) {
         case 8: NEDNER_SPREAD(8); break;
         case 12: NEDNER_SPREAD(12); break;
@@ -514,8 +540,8 @@ cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float
 
 cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s) {
     const Geo& G = p.geo;
-    dim3 grid(G.nxh, G.Nt / p.ch.c2);
-    k_ned_yfft<<<grid, 256, p.ch.smem2, s>>>(G, p.ch.c2, R, p.t.deconv_y, p.t.tw, Ghat);
+    dim3 grid(G.nxh, G.Nt / p.ch.c2f);
+    k_ned_yfft<<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, R, p.t.deconv_y, p.t.tw, Ghat);
     return cudaGetLastError();
 }
 

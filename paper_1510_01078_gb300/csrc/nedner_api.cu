@@ -423,13 +423,15 @@ void choose_chunks(nedner_plan_s& p) {
     // row fits in 128 KB of shared memory, smaller groups beyond
     c.c1 = std::min<long>(32, std::max<long>(2, pow2_floor((128L * 1024) / (8L * G.Lx))));
     c.c1 = std::min(c.c1, G.Nt);
-    c.threads1 = G.Lx >= 512 ? 512 : 256;
+    c.threads1 = 256;
     c.groups1 = c.threads1 / c.c1;
-    c.smem1 = (size_t)G.Lx * c.c1 * 8;                 // real row + complex scratch
     {
-        // the spread's batch staging (16 entries per lane group) lives in the scratch half
-        const size_t staging = (size_t)c.groups1 * 16 * (1 + spread_taps(G.w) + c.c1) * 4;
-        c.smem1 = std::max(c.smem1, (size_t)G.Lx * c.c1 * 4 + staging);
+        // complex row [Lx][c1/2], padded and rounded to 16 bytes, then the
+        // sweep's double-buffered batch staging (8 entries per lane group)
+        const long zlen = (padded((long)G.Lx * c.c1 / 2) + 1) & ~1L;
+        const size_t staging = (size_t)c.groups1 * (2 * 8 + 2 * 8 * (1 + spread_taps(G.w) + c.c1)) * 4;
+        c.smem1 = (size_t)zlen * 8 + staging;
+        c.per1 = (long)G.Lx * c.c1 / 2 <= 16L * c.threads1 ? 16 : 32;
     }
     c.ca = c.c1;
     c.smax = (int)std::max<long>(32, budget / (4L * c.ca));
@@ -438,6 +440,8 @@ void choose_chunks(nedner_plan_s& p) {
     c.c2 = std::min<long>(16, std::max<long>(1, pow2_floor(budget / (16L * G.Ly))));
     c.c2 = std::min(c.c2, G.Nt);
     c.smem2 = (size_t)G.Ly * c.c2 * 16;
+    c.c2f = (int)std::min<long>(std::min<long>(16, G.Nt), std::max<long>(1, 4096 / G.Ly));
+    c.smem2f = (size_t)padded((long)G.Ly * c.c2f) * 8;
     // NER: lines per CTA such that the batched line FFT has Lt * lpc = 4096 points
     // (16 per thread of 256; 512 threads for Lt = 8192), within nz * lpc <= 4096
     c.threads3 = G.Lt > 4096 ? 512 : 256;
@@ -584,7 +588,7 @@ nedner_status nedner_set_positions(nedner_plan_t p, const double* sensor_xy) {
 
 nedner_status nedner_forward(nedner_plan_t p, const float* g, float* p0, void* stream) {
     if (!p || !p0 || (p->M > 0 && !g)) return NEDNER_EINVAL;
-    if (((uintptr_t)p0 & 7) != 0) return NEDNER_EINVAL;
+    if (((uintptr_t)p0 & 7) != 0 || ((uintptr_t)g & 15) != 0) return NEDNER_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     float2* A = (float2*)p->ws;
     float2* B = (float2*)((char*)p->ws + p->region_a);
@@ -603,7 +607,7 @@ nedner_status nedner_forward(nedner_plan_t p, const float* g, float* p0, void* s
 nedner_status nedner_forward_profiled(nedner_plan_t p, const float* g, float* p0, void* stream,
                                       float* stage_ms) {
     if (!p || !p0 || !stage_ms || (p->M > 0 && !g)) return NEDNER_EINVAL;
-    if (((uintptr_t)p0 & 7) != 0) return NEDNER_EINVAL;
+    if (((uintptr_t)p0 & 7) != 0 || ((uintptr_t)g & 15) != 0) return NEDNER_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     float2* A = (float2*)p->ws;
     float2* B = (float2*)((char*)p->ws + p->region_a);
@@ -636,6 +640,7 @@ nedner_status nedner_forward_profiled(nedner_plan_t p, const float* g, float* p0
 
 nedner_status nedner_ned_stage(nedner_plan_t p, const float* g, void* Ghat, void* stream) {
     if (!p || !Ghat || (p->M > 0 && !g)) return NEDNER_EINVAL;
+    if (((uintptr_t)g & 15) != 0) return NEDNER_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     float2* A = (float2*)p->ws;
     cudaError_t e;

@@ -46,6 +46,7 @@ cudaError_t scratch_address(void** out) {
 
 extern "C" nedner_status nedner_ned_stage_static(nedner_plan_t p, const float* g, void* Ghat, void* stream) {
     if (!p || !Ghat || (p->M > 0 && !g)) return NEDNER_EINVAL;
+    if (((uintptr_t)g & 15) != 0) return NEDNER_EINVAL;
     const nedner::Geo& G = p->geo;
     const size_t need = (size_t)G.nxh * G.Ly * G.Nt * sizeof(float2);
     if (need > (size_t)NEDNER_STATIC_SCRATCH_BYTES) return NEDNER_ENOMEM;
