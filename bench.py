@@ -126,17 +126,18 @@ def traffic_for(kernel: str):
         return None
 
 
-def oracle_forward_seconds(cfg, steps: int = 1):
+def oracle_forward_seconds(cfg, steps: int = 1, want_output: bool = False):
     import numpy as np
     import oracle
     pr = oracle.Problem(sensor_xy=cfg["sensor_xy"], h=cfg["h"], Nt=cfg["Nt"], dt=cfg["dt"], c=cfg["c"],
                         nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], dx=cfg["dx"], dy=cfg["dy"], dz=cfg["dz"])
     times = []
+    out = None
     for _ in range(steps):
         t0 = time.perf_counter()
-        oracle.forward(pr, np.asarray(cfg["g"], dtype=np.float64))
+        out = oracle.forward(pr, np.asarray(cfg["g"], dtype=np.float64))
         times.append(time.perf_counter() - t0)
-    return times
+    return (times, out) if want_output else times
 
 
 
@@ -286,13 +287,18 @@ def main():
                    if "ned_spread_xfft" in avg else None)
 
     cpu = None
+    accuracy = {"rel_l2_vs_oracle": None, "tolerance": 1e-5 if args.ned_mode == "nufft" else 3e-5}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             import oracle
             oracle.build()
-            secs = oracle_forward_seconds(cfg, 1)[0]
+            secs, ref = oracle_forward_seconds(cfg, 1, want_output=True)
+            secs = secs[0]
             cpu = {"value": voxels / secs, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "one full FP64 oracle reconstruction of the workload (%.1f s)" % secs}
+            # the accuracy the throughput is quoted at: the timed run's p0 against the oracle's
+            got = p0.double().cpu().numpy()
+            accuracy["rel_l2_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         except Exception as ex:  # the baseline is reported, not required
             cpu = {"value": None, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "failed: %s" % ex}
@@ -303,7 +309,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded balls + 20 dB noise)",
                 "config": {"workload": describe(cfg), "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": "independent reconstruction per GPU", "ned_mode": args.ned_mode},
-                "roofline": roofline, "spread_frac_of_peak": spread_frac, "kernels": kernels,
+                "roofline": roofline, "spread_frac_of_peak": spread_frac, "accuracy": accuracy, "kernels": kernels,
                 "cpu_baseline": cpu, "clocks": clk,
                 "e2e": {"value": voxels * world / (e2e_step / 1e3), "unit": "voxels/s",
                         "h2d_bytes_per_step": int(g_host.numel() * 4), "d2h_bytes_per_step": int(p_host.numel() * 4)},

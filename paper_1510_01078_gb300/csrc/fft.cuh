@@ -239,8 +239,28 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, int N, int Ns, int nb, 
             const int j = it >> lnb, b = it & (nb - 1);
             const int k = j & (Ns - 1);
             if (Ns > 1) {
+                if (R == 16 && nb < 4) {
+                    // few columns: neighbouring lanes need different twiddles, so
+                    // the 15 table loads would touch up to 15 x 32 distinct lines;
+                    // load w^k and w^4k (w = exp(DIR 2 pi i step / N)) and form
+                    // w^(r1 + 4 r2) = (w^k)^r1 (w^4k)^r2 with at most two products
+                    // per factor (a few units in the last place)
+                    const float2 a1 = twiddle(tw, k * step, N, DIR);
+                    const float2 b1 = twiddle(tw, 4 * k * step, N, DIR);
+                    const float2 a2 = cmul(a1, a1), a3 = cmul(a2, a1);
+                    const float2 b2 = cmul(b1, b1), b3 = cmul(b2, b1);
+                    const float2 wa[4] = {make_float2(1.f, 0.f), a1, a2, a3};
+                    const float2 wb[4] = {make_float2(1.f, 0.f), b1, b2, b3};
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], twiddle(tw, k * r * step, N, DIR));
+                    for (int r = 1; r < R; ++r) {
+                        const int r1 = r & 3, r2 = r >> 2;
+                        const float2 t = (r1 == 0) ? wb[r2] : (r2 == 0) ? wa[r1] : cmul(wa[r1], wb[r2]);
+                        v[i][r] = cmul(v[i][r], t);
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], twiddle(tw, k * r * step, N, DIR));
+                }
             }
             dft_reg<R, DIR>(v[i]);
             const int i0 = (j - k) * R + k;

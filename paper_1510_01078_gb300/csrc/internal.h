@@ -34,6 +34,7 @@ struct Chunks {
     int groups1;   // lane groups (column segments) per CTA in the spread stage
     int threads1;  // threads per CTA in the spread stage
     int per1;      // values per thread in the spread stage's in-place x-FFT (16 or 32)
+    int tpl1;      // time samples per lane in the spread stage (1 or 2)
     int ca;        // time samples per CTA in the transposed interpolation stage
     int smax;      // sensors per task in the transposed interpolation stage
     int lpc;       // line groups per CTA in the NER stage

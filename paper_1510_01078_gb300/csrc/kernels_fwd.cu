@@ -197,6 +197,149 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_spread_xfft(Geo 
     }
 }
 
+// Two time samples per lane (C = 64 per CTA, lane groups of a full warp): the
+// lane's samples 2 ln, 2 ln + 1 are exactly complex column ln of the row, so
+// the register window holds float2 pairs, every tap is applied to both with
+// one packed FMA, and a finished column is one 8-byte store.
+template <int WT>
+__device__ __forceinline__ void flush_lower2(float2 (&acc)[2 * WT], float2* Z, int ln, int base, int c0, int c1) {
+#pragma unroll
+    for (int k = 0; k < WT; ++k) {
+        const int col = base + k;
+        if (col >= c0 && col < c1) Z[padx((col << 5) + ln)] = acc[k];
+        acc[k] = acc[k + WT];
+        acc[k + WT] = make_float2(0.f, 0.f);
+    }
+}
+
+template <int WT, int D>
+__device__ __forceinline__ void add_taps2(float2 (&acc)[2 * WT], const float4 (&wv)[WT / 4], float2 g2) {
+#pragma unroll
+    for (int k4 = 0; k4 < WT / 4; ++k4) {
+        acc[D + 4 * k4 + 0] = __ffma2_rn(make_float2(wv[k4].x, wv[k4].x), g2, acc[D + 4 * k4 + 0]);
+        acc[D + 4 * k4 + 1] = __ffma2_rn(make_float2(wv[k4].y, wv[k4].y), g2, acc[D + 4 * k4 + 1]);
+        acc[D + 4 * k4 + 2] = __ffma2_rn(make_float2(wv[k4].z, wv[k4].z), g2, acc[D + 4 * k4 + 2]);
+        acc[D + 4 * k4 + 3] = __ffma2_rn(make_float2(wv[k4].w, wv[k4].w), g2, acc[D + 4 * k4 + 3]);
+    }
+}
+
+template <int WT>
+__device__ __forceinline__ void sweep_entry2(float2 (&acc)[2 * WT], float2* Z, int ln, int& base, int c0, int c1,
+                                             int bx4, const float4 (&wv)[WT / 4], float2 g2) {
+    while (bx4 - base > WT) {
+        flush_lower2<WT>(acc, Z, ln, base, c0, c1);
+        base += WT;
+    }
+    const int d = (bx4 - base) >> 2;
+    if (d == 0) add_taps2<WT, 0>(acc, wv, g2);
+    else if (d == 1) add_taps2<WT, 4>(acc, wv, g2);
+    else if (d == 2) add_taps2<WT, (WT >= 8 ? 8 : 0)>(acc, wv, g2);
+    else if (WT >= 12 && d == 3) add_taps2<WT, (WT >= 12 ? 12 : 0)>(acc, wv, g2);
+    else if (WT >= 16 && d == 4) add_taps2<WT, (WT >= 16 ? 16 : 0)>(acc, wv, g2);
+    else if (WT >= 20 && d == 5) add_taps2<WT, (WT >= 20 ? 20 : 0)>(acc, wv, g2);
+}
+
+template <int WT>
+__global__ void __launch_bounds__(256, 2) k_ned_spread2_xfft(Geo G, const float* __restrict__ g,
+                                                             const int4* __restrict__ seg,
+                                                             const int* __restrict__ xent_m,
+                                                             const float* __restrict__ xent_wx,
+                                                             const int* __restrict__ xent_bx,
+                                                             const float* __restrict__ deconv_x,
+                                                             const float2* __restrict__ tw,
+                                                             float2* __restrict__ R) {
+    constexpr int NT = 256, B = 8, C = 64, NB = 32;
+    extern __shared__ float4 smem4[];
+    const int Lx = G.Lx;
+    float2* Z = reinterpret_cast<float2*>(smem4);                  // [Lx][32] complex row, padded
+    const int zlen = (padded_len(Lx * NB) + 1) & ~1;
+    const int gy = blockIdx.x;
+    const int n0 = blockIdx.y * C;
+    const int q = threadIdx.x >> 5;                                // lane group = warp
+    const int ln = threadIdx.x & 31;
+
+    const int4 sg = seg[(size_t)gy * (NT / 32) + q];   // c0, c1, first entry, end entry
+    float2 acc[2 * WT];
+#pragma unroll
+    for (int k = 0; k < 2 * WT; ++k) acc[k] = make_float2(0.f, 0.f);
+    int base = (sg.x - WT) & ~3;
+
+    // double-buffered staging as in k_ned_spread_xfft: m[2][B], then per buffer
+    // bx4[B], taps[B][WT], g[B][C]
+    constexpr int DB = B + B * WT;
+    constexpr int dsz = DB + B * C;
+    int* st_m = reinterpret_cast<int*>(Z + zlen) + (size_t)q * (2 * B + 2 * dsz);
+    int* st_d = st_m + 2 * B;
+    const int nent = sg.w - sg.z;
+    const int nbt = (nent + B - 1) / B;
+    auto issue_m = [&](int b) {
+        const int e0 = sg.z + b * B, nb_ = min(B, sg.w - e0);
+        if (ln < nb_) cp_async(st_m + (b & 1) * B + ln, xent_m + e0 + ln, 4);
+    };
+    auto issue_data = [&](int b) {
+        const int e0 = sg.z + b * B, nb_ = min(B, sg.w - e0);
+        int* d = st_d + (b & 1) * dsz;
+        const int* mm = st_m + (b & 1) * B;
+        if (ln < nb_) cp_async(d + ln, xent_bx + e0 + ln, 4);
+        const float* wsrc = xent_wx + (size_t)e0 * WT;
+        for (int i = ln; i < nb_ * (WT / 4); i += 32) cp_async(d + B + 4 * i, wsrc + 4 * i, 16);
+#pragma unroll
+        for (int r = 0; r < B * (C / 4) / 32; ++r) {
+            const int i = ln + 32 * r;
+            const int j = i >> 4, c = i & 15;
+            if (j < nb_) cp_async(d + DB + j * C + 4 * c, g + (size_t)mm[j] * G.Nt + n0 + 4 * c, 16);
+        }
+    };
+    if (nbt > 0) {
+        issue_m(0);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+        issue_data(0);
+        if (nbt > 1) issue_m(1);
+        cp_async_commit();
+    }
+    for (int b = 0; b < nbt; ++b) {
+        cp_async_wait_all();
+        __syncwarp();
+        if (b + 1 < nbt) issue_data(b + 1);
+        if (b + 2 < nbt) issue_m(b + 2);
+        cp_async_commit();
+        const int nbat = min(B, nent - b * B);
+        const int* st_bx = st_d + (b & 1) * dsz;
+        const float4* wst = reinterpret_cast<const float4*>(st_bx + B);
+        const float2* st_g = reinterpret_cast<const float2*>(st_bx + DB);
+#pragma unroll 1
+        for (int j = 0; j < nbat; ++j) {
+            const int bxa = st_bx[j];
+            const float2 ga = st_g[j * NB + ln];
+            float4 wa[WT / 4];
+#pragma unroll
+            for (int k4 = 0; k4 < WT / 4; ++k4) wa[k4] = wst[j * (WT / 4) + k4];
+            sweep_entry2<WT>(acc, Z, ln, base, sg.x, sg.y, bxa, wa, ga);
+        }
+        __syncwarp();
+    }
+    while (base < sg.y) {
+        flush_lower2<WT>(acc, Z, ln, base, sg.x, sg.y);
+        base += WT;
+    }
+
+    block_fft_ip<32>(Z, Lx, NB, -1, tw);
+
+    const int items = G.nxh * C;
+    for (int it = threadIdx.x; it < items; it += NT) {
+        const int jx = it >> 6;
+        const int c = it & (C - 1);
+        const int b = c >> 1;
+        const float2 zk = Z[padx((jx << 5) + b)];
+        const float2 zm = cconj(Z[padx((((Lx - jx) & (Lx - 1)) << 5) + b)]);
+        float2 x = (c & 1) ? mul_i(csub(zk, zm), -1) : cadd(zk, zm);
+        x = cscale(x, 0.5f * __ldg(&deconv_x[jx]));
+        R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c] = x;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Stage (a), part 2: y-FFT of length Ly for one jx and C time samples; keeps
 // jy = -ny/2..ny/2 (both Nyquist rows) divided by phihat(jy/Ly).  The FFT
@@ -505,6 +648,10 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 16>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e; \
     if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 32>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
     NEDNER_ATTR_SPREAD(8) NEDNER_ATTR_SPREAD(12) NEDNER_ATTR_SPREAD(16) NEDNER_ATTR_SPREAD(20)
+    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<8>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<12>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<16>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<20>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
 #undef NEDNER_ATTR_SPREAD
     if ((e = cudaFuncSetAttribute(k_ned_yfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2f))) return e;
 #define NEDNER_ATTR_NER(W, D)                                                                                   \
@@ -522,7 +669,10 @@ cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float
     const Geo& G = p.geo;
     dim3 grid(G.Ly, G.Nt / p.ch.c1);
 #define NEDNER_SPREAD(WT)                                                                                   \
-    if (p.ch.per1 <= 16)                                                                                    \
+    if (p.ch.tpl1 == 2)                                                                                     \
+        k_ned_spread2_xfft<WT><<<grid, 256, p.ch.smem1, s>>>(G, g, p.t.seg, p.t.xent_m, p.t.xent_wx,       \
+                                                             p.t.xent_bx, p.t.deconv_x, p.t.tw, R);         \
+    else if (p.ch.per1 <= 16)                                                                                    \
         k_ned_spread_xfft<WT, 16><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
                                                                 p.t.xent_bx, p.t.deconv_x, p.t.tw, R);      \
     else                                                                                                    \

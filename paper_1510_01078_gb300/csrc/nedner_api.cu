@@ -423,17 +423,31 @@ void choose_chunks(nedner_plan_s& p) {
     // row fits in 128 KB of shared memory, smaller groups beyond
     c.c1 = std::min<long>(32, std::max<long>(2, pow2_floor((128L * 1024) / (8L * G.Lx))));
     c.c1 = std::min(c.c1, G.Nt);
-    c.threads1 = 256;
-    c.groups1 = c.threads1 / c.c1;
-    {
-        // complex row [Lx][c1/2], padded and rounded to 16 bytes, then the
-        // sweep's double-buffered batch staging (8 entries per lane group)
-        const long zlen = (padded((long)G.Lx * c.c1 / 2) + 1) & ~1L;
-        const size_t staging = (size_t)c.groups1 * (2 * 8 + 2 * 8 * (1 + spread_taps(G.w) + c.c1)) * 4;
-        c.smem1 = (size_t)zlen * 8 + staging;
-        c.per1 = (long)G.Lx * c.c1 / 2 <= 16L * c.threads1 ? 16 : 32;
-    }
     c.ca = c.c1;
+    c.threads1 = 256;
+    c.tpl1 = 1;
+    {
+        // Complex row [Lx][c1/2], padded and rounded to 16 bytes, then the
+        // sweep's double-buffered batch staging (8 entries per lane group).
+        // Two samples per lane (c1 = 64, warp-wide groups) when that fits two
+        // CTAs per SM; else one sample per lane.
+        const int wt = spread_taps(G.w);
+        auto smem_for = [&](long cc, long groups) {
+            const long zlen = (padded((long)G.Lx * cc / 2) + 1) & ~1L;
+            return (size_t)zlen * 8 + (size_t)groups * (2 * 8 + 2 * 8 * (1 + wt + cc)) * 4;
+        };
+        if (G.Nt >= 64 && smem_for(64, 8) <= 115200) {
+            c.tpl1 = 2;
+            c.c1 = 64;
+            c.groups1 = 8;
+            c.smem1 = smem_for(64, 8);
+            c.per1 = 32;
+        } else {
+            c.groups1 = c.threads1 / c.c1;
+            c.smem1 = smem_for(c.c1, c.groups1);
+            c.per1 = (long)G.Lx * c.c1 / 2 <= 16L * c.threads1 ? 16 : 32;
+        }
+    }
     c.smax = (int)std::max<long>(32, budget / (4L * c.ca));
     c.smem_interp = (size_t)G.Lx * c.ca * 8 + (size_t)c.smax * c.ca * 4;
     c.smem_grad = (size_t)G.Lx * c.ca * 8 + (size_t)c.smax * 8;
