@@ -59,14 +59,20 @@ __device__ __forceinline__ void flush_lower(float (&acc)[2 * WT], float* Zf, int
     }
 }
 
+// taps applied to column pairs with packed FP32x2 FMAs
 template <int WT, int D>
 __device__ __forceinline__ void add_taps(float (&acc)[2 * WT], const float4 (&wv)[WT / 4], float gval) {
+    const float2 g2 = make_float2(gval, gval);
 #pragma unroll
     for (int k4 = 0; k4 < WT / 4; ++k4) {
-        acc[D + 4 * k4 + 0] = fmaf(wv[k4].x, gval, acc[D + 4 * k4 + 0]);
-        acc[D + 4 * k4 + 1] = fmaf(wv[k4].y, gval, acc[D + 4 * k4 + 1]);
-        acc[D + 4 * k4 + 2] = fmaf(wv[k4].z, gval, acc[D + 4 * k4 + 2]);
-        acc[D + 4 * k4 + 3] = fmaf(wv[k4].w, gval, acc[D + 4 * k4 + 3]);
+        float2 lo = __ffma2_rn(make_float2(wv[k4].x, wv[k4].y), g2,
+                               make_float2(acc[D + 4 * k4 + 0], acc[D + 4 * k4 + 1]));
+        float2 hi = __ffma2_rn(make_float2(wv[k4].z, wv[k4].w), g2,
+                               make_float2(acc[D + 4 * k4 + 2], acc[D + 4 * k4 + 3]));
+        acc[D + 4 * k4 + 0] = lo.x;
+        acc[D + 4 * k4 + 1] = lo.y;
+        acc[D + 4 * k4 + 2] = hi.x;
+        acc[D + 4 * k4 + 3] = hi.y;
     }
 }
 
@@ -239,8 +245,8 @@ __device__ __forceinline__ void sweep_entry2(float2 (&acc)[2 * WT], float2* Z, i
     else if (WT >= 20 && d == 5) add_taps2<WT, (WT >= 20 ? 20 : 0)>(acc, wv, g2);
 }
 
-template <int WT>
-__global__ void __launch_bounds__(256, 2) k_ned_spread2_xfft(Geo G, const float* __restrict__ g,
+template <int WT, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo G, const float* __restrict__ g,
                                                              const int4* __restrict__ seg,
                                                              const int* __restrict__ xent_m,
                                                              const float* __restrict__ xent_wx,
@@ -248,7 +254,8 @@ __global__ void __launch_bounds__(256, 2) k_ned_spread2_xfft(Geo G, const float*
                                                              const float* __restrict__ deconv_x,
                                                              const float2* __restrict__ tw,
                                                              float2* __restrict__ R) {
-    constexpr int NT = 256, B = 8, C = 64, NB = 32;
+    constexpr int B = 8, C = 64, NB = 32;
+    constexpr int PER = 32;                          // values per thread of the in-place x-FFT, Lx * 32 <= PER * NT
     extern __shared__ float4 smem4[];
     const int Lx = G.Lx;
     float2* Z = reinterpret_cast<float2*>(smem4);                  // [Lx][32] complex row, padded
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(256, 2) k_ned_spread2_xfft(Geo G, const float*
         base += WT;
     }
 
-    block_fft_ip<32>(Z, Lx, NB, -1, tw);
+    block_fft_ip<PER>(Z, Lx, NB, -1, tw);
 
     const int items = G.nxh * C;
     for (int it = threadIdx.x; it < items; it += NT) {
@@ -418,19 +425,31 @@ __device__ __forceinline__ FF nu_abs(const Geo& G, float2 axy, int l) {
     return quick_two_sum(r, resid * (0.5f / r));
 }
 
-// sum_k P_k(s) B[((mu0 + k) mod Lt) * 2^lld + col] (padded buffer) with the tap polynomials unrolled (Horner)
+// sum_k P_k(s) B[((mu0 + k) mod Lt) * 2^lld + col] (padded buffer).  The window
+// is even, so tap W-1-k is tap k mirrored, P_{W-1-k}(s) = P_k(-s) (the tap
+// polynomials interpolate at nodes symmetric in s); with P_k(s) = E_k(s^2) +
+// s O_k(s^2) both taps of a pair come from one Horner evaluation of E_k and O_k.
 template <int W, int D>
 __device__ __forceinline__ float2 ner_gather(const TapPoly& P, const float2* Bf, int mu0, float s, int Lt, int lld,
                                              int col) {
+    constexpr int DE = D & ~1;                    // highest even power
+    constexpr int DO = (D & 1) ? D : D - 1;       // highest odd power
+    const float u = s * s;
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
-        float p = P.c[k * (D + 1) + D];
+    for (int k = 0; k < W / 2; ++k) {
+        float e = P.c[k * (D + 1) + DE];
 #pragma unroll
-        for (int d = D - 1; d >= 0; --d) p = fmaf(p, s, P.c[k * (D + 1) + d]);
-        const float2 b = Bf[padx((((mu0 + k) & (Lt - 1)) << lld) + col)];
-        acc.x = fmaf(p, b.x, acc.x);
-        acc.y = fmaf(p, b.y, acc.y);
+        for (int d = DE - 2; d >= 0; d -= 2) e = fmaf(e, u, P.c[k * (D + 1) + d]);
+        float o = P.c[k * (D + 1) + DO];
+#pragma unroll
+        for (int d = DO - 2; d >= 1; d -= 2) o = fmaf(o, u, P.c[k * (D + 1) + d]);
+        const float so = s * o;
+        const float pk = e + so, pm = e - so;     // taps k and W-1-k
+        const float2 bk = Bf[padx((((mu0 + k) & (Lt - 1)) << lld) + col)];
+        const float2 bm = Bf[padx((((mu0 + W - 1 - k) & (Lt - 1)) << lld) + col)];
+        acc = __ffma2_rn(make_float2(pk, pk), bk, acc);
+        acc = __ffma2_rn(make_float2(pm, pm), bm, acc);
     }
     return acc;
 }
@@ -648,10 +667,11 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 16>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e; \
     if ((e = cudaFuncSetAttribute(k_ned_spread_xfft<WT, 32>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
     NEDNER_ATTR_SPREAD(8) NEDNER_ATTR_SPREAD(12) NEDNER_ATTR_SPREAD(16) NEDNER_ATTR_SPREAD(20)
-    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<8>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
-    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<12>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
-    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<16>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
-    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<20>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+#define NEDNER_ATTR_SPREAD2(WT)                                                                              \
+    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<WT, 256>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ned_spread2_xfft<WT, 512>, (cudaFuncAttribute)a, (int)p.ch.smem1))) return e;
+    NEDNER_ATTR_SPREAD2(8) NEDNER_ATTR_SPREAD2(12) NEDNER_ATTR_SPREAD2(16) NEDNER_ATTR_SPREAD2(20)
+#undef NEDNER_ATTR_SPREAD2
 #undef NEDNER_ATTR_SPREAD
     if ((e = cudaFuncSetAttribute(k_ned_yfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2f))) return e;
 #define NEDNER_ATTR_NER(W, D)                                                                                   \
@@ -669,9 +689,12 @@ cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float
     const Geo& G = p.geo;
     dim3 grid(G.Ly, G.Nt / p.ch.c1);
 #define NEDNER_SPREAD(WT)                                                                                   \
-    if (p.ch.tpl1 == 2)                                                                                     \
-        k_ned_spread2_xfft<WT><<<grid, 256, p.ch.smem1, s>>>(G, g, p.t.seg, p.t.xent_m, p.t.xent_wx,       \
-                                                             p.t.xent_bx, p.t.deconv_x, p.t.tw, R);         \
+    if (p.ch.tpl1 == 2 && p.ch.threads1 <= 256)                                                             \
+        k_ned_spread2_xfft<WT, 256><<<grid, 256, p.ch.smem1, s>>>(G, g, p.t.seg, p.t.xent_m, p.t.xent_wx,  \
+                                                                  p.t.xent_bx, p.t.deconv_x, p.t.tw, R);    \
+    else if (p.ch.tpl1 == 2)                                                                                \
+        k_ned_spread2_xfft<WT, 512><<<grid, 512, p.ch.smem1, s>>>(G, g, p.t.seg, p.t.xent_m, p.t.xent_wx,  \
+                                                                  p.t.xent_bx, p.t.deconv_x, p.t.tw, R);    \
     else if (p.ch.per1 <= 16)                                                                                    \
         k_ned_spread_xfft<WT, 16><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
                                                                 p.t.xent_bx, p.t.deconv_x, p.t.tw, R);      \

@@ -442,6 +442,14 @@ void choose_chunks(nedner_plan_s& p) {
             c.groups1 = 8;
             c.smem1 = smem_for(64, 8);
             c.per1 = 32;
+        } else if (G.Nt >= 64 && (long)G.Lx * 32 <= 32L * 512 && smem_for(64, 16) <= 227 * 1024) {
+            // one CTA of 512 threads per SM
+            c.tpl1 = 2;
+            c.c1 = 64;
+            c.threads1 = 512;
+            c.groups1 = 16;
+            c.smem1 = smem_for(64, 16);
+            c.per1 = 32;
         } else {
             c.groups1 = c.threads1 / c.c1;
             c.smem1 = smem_for(c.c1, c.groups1);
