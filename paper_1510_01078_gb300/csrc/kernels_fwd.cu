@@ -350,9 +350,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
 // ---------------------------------------------------------------------------
 // Stage (a), part 2: y-FFT of length Ly for one jx and C time samples; keeps
 // jy = -ny/2..ny/2 (both Nyquist rows) divided by phihat(jy/Ly).  The FFT
-// runs in place in a padded buffer, Ly * C <= 4096 (16 values per thread).
+// runs in place in a padded buffer, Ly * C <= 256 PER (PER values per thread).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 3) k_ned_yfft(Geo G, int C, const float2* __restrict__ R,
+template <int PER>
+__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int C, const float2* __restrict__ R,
                                                      const float* __restrict__ deconv_y,
                                                      const float2* __restrict__ tw, float2* __restrict__ Ghat) {
     extern __shared__ float4 smem4[];
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(256, 3) k_ned_yfft(Geo G, int C, const float2*
         const int c = it & (C - 1);
         A[padx(it)] = R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c];
     }
-    block_fft_ip<16>(A, G.Ly, C, -1, tw);
+    block_fft_ip<PER>(A, G.Ly, C, -1, tw);
     const int items = G.nyp * C;
     for (int it = threadIdx.x; it < items; it += 256) {
         const int b = it >> lc;                // jy = b - ny/2
@@ -673,7 +674,8 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     NEDNER_ATTR_SPREAD2(8) NEDNER_ATTR_SPREAD2(12) NEDNER_ATTR_SPREAD2(16) NEDNER_ATTR_SPREAD2(20)
 #undef NEDNER_ATTR_SPREAD2
 #undef NEDNER_ATTR_SPREAD
-    if ((e = cudaFuncSetAttribute(k_ned_yfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2f))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_yfft<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2f))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_yfft<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2f))) return e;
 #define NEDNER_ATTR_NER(W, D)                                                                                   \
     if ((e = cudaFuncSetAttribute(k_ner_lines<W, D, 256>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e; \
     if ((e = cudaFuncSetAttribute(k_ner_lines<W, D, 512>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e;
@@ -714,7 +716,10 @@ cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float
 cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s) {
     const Geo& G = p.geo;
     dim3 grid(G.nxh, G.Nt / p.ch.c2f);
-    k_ned_yfft<<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, R, p.t.deconv_y, p.t.tw, Ghat);
+    if ((long)G.Ly * p.ch.c2f <= 16L * 256)
+        k_ned_yfft<16><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, R, p.t.deconv_y, p.t.tw, Ghat);
+    else
+        k_ned_yfft<32><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, R, p.t.deconv_y, p.t.tw, Ghat);
     return cudaGetLastError();
 }
 
