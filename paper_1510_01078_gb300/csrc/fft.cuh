@@ -25,8 +25,9 @@ constexpr int TW_N = 8192;
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// complex add / subtract as packed FP32x2 operations
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // multiply by -i (dir = -1) or +i (dir = +1)
@@ -221,14 +222,26 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, int N, int Ns, int nb, 
     const int lnb = ilog2(nb);
     const int items = stride << lnb;
     const int step = N / (Ns * R);
+    // Linear distance between the R loads (stride nb) and the R stores (Ns nb)
+    // of an item; once it is a multiple of 16 the padded distance is constant,
+    // so the addresses advance by one add each.
+    const int lld = stride << lnb, lst = Ns << lnb;
+    const int dld = lld + (lld >> 4), dst = lst + (lst >> 4);
     float2 v[IT][R];
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
         const int it = threadIdx.x + i * blockDim.x;
         if (it < items) {
             const int j = it >> lnb, b = it & (nb - 1);
+            const int a0 = (j << lnb) + b;
+            if (lld >= 16) {
+                const float2* p = buf + padx(a0);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[i][r] = buf[padx(((j + r * stride) << lnb) + b)];
+                for (int r = 0; r < R; ++r, p += dld) v[i][r] = *p;
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[i][r] = buf[padx(a0 + r * lld)];
+            }
         }
     }
     __syncthreads();
@@ -258,14 +271,27 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, int N, int Ns, int nb, 
                         v[i][r] = cmul(v[i][r], t);
                     }
                 } else {
+                    const float2* tp = tw + N;
+                    const int ks = k * step;
+                    int q = 0;
 #pragma unroll
-                    for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], twiddle(tw, k * r * step, N, DIR));
+                    for (int r = 1; r < R; ++r) {
+                        q += ks;
+                        const float2 t = __ldg(tp + q);
+                        v[i][r] = cmul(v[i][r], DIR < 0 ? t : cconj(t));
+                    }
                 }
             }
             dft_reg<R, DIR>(v[i]);
-            const int i0 = (j - k) * R + k;
+            const int a0 = (((j - k) * R + k) << lnb) + b;
+            if (lst >= 16) {
+                float2* p = buf + padx(a0);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[padx(((i0 + r * Ns) << lnb) + b)] = v[i][out_index<R>(r)];
+                for (int r = 0; r < R; ++r, p += dst) *p = v[i][out_index<R>(r)];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) buf[padx(a0 + r * lst)] = v[i][out_index<R>(r)];
+            }
         }
     }
     __syncthreads();
