@@ -152,7 +152,7 @@ nedner_status nedner_grad_positions(nedner_plan_t plan, const float* g, const fl
  * weight and inverse FFT) on the half lattice used internally,
  *   Ghat  device float2 [nx/2+1][ny+1][Nt],  Ghat[a][b][n] = G[(jx=a, jy=b-ny/2), n],
  * i.e. jx = 0..nx/2 and jy = -ny/2..ny/2 (both Nyquist rows included).
- * g as in nedner_forward (16-byte aligned, else NEDNER_EINVAL).
+ * g as in nedner_forward; g and Ghat 16-byte aligned, else NEDNER_EINVAL.
  */
 nedner_status nedner_ned_stage(nedner_plan_t plan, const float* g, void* Ghat, void* stream);
 

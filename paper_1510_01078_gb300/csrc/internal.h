@@ -96,7 +96,7 @@ struct TPState {
     void* work = nullptr;         // device: operand matrices of the data, GEMM 1 output, Nyquist line
     size_t work_bytes = 0;
     void* ex = nullptr;           // device BF16: 4 matrices (Re hi, Re lo, Im hi, Im lo), rows jx < nx/2, K = a
-    void* ey = nullptr;           // device BF16: 3 tiles x 6 matrices (Re hi/lo, Im hi/lo, -Im hi/lo), rows jy, K = b
+    void* ey = nullptr;           // device BF16: 2 tiles x 4 matrices (Re hi/lo, Im hi/lo), rows jy, K = b
     float2* exn = nullptr;        // device FP32: Ex row jx = nx/2
     float2* eyf = nullptr;        // device FP32: Ey [ny+1][nys]
     int* err = nullptr;           // device flag: a bounded wait ran out

@@ -6,25 +6,27 @@
 //   G[jx, jy, n] = sum_b Ey[jy, b] sum_a Ex[jx, a] A[b, a, n],
 //   Ex[jx, a] = exp(-2 pi i jx xs[a] / X), Ey[jy, b] = exp(-2 pi i jy ys[b] / Y),
 //   A[b, a, n] = w_m g[m, n],
-// i.e. two dense complex contractions per time sample, evaluated exactly (no
-// window, no oversampled grid) on the tensor cores:
-//   GEMM 1 (per n):  D[jx, b] = sum_a Ex[jx, a] A[b, a, n]        M = jx, N = b, K = a
-//   GEMM 2 (per n):  G[jx, jy] = sum_b D[jx, b] Ey[jy, b]         M = jx, N = jy, K = b
-// Operands are BF16 with a hi + lo split of every real factor
-// (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)); each real product is
-// formed as hi*hi + lo*hi + hi*lo with FP32 accumulation in tensor memory.
-// Shapes handled: nxs = nys = 128 sensors per axis, nx = ny = 256 output
-// grid (jx = 0..127 from GEMM tiles of M = 128; jy in three N tiles:
-// -128..-1, 0..127 and +128 padded to 16).  The line jx = 128 is evaluated on
-// the CUDA cores in FP32 (k_tp_nyq_t, k_tp_nyq_g).
+// i.e. two dense complex contractions, evaluated exactly (no window, no
+// oversampled grid) on the tensor cores:
+//   GEMM 1 (per n):       D[jx, b] = sum_a Ex[jx, a] A[b, a, n]     M = jx, N = b, K = a
+//   GEMM 2 (per jx):      G[jy, n] = sum_b Ey[jy, b] D[jx, b, n]    M = jy, N = n, K = b
+// GEMM 2 takes n as its N dimension so that every output row jy is a run of
+// contiguous time samples of Ghat.  Operands are BF16 with a hi + lo split of
+// every real factor (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)); each real
+// product is formed as hi*hi + lo*hi + hi*lo with FP32 accumulation in tensor
+// memory.  Shapes handled: nxs = nys = 128 sensors per axis, nx = ny = 256
+// output grid: jx = 0..127 as GEMM tiles of 128 rows, jy in two M tiles
+// (-128..-1 and 0..127); the row jy = +128 is summed in FP32 in GEMM 1's
+// epilogue and the line jx = 128 on the CUDA cores (k_tp_nyq_t, k_tp_nyq_g).
 //
 // Operand tiles live in global memory already in the tensor cores'
 // K-major, unswizzled shared-memory layout, split in K chunks of 64 so that
-// every (matrix, chunk) is one contiguous block moved by a single bulk copy
-// (cp.async.bulk, completion on an mbarrier).  Within a chunk, element
-// (row r, k) is at ((r/8) * 8 + k/8) * 64 + (r%8) * 8 + k%8 (core matrices
-// of 8 rows x 16 bytes; 128 bytes between core matrices along K, 1024 bytes
-// between 8-row groups).
+// every operand block is contiguous and moved by a single bulk copy
+// (cp.async.bulk, completion on an mbarrier).  Within a chunk of a matrix
+// with `rows` rows, element (row r, k) is at
+// ((r/8) * 8 + k/8) * 64 + (r%8) * 8 + k%8 (core matrices of 8 rows x 16
+// bytes; 128 bytes between core matrices along K, 1024 bytes between 8-row
+// groups).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -40,9 +42,11 @@ constexpr int KC = 64;                 // K chunk
 constexpr int ROWS = 128;              // M and N of the main tiles
 constexpr uint32_t CHUNK = ROWS * KC * 2;          // 16 KB per (128-row matrix, chunk)
 constexpr uint32_t MAT = ROWS * K * 2;             // 32 KB per 128-row matrix
-constexpr uint32_t SMALL_ROWS = 16;                // rows of the jy = +128 tile
-constexpr uint32_t SMALL_CHUNK = SMALL_ROWS * KC * 2;  // 2 KB
-constexpr uint32_t SMALL_MAT = SMALL_ROWS * K * 2;     // 4 KB
+constexpr int TN = 32;                              // time samples per GEMM 2 tile (its N)
+constexpr uint32_t DT_CHUNK = TN * KC * 2;          // 4 KB per (32-row matrix, chunk)
+constexpr uint32_t DT_MAT = TN * K * 2;             // 8 KB per 32-row matrix
+constexpr uint32_t DT_TILE = 4 * DT_MAT;            // D tile of one (jx, n tile): Re hi, Re lo, Im hi, Im lo
+constexpr int STAGES = 3;                           // GEMM 2 operand ring
 constexpr int WAIT_LIMIT = 1 << 26;    // iterations of a bounded mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -77,6 +81,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 
 __device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -153,13 +161,16 @@ __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __res
 // ---------------------------------------------------------------------------
 // GEMM 1: persistent over n.  Ex (4 matrices: Re hi, Re lo, Im hi, Im lo;
 // rows jx = 0..127, K = a) stays in shared memory; per n the two matrices of
-// A (hi, lo; rows b) are loaded, 12 MMAs per K step of 16 accumulate
-// D_re, D_im (128 x 128 each) in tensor memory, and the epilogue writes D as
-// BF16 hi/lo matrices (rows jx, K = b) for GEMM 2.
+// A (hi, lo; rows b) are loaded, 6 MMAs per K step of 16 accumulate D_re,
+// D_im (128 x 128 each) in tensor memory.  The epilogue writes D as BF16
+// hi/lo into the GEMM 2 operand tiles (per jx and n tile: rows n, K = b) and
+// sums the row jy = +ny/2 of G in FP32: G[jx, +ny/2, n] = sum_b Ey[+ny/2, b] D[jx, b].
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128, 1) k_tp_gemm1(const Geo G, const __nv_bfloat16* __restrict__ Ex,
                                                      const __nv_bfloat16* __restrict__ At,
-                                                     __nv_bfloat16* __restrict__ Dt, int* __restrict__ err) {
+                                                     const float2* __restrict__ eyf,
+                                                     __nv_bfloat16* __restrict__ Dt, float2* __restrict__ Ghat,
+                                                     int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __nv_bfloat16* sEx = reinterpret_cast<__nv_bfloat16*>(smem);             // 4 x 32 KB
     __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem + 4 * MAT);    // 2 x 32 KB
@@ -224,23 +235,34 @@ __global__ void __launch_bounds__(128, 1) k_tp_gemm1(const Geo G, const __nv_bfl
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: row jx = 32 warp + lane; columns b
         const int jx = warp * 32 + lane;
-        __nv_bfloat16* out = Dt + (size_t)n * 4 * (ROWS * K);      // matrices Re hi, Re lo, Im hi, Im lo
-        for (int part = 0; part < 2; ++part) {
-            for (int c0 = 0; c0 < 128; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tD + ((uint32_t)(warp * 32) << 16) + part * 128 + c0, v);
+        const int ntn = G.Nt / TN, nr = n % TN;
+        __nv_bfloat16* out = Dt + ((size_t)jx * ntn + n / TN) * (DT_TILE / 2);
+        const float2* eyp = eyf + (size_t)G.ny * K;          // Ey row jy = +ny/2
+        float gr = 0.f, gi = 0.f;
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            uint32_t vr[32], vi[32];
+            tmem_ld32(tD + ((uint32_t)(warp * 32) << 16) + c0, vr);
+            tmem_ld32(tD + ((uint32_t)(warp * 32) << 16) + 128 + c0, vi);
 #pragma unroll
-                for (int g8 = 0; g8 < 4; ++g8) {
-                    __align__(16) __nv_bfloat16 hi[8], lo[8];
+            for (int g8 = 0; g8 < 4; ++g8) {
+                __align__(16) __nv_bfloat16 rh[8], rl[8], ih[8], il[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) split_bf16(__uint_as_float(v[g8 * 8 + j]), hi[j], lo[j]);
-                    const int off = tile_off(jx, c0 + g8 * 8, ROWS);
-                    *reinterpret_cast<uint4*>(out + (2 * part) * (ROWS * K) + off) = *reinterpret_cast<uint4*>(hi);
-                    *reinterpret_cast<uint4*>(out + (2 * part + 1) * (ROWS * K) + off) =
-                        *reinterpret_cast<uint4*>(lo);
+                for (int j = 0; j < 8; ++j) {
+                    const float dr = __uint_as_float(vr[g8 * 8 + j]), di = __uint_as_float(vi[g8 * 8 + j]);
+                    split_bf16(dr, rh[j], rl[j]);
+                    split_bf16(di, ih[j], il[j]);
+                    const float2 e = __ldg(&eyp[c0 + g8 * 8 + j]);
+                    gr = fmaf(e.x, dr, fmaf(-e.y, di, gr));
+                    gi = fmaf(e.x, di, fmaf(e.y, dr, gi));
                 }
+                const int off = tile_off(nr, c0 + g8 * 8, TN);
+                *reinterpret_cast<uint4*>(out + 0 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(rh);
+                *reinterpret_cast<uint4*>(out + 1 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(rl);
+                *reinterpret_cast<uint4*>(out + 2 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(ih);
+                *reinterpret_cast<uint4*>(out + 3 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(il);
             }
         }
+        Ghat[((size_t)jx * G.nyp + G.ny) * G.Nt + n] = make_float2(gr, gi);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -257,117 +279,151 @@ __global__ void __launch_bounds__(128, 1) k_tp_gemm1(const Geo G, const __nv_bfl
 }
 
 // ---------------------------------------------------------------------------
-// GEMM 2: CTA per (n, jy tile).  Per K chunk: D (4 matrices, rows jx, K = b)
-// and the tile of Ey (6 matrices: Re hi/lo, Im hi/lo, -Im hi/lo; rows jy);
-// 24 MMAs per K step of 16:
-//   G_re = D_re Ey_re - D_im Ey_im,  G_im = D_re Ey_im + D_im Ey_re.
-// Epilogue writes G[jx][jy + ny/2][n] (complex64) for the tile's real rows.
+// GEMM 2: persistent and warp-specialised.  A CTA owns one M tile of jy
+// (blockIdx.x even: jy = -128..-1, odd: 0..127) and keeps that tile of Ey
+// (Re hi, Re lo, Im hi, Im lo; rows jy, K = b; 128 KB) in shared memory; it
+// loops over work items (jx, n tile of 32) shared out among the CTAs of its
+// tile.  Warp 0 streams the items' D tiles (32 KB, rows n) into a ring of
+// STAGES buffers; warp 1 issues 12 MMAs (M 128, N 32) per K step of 16:
+//   G_re = Ey_re D_re - Ey_im D_im,  G_im = Ey_re D_im + Ey_im D_re
+// (the minus by the instruction's negate-A bit) into one of two accumulator
+// pairs in tensor memory; warps 2-5 read an accumulator pair back (lane
+// quarter = warp % 4, row jy) and write 32 contiguous time samples of Ghat
+// per row.  Every wait is bounded: a wait that runs out sets *err and the
+// role stops; the others then run out too, and the CTA waits for its own
+// copies and MMAs in flight before it frees tensor memory.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 1) k_tp_gemm2(const Geo G, const __nv_bfloat16* __restrict__ Dt,
+__global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfloat16* __restrict__ Dt,
                                                      const __nv_bfloat16* __restrict__ Ey,
                                                      float2* __restrict__ Ghat, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t load_bar, mma_bar;
+    unsigned char* sEy = smem;                                  // 4 x 32 KB
+    unsigned char* sD = smem + 4 * MAT;                         // STAGES x 32 KB
+    __shared__ __align__(8) uint64_t ey_bar, full[STAGES], empty[STAGES], tfull[2], tempty[2], done_bar;
     __shared__ uint32_t taddr_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n = blockIdx.x;
-    const int tile = blockIdx.y;                                  // 0: jy -128..-1, 1: 0..127, 2: +128
-    const int ntile = (tile == 2) ? (int)SMALL_ROWS : ROWS;
-    const uint32_t bchunk = (tile == 2) ? SMALL_CHUNK : CHUNK;
-    const uint32_t bmat = (tile == 2) ? SMALL_MAT : MAT;
-    // Ey global layout: tile 0 (6 matrices of 32 KB), tile 1 (6 x 32 KB), tile 2 (6 x 4 KB)
-    const __nv_bfloat16* eyt = Ey + (size_t)tile * 6 * (MAT / 2);
-    __nv_bfloat16* sD = reinterpret_cast<__nv_bfloat16*>(smem);                   // 4 x 16 KB (one chunk)
-    __nv_bfloat16* sE = reinterpret_cast<__nv_bfloat16*>(smem + 4 * CHUNK);       // 6 x bchunk
+    const int tile = blockIdx.x & 1;
+    const int slot = blockIdx.x >> 1, nslots = gridDim.x >> 1;
+    const int ntn = G.Nt / TN;
+    const int items = K * ntn;                                  // jx = 0..127 x n tiles
 
     if (tid == 0) {
-        bar_init(&load_bar, 1);
-        bar_init(&mma_bar, 1);
+        bar_init(&ey_bar, 1);
+        for (int s = 0; s < STAGES; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            bar_init(&tfull[a], 1);
+            bar_init(&tempty[a], 4);
+        }
+        bar_init(&done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
-                     "r"(256));
+                     "r"(128));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tG = taddr_s;                  // Re at [0, ntile), Im at [128, 128 + ntile)
-    const uint32_t idesc = idesc_bf16(ntile);
-    bool ok = true;
-    uint32_t lphase = 0, mphase = 0;
-    const __nv_bfloat16* dsrc = Dt + (size_t)n * 4 * (ROWS * K);
-    for (int c = 0; c < 2 && ok; ++c) {
-        if (tid == 0) {
-            expect_tx(&load_bar, 4 * CHUNK + 6 * bchunk);
+    const uint32_t tacc = taddr_s;                              // pair a: Re at 64 a, Im at 64 a + 32
+
+    if (warp == 0) {
+        if (lane == 0) {
+            expect_tx(&ey_bar, 4 * MAT);
             for (int q = 0; q < 4; ++q)
-                bulk_load(sD + q * (CHUNK / 2), dsrc + q * (ROWS * K) + c * (ROWS * KC), CHUNK, &load_bar);
-            for (int q = 0; q < 6; ++q)
-                bulk_load(sE + q * (bchunk / 2), eyt + q * (bmat / 2) + c * (ntile * KC), bchunk, &load_bar);
-        }
-        ok = __syncthreads_and(bar_wait(&load_bar, lphase));
-        lphase ^= 1;
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            const uint32_t d = smem_u32(sD), e = smem_u32(sE);
-            for (int s = 0; s < KC / 16; ++s) {
-                const uint32_t off = s * 256;
-                const uint64_t drh = sdesc(d + 0 * CHUNK + off), drl = sdesc(d + 1 * CHUNK + off);
-                const uint64_t dih = sdesc(d + 2 * CHUNK + off), dil = sdesc(d + 3 * CHUNK + off);
-                const uint64_t erh = sdesc(e + 0 * bchunk + off), erl = sdesc(e + 1 * bchunk + off);
-                const uint64_t eih = sdesc(e + 2 * bchunk + off), eil = sdesc(e + 3 * bchunk + off);
-                const uint64_t nih = sdesc(e + 4 * bchunk + off), nil = sdesc(e + 5 * bchunk + off);
-                const uint32_t acc = (c | s) ? 1u : 0u;
-                // G_re = D_re Ey_re + D_im (-Ey_im)
-                mma(tG, drh, erh, idesc, acc);
-                mma(tG, drl, erh, idesc, 1u);
-                mma(tG, drh, erl, idesc, 1u);
-                mma(tG, dih, nih, idesc, 1u);
-                mma(tG, dil, nih, idesc, 1u);
-                mma(tG, dih, nil, idesc, 1u);
-                // G_im = D_re Ey_im + D_im Ey_re
-                mma(tG + 128, drh, eih, idesc, acc);
-                mma(tG + 128, drl, eih, idesc, 1u);
-                mma(tG + 128, drh, eil, idesc, 1u);
-                mma(tG + 128, dih, erh, idesc, 1u);
-                mma(tG + 128, dil, erh, idesc, 1u);
-                mma(tG + 128, dih, erl, idesc, 1u);
+                bulk_load(sEy + q * MAT, Ey + (size_t)(tile * 4 + q) * (MAT / 2), MAT, &ey_bar);
+            int q = 0, last = -1;
+            for (int it = slot; it < items; it += nslots, ++q) {
+                const int s = q % STAGES;
+                if (!bar_wait(&empty[s], ((q / STAGES) & 1) ^ 1)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                const int jx = it / ntn, nt = it - jx * ntn;
+                expect_tx(&full[s], DT_TILE);
+                bulk_load(sD + s * DT_TILE, Dt + ((size_t)jx * ntn + nt) * (DT_TILE / 2), DT_TILE, &full[s]);
+                last = q;
             }
-            mma_commit(&mma_bar);
+            // the copies issued last have landed before the CTA exits
+            if (last >= 0) bar_wait(&full[last % STAGES], (last / STAGES) & 1);
+            bar_wait(&ey_bar, 0);
         }
-        ok = __syncthreads_and(bar_wait(&mma_bar, mphase));
-        mphase ^= 1;
-    }
-    if (ok) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int jx = warp * 32 + lane;
-        const int jy0 = (tile == 0) ? -G.ny / 2 : (tile == 1 ? 0 : G.ny / 2);
-        const int nreal = (tile == 2) ? 1 : ROWS;
-        for (int c0 = 0; c0 < ntile; c0 += 32) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = bar_wait(&ey_bar, 0);
+            const uint32_t id = idesc_bf16(TN), idn = id | (1u << 13);     // N = 32; negate A
+            const uint32_t ey = smem_u32(sEy);
+            int q = 0;
+            for (int it = slot; it < items && ok; it += nslots, ++q) {
+                const int s = q % STAGES, a = q & 1;
+                if (!bar_wait(&tempty[a], ((q >> 1) & 1) ^ 1) || !bar_wait(&full[s], (q / STAGES) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = smem_u32(sD + s * DT_TILE);
+                const uint32_t tre = tacc + 64 * a, tim = tre + 32;
+                for (int c = 0; c < 2; ++c)
+                    for (int k = 0; k < KC / 16; ++k) {
+                        const uint32_t oa = c * CHUNK + k * 256, ob = c * DT_CHUNK + k * 256;
+                        const uint64_t erh = sdesc(ey + 0 * MAT + oa), erl = sdesc(ey + 1 * MAT + oa);
+                        const uint64_t eih = sdesc(ey + 2 * MAT + oa), eil = sdesc(ey + 3 * MAT + oa);
+                        const uint64_t drh = sdesc(d + 0 * DT_MAT + ob), drl = sdesc(d + 1 * DT_MAT + ob);
+                        const uint64_t dih = sdesc(d + 2 * DT_MAT + ob), dil = sdesc(d + 3 * DT_MAT + ob);
+                        const uint32_t acc = (c | k) ? 1u : 0u;
+                        mma(tre, erh, drh, id, acc);
+                        mma(tre, erl, drh, id, 1u);
+                        mma(tre, erh, drl, id, 1u);
+                        mma(tre, eih, dih, idn, 1u);
+                        mma(tre, eil, dih, idn, 1u);
+                        mma(tre, eih, dil, idn, 1u);
+                        mma(tim, erh, dih, id, acc);
+                        mma(tim, erl, dih, id, 1u);
+                        mma(tim, erh, dil, id, 1u);
+                        mma(tim, eih, drh, id, 1u);
+                        mma(tim, eil, drh, id, 1u);
+                        mma(tim, eih, drl, id, 1u);
+                    }
+                mma_commit(&empty[s]);
+                mma_commit(&tfull[a]);
+            }
+            if (!ok) atomicExch(err, 1);
+            // every MMA issued has completed before tensor memory is freed
+            mma_commit(&done_bar);
+            bar_wait(&done_bar, 0);
+        }
+    } else {
+        const int quarter = warp & 3;                           // TMEM lanes 32 quarter .. + 31
+        const int b = tile * K + quarter * 32 + lane;           // Ghat row: jy + ny/2
+        int q = 0;
+        for (int it = slot; it < items; it += nslots, ++q) {
+            const int a = q & 1;
+            if (!__all_sync(0xffffffffu, bar_wait(&tfull[a], (q >> 1) & 1))) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t vr[32], vi[32];
-            if (c0 + 32 <= ntile) {
-                tmem_ld32(tG + ((uint32_t)(warp * 32) << 16) + c0, vr);
-                tmem_ld32(tG + ((uint32_t)(warp * 32) << 16) + 128 + c0, vi);
-            } else {
-                // a 16-column tile: read 32 columns (the upper 16 hold no data of ours) and use the first
-                tmem_ld32(tG + ((uint32_t)(warp * 32) << 16) + c0, vr);
-                tmem_ld32(tG + ((uint32_t)(warp * 32) << 16) + 128 + c0, vi);
-            }
-            for (int j = 0; j < 32 && c0 + j < nreal; ++j) {
-                const int b = jy0 + c0 + j + G.ny / 2;
-                Ghat[((size_t)jx * G.nyp + b) * G.Nt + n] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
-            }
+            const uint32_t ta = tacc + ((uint32_t)(quarter * 32) << 16) + 64 * a;
+            tmem_ld32(ta, vr);
+            tmem_ld32(ta + 32, vi);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&tempty[a]);
+            const int jx = it / ntn, nt = it - jx * ntn;
+            float4* o = reinterpret_cast<float4*>(Ghat + ((size_t)jx * G.nyp + b) * G.Nt + nt * TN);
+#pragma unroll
+            for (int j = 0; j < TN / 2; ++j)
+                o[j] = make_float4(__uint_as_float(vr[2 * j]), __uint_as_float(vi[2 * j]), __uint_as_float(vr[2 * j + 1]),
+                                   __uint_as_float(vi[2 * j + 1]));
         }
-    }
-    if (!ok) {
-        if (lane == 0) atomicExch(err, 1);
-        bar_wait(&load_bar, lphase);
-        bar_wait(&mma_bar, mphase);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tG), "r"(256));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(128));
 }
 
 // ---------------------------------------------------------------------------
@@ -417,7 +473,7 @@ size_t tp_work_bytes(int Nt) {
 }
 
 size_t tp_gemm1_smem() { return 6 * tp::MAT; }
-size_t tp_gemm2_smem() { return 4 * tp::CHUNK + 6 * tp::CHUNK; }
+size_t tp_gemm2_smem() { return 4 * tp::MAT + tp::STAGES * tp::DT_TILE; }
 
 cudaError_t configure_tp_kernels() {
     cudaError_t e;
@@ -432,10 +488,10 @@ cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, 
     __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(p.tp.work);
     __nv_bfloat16* Dt = At + (size_t)G.Nt * 2 * (tp::ROWS * tp::K);
     tp::k_tp_prep<<<dim3((G.Nt + 15) / 16, tp::K / 4), 256, 0, s>>>(G, g, p.t.sens_fac, At);
-    tp::k_tp_gemm1<<<std::min(G.Nt, p.tp.sms), 128, tp_gemm1_smem(), s>>>(G, reinterpret_cast<const __nv_bfloat16*>(p.tp.ex),
-                                                                          At, Dt, p.tp.err);
-    tp::k_tp_gemm2<<<dim3(G.Nt, 3), 128, tp_gemm2_smem(), s>>>(G, Dt, reinterpret_cast<const __nv_bfloat16*>(p.tp.ey),
-                                                               Ghat, p.tp.err);
+    tp::k_tp_gemm1<<<std::min(G.Nt, p.tp.sms), 128, tp_gemm1_smem(), s>>>(
+        G, reinterpret_cast<const __nv_bfloat16*>(p.tp.ex), At, p.tp.eyf, Dt, Ghat, p.tp.err);
+    tp::k_tp_gemm2<<<2 * std::max(1, p.tp.sms / 2), 192, tp_gemm2_smem(), s>>>(
+        G, Dt, reinterpret_cast<const __nv_bfloat16*>(p.tp.ey), Ghat, p.tp.err);
     float2* tl = reinterpret_cast<float2*>(Dt + (size_t)G.Nt * 4 * (tp::ROWS * tp::K));
     tp::k_tp_nyq_t<<<dim3((G.Nt + 31) / 32, tp::K), 32, 0, s>>>(G, g, p.t.sens_fac, p.tp.exn, tl);
     tp::k_tp_nyq_g<<<dim3((G.Nt + 31) / 32, G.nyp), 32, 0, s>>>(G, tl, p.tp.eyf, Ghat);

@@ -97,7 +97,8 @@ nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
                 return NEDNER_EINVAL;
         }
     const size_t MATE = (size_t)NS * NS;               // elements of a 128-row matrix
-    std::vector<uint16_t> ex(4 * MATE), ey(2 * 6 * MATE + 6 * 16 * NS, 0);
+    if (G.Nt < 32) return NEDNER_EINVAL;                // GEMM 2 tiles hold 32 time samples
+    std::vector<uint16_t> ex(4 * MATE), ey(2 * 4 * MATE, 0);
     for (int jx = 0; jx < NS; ++jx)
         for (int a = 0; a < NS; ++a) {
             const double ph = -2.0 * kPi * (double)jx * xs[a] / X;
@@ -109,27 +110,21 @@ nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
             ex[2 * MATE + o] = ih;
             ex[3 * MATE + o] = f2bf(im - bf2f(ih));
         }
-    for (int t = 0; t < 3; ++t) {
-        const int rows = (t == 2) ? 16 : NS;
-        const size_t mat = (size_t)rows * NS;
-        const size_t tbase = (size_t)t * 6 * MATE;
-        for (int r = 0; r < rows; ++r) {
-            if (t == 2 && r > 0) continue;                 // padding rows stay zero
-            const int jy = (t == 0) ? r - NS : (t == 1 ? r : NS);
+    // Ey as GEMM 2's A operand: two M tiles (jy = -128..-1, 0..127), 4 matrices each
+    for (int t = 0; t < 2; ++t)
+        for (int r = 0; r < NS; ++r) {
+            const int jy = (t == 0) ? r - NS : r;
             for (int b = 0; b < NS; ++b) {
                 const double ph = -2.0 * kPi * (double)jy * ys[b] / Y;
                 const float re = (float)std::cos(ph), im = (float)std::sin(ph);
-                const size_t o = tp_off(r, b, rows);
-                const uint16_t rh = f2bf(re), ih = f2bf(im), nh = f2bf(-im);
-                ey[tbase + 0 * mat + o] = rh;
-                ey[tbase + 1 * mat + o] = f2bf(re - bf2f(rh));
-                ey[tbase + 2 * mat + o] = ih;
-                ey[tbase + 3 * mat + o] = f2bf(im - bf2f(ih));
-                ey[tbase + 4 * mat + o] = nh;
-                ey[tbase + 5 * mat + o] = f2bf(-im - bf2f(nh));
+                const size_t o = (size_t)t * 4 * MATE + tp_off(r, b, NS);
+                const uint16_t rh = f2bf(re), ih = f2bf(im);
+                ey[o + 0 * MATE] = rh;
+                ey[o + 1 * MATE] = f2bf(re - bf2f(rh));
+                ey[o + 2 * MATE] = ih;
+                ey[o + 3 * MATE] = f2bf(im - bf2f(ih));
             }
         }
-    }
     std::vector<float2> exn(NS), eyf((size_t)G.nyp * NS);
     for (int a = 0; a < NS; ++a) {
         const double ph = -2.0 * kPi * (double)(G.nx / 2) * xs[a] / X;
@@ -662,7 +657,7 @@ nedner_status nedner_forward_profiled(nedner_plan_t p, const float* g, float* p0
 
 nedner_status nedner_ned_stage(nedner_plan_t p, const float* g, void* Ghat, void* stream) {
     if (!p || !Ghat || (p->M > 0 && !g)) return NEDNER_EINVAL;
-    if (((uintptr_t)g & 15) != 0) return NEDNER_EINVAL;
+    if (((uintptr_t)g & 15) != 0 || ((uintptr_t)Ghat & 15) != 0) return NEDNER_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     float2* A = (float2*)p->ws;
     cudaError_t e;

@@ -94,3 +94,13 @@ def test_tensor_mode_rejects_other_layouts(nd):
     with pytest.raises(nd.NednerError) as ei:
         nd.plan_from_config(case, ned_mode="tensor_bf16")
     assert ei.value.status == 1
+
+
+def test_tensor_kernels_report_no_timeouts(nd, c5_sparse):
+    cfg, ns, gs, g = c5_sparse
+    plan = nd.plan_from_config(cfg, ned_mode="tensor_bf16")
+    x = torch.as_tensor(g, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        plan.forward(x)
+    assert plan.device_status() == 0        # no bounded mbarrier wait ran out
+    plan.close()
