@@ -17,7 +17,7 @@
 // memory.  Shapes handled: nxs = nys = 128 sensors per axis, nx = ny = 256
 // output grid: jx = 0..127 as GEMM tiles of 128 rows, jy in two M tiles
 // (-128..-1 and 0..127); the row jy = +128 is summed in FP32 in GEMM 1's
-// epilogue and the line jx = 128 on the CUDA cores (k_tp_nyq_t, k_tp_nyq_g).
+// epilogue and the line jx = 128 on the CUDA cores (k_tp_prep, k_tp_nyq_g).
 //
 // Operand tiles live in global memory already in the tensor cores'
 // K-major, unswizzled shared-memory layout, split in K chunks of 64 so that
@@ -133,7 +133,8 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 // (256 threads; CTA = 16 time samples x 4 rows b)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __restrict__ g,
-                                                 const float* __restrict__ fac, __nv_bfloat16* __restrict__ At) {
+                                                 const float* __restrict__ fac, const float2* __restrict__ exn,
+                                                 __nv_bfloat16* __restrict__ At, float2* __restrict__ t) {
     __shared__ float tile[4 * K][17];
     const int n0 = blockIdx.x * 16;
     const int b0 = blockIdx.y * 4;
@@ -155,6 +156,20 @@ __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __res
         __nv_bfloat16* base = At + (size_t)n * 2 * (ROWS * K);
         *reinterpret_cast<uint4*>(base + off) = *reinterpret_cast<uint4*>(hi);
         *reinterpret_cast<uint4*>(base + ROWS * K + off) = *reinterpret_cast<uint4*>(lo);
+    }
+    // the line jx = nx/2 (CUDA cores, FP32): t[b][n] = sum_a Ex[nx/2, a] A[b, a, n]
+    if (threadIdx.x < 64) {
+        const int c = threadIdx.x & 15, rb = threadIdx.x >> 4;
+        const int n = n0 + c;
+        float2 sacc = make_float2(0.f, 0.f);
+#pragma unroll 8
+        for (int a = 0; a < K; ++a) {
+            const float v = tile[rb * K + a][c];
+            const float2 e = __ldg(&exn[a]);
+            sacc.x = fmaf(e.x, v, sacc.x);
+            sacc.y = fmaf(e.y, v, sacc.y);
+        }
+        if (n < G.Nt) t[(size_t)(b0 + rb) * G.Nt + n] = sacc;
     }
 }
 
@@ -354,7 +369,11 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
         if (lane == 0) {
             bool ok = bar_wait(&ey_bar, 0);
             const uint32_t id = idesc_bf16(TN), idn = id | (1u << 13);     // N = 32; negate A
-            const uint32_t ey = smem_u32(sEy);
+            // descriptors of the operand bases; a K step adds its byte offset / 16
+            // to the start-address field (no carry: shared addresses < 2^18)
+            const uint64_t e0 = sdesc(smem_u32(sEy)), e1 = e0 + (MAT >> 4), e2 = e0 + 2 * (MAT >> 4),
+                           e3 = e0 + 3 * (MAT >> 4);
+            const uint64_t dbase = sdesc(smem_u32(sD));
             int q = 0;
             for (int it = slot; it < items && ok; it += nslots, ++q) {
                 const int s = q % STAGES, a = q & 1;
@@ -363,15 +382,16 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t d = smem_u32(sD + s * DT_TILE);
+                const uint64_t d0 = dbase + (uint64_t)((s * DT_TILE) >> 4);
                 const uint32_t tre = tacc + 64 * a, tim = tre + 32;
+#pragma unroll
                 for (int c = 0; c < 2; ++c)
+#pragma unroll
                     for (int k = 0; k < KC / 16; ++k) {
-                        const uint32_t oa = c * CHUNK + k * 256, ob = c * DT_CHUNK + k * 256;
-                        const uint64_t erh = sdesc(ey + 0 * MAT + oa), erl = sdesc(ey + 1 * MAT + oa);
-                        const uint64_t eih = sdesc(ey + 2 * MAT + oa), eil = sdesc(ey + 3 * MAT + oa);
-                        const uint64_t drh = sdesc(d + 0 * DT_MAT + ob), drl = sdesc(d + 1 * DT_MAT + ob);
-                        const uint64_t dih = sdesc(d + 2 * DT_MAT + ob), dil = sdesc(d + 3 * DT_MAT + ob);
+                        const uint64_t oa = (c * CHUNK + k * 256) >> 4, ob = (c * DT_CHUNK + k * 256) >> 4;
+                        const uint64_t erh = e0 + oa, erl = e1 + oa, eih = e2 + oa, eil = e3 + oa;
+                        const uint64_t drh = d0 + ob, drl = d0 + (DT_MAT >> 4) + ob;
+                        const uint64_t dih = d0 + 2 * (DT_MAT >> 4) + ob, dil = d0 + 3 * (DT_MAT >> 4) + ob;
                         const uint32_t acc = (c | k) ? 1u : 0u;
                         mma(tre, erh, drh, id, acc);
                         mma(tre, erl, drh, id, 1u);
@@ -428,41 +448,31 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
 
 // ---------------------------------------------------------------------------
 // The line jx = nx/2 for every jy and n, on the CUDA cores in FP32:
-//   t[b][n] = sum_a Ex[nx/2, a] A[b, a, n]            (k_tp_nyq_t: CTA = 32 n, one b)
-//   G[nx/2, jy, n] = sum_b Ey[jy, b] t[b][n]          (k_tp_nyq_g: CTA = 32 n, one jy)
+//   t[b][n] = sum_a Ex[nx/2, a] A[b, a, n]            (in k_tp_prep, from its tile of A)
+//   G[nx/2, jy, n] = sum_b Ey[jy, b] t[b][n]          (k_tp_nyq_g: CTA = 32 n x 8 jy at a time)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) k_tp_nyq_t(const Geo G, const float* __restrict__ g,
-                                                 const float* __restrict__ fac, const float2* __restrict__ exn,
-                                                 float2* __restrict__ t) {
-    const int n = blockIdx.x * 32 + threadIdx.x;
-    const int b = blockIdx.y;
-    if (n >= G.Nt) return;
-    float2 s = make_float2(0.f, 0.f);
-#pragma unroll 8
-    for (int a = 0; a < K; ++a) {
-        const int m = b * K + a;
-        const float v = __ldg(&fac[m]) * __ldg(&g[(size_t)m * G.Nt + n]);
-        const float2 e = __ldg(&exn[a]);
-        s.x = fmaf(e.x, v, s.x);
-        s.y = fmaf(e.y, v, s.y);
+__global__ void __launch_bounds__(256) k_tp_nyq_g(const Geo G, const float2* __restrict__ t,
+                                                  const float2* __restrict__ eyf, float2* __restrict__ Ghat) {
+    __shared__ float2 ts[K][33];                     // t[b][n0 .. n0 + 31]
+    const int n0 = blockIdx.x * 32;
+    const int ln = threadIdx.x & 31, jr = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < K * 32; i += 256) {
+        const int b = i >> 5, c = i & 31;
+        ts[b][c] = (n0 + c < G.Nt) ? t[(size_t)b * G.Nt + n0 + c] : make_float2(0.f, 0.f);
     }
-    t[(size_t)b * G.Nt + n] = s;
-}
-
-__global__ void __launch_bounds__(32) k_tp_nyq_g(const Geo G, const float2* __restrict__ t,
-                                                 const float2* __restrict__ eyf, float2* __restrict__ Ghat) {
-    const int n = blockIdx.x * 32 + threadIdx.x;
-    const int bj = blockIdx.y;                       // jy = bj - ny/2
-    if (n >= G.Nt) return;
-    float2 s = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int n = n0 + ln;
+    for (int bj = blockIdx.y * 8 + jr; bj < G.nyp; bj += gridDim.y * 8) {   // jy = bj - ny/2
+        float2 sacc = make_float2(0.f, 0.f);
 #pragma unroll 8
-    for (int b = 0; b < K; ++b) {
-        const float2 e = __ldg(&eyf[(size_t)bj * K + b]);
-        const float2 v = __ldg(&t[(size_t)b * G.Nt + n]);
-        s.x = fmaf(e.x, v.x, fmaf(-e.y, v.y, s.x));
-        s.y = fmaf(e.x, v.y, fmaf(e.y, v.x, s.y));
+        for (int b = 0; b < K; ++b) {
+            const float2 e = __ldg(&eyf[(size_t)bj * K + b]);
+            const float2 v = ts[b][ln];
+            sacc.x = fmaf(e.x, v.x, fmaf(-e.y, v.y, sacc.x));
+            sacc.y = fmaf(e.x, v.y, fmaf(e.y, v.x, sacc.y));
+        }
+        if (n < G.Nt) Ghat[((size_t)(G.nx / 2) * G.nyp + bj) * G.Nt + n] = sacc;
     }
-    Ghat[((size_t)(G.nx / 2) * G.nyp + bj) * G.Nt + n] = s;
 }
 
 }  // namespace tp
@@ -487,14 +497,13 @@ cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, 
     const Geo& G = p.geo;
     __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(p.tp.work);
     __nv_bfloat16* Dt = At + (size_t)G.Nt * 2 * (tp::ROWS * tp::K);
-    tp::k_tp_prep<<<dim3((G.Nt + 15) / 16, tp::K / 4), 256, 0, s>>>(G, g, p.t.sens_fac, At);
+    float2* tl = reinterpret_cast<float2*>(Dt + (size_t)G.Nt * 4 * (tp::ROWS * tp::K));
+    tp::k_tp_prep<<<dim3((G.Nt + 15) / 16, tp::K / 4), 256, 0, s>>>(G, g, p.t.sens_fac, p.tp.exn, At, tl);
     tp::k_tp_gemm1<<<std::min(G.Nt, p.tp.sms), 128, tp_gemm1_smem(), s>>>(
         G, reinterpret_cast<const __nv_bfloat16*>(p.tp.ex), At, p.tp.eyf, Dt, Ghat, p.tp.err);
     tp::k_tp_gemm2<<<2 * std::max(1, p.tp.sms / 2), 192, tp_gemm2_smem(), s>>>(
         G, Dt, reinterpret_cast<const __nv_bfloat16*>(p.tp.ey), Ghat, p.tp.err);
-    float2* tl = reinterpret_cast<float2*>(Dt + (size_t)G.Nt * 4 * (tp::ROWS * tp::K));
-    tp::k_tp_nyq_t<<<dim3((G.Nt + 31) / 32, tp::K), 32, 0, s>>>(G, g, p.t.sens_fac, p.tp.exn, tl);
-    tp::k_tp_nyq_g<<<dim3((G.Nt + 31) / 32, G.nyp), 32, 0, s>>>(G, tl, p.tp.eyf, Ghat);
+    tp::k_tp_nyq_g<<<dim3((G.Nt + 31) / 32, 4), 256, 0, s>>>(G, tl, p.tp.eyf, Ghat);
     return cudaGetLastError();
 }
 
