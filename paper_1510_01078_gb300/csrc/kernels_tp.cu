@@ -174,123 +174,179 @@ __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __res
 }
 
 // ---------------------------------------------------------------------------
-// GEMM 1: persistent over n.  Ex (4 matrices: Re hi, Re lo, Im hi, Im lo;
-// rows jx = 0..127, K = a) stays in shared memory; per n the two matrices of
-// A (hi, lo; rows b) are loaded, 6 MMAs per K step of 16 accumulate D_re,
-// D_im (128 x 128 each) in tensor memory.  The epilogue writes D as BF16
-// hi/lo into the GEMM 2 operand tiles (per jx and n tile: rows n, K = b) and
-// sums the row jy = +ny/2 of G in FP32: G[jx, +ny/2, n] = sum_b Ey[+ny/2, b] D[jx, b].
+// GEMM 1: persistent and warp-specialised.  Ex (Re hi, Re lo, Im hi, Im lo;
+// rows jx = 0..127, K = a; 128 KB) stays in shared memory.  Warp 0 streams
+// each time sample's A (hi, lo; rows b) in K chunks of 64 (32 KB) through a
+// ring of STAGES buffers; warp 1 issues 6 MMAs (M 128, N 128) per K step of
+// 16 into one of two accumulator pairs (D_re, D_im; 256 columns each) in
+// tensor memory; warps 2-9 read a pair back (lane quarter = warp % 4, row
+// jx; warps 2-5 take b = 0..63, warps 6-9 b = 64..127) and write D as BF16
+// hi/lo into the GEMM 2 operand tiles (per jx and n tile: rows n, K = b).
+// Warps 2-5 also sum the row jy = +ny/2 of G in FP32:
+//   G[jx, +ny/2, n] = sum_b Ey[+ny/2, b] D[jx, b].
+// Waits are bounded as in GEMM 2.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 1) k_tp_gemm1(const Geo G, const __nv_bfloat16* __restrict__ Ex,
+__global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfloat16* __restrict__ Ex,
                                                      const __nv_bfloat16* __restrict__ At,
                                                      const float2* __restrict__ eyf,
                                                      __nv_bfloat16* __restrict__ Dt, float2* __restrict__ Ghat,
                                                      int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __nv_bfloat16* sEx = reinterpret_cast<__nv_bfloat16*>(smem);             // 4 x 32 KB
-    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem + 4 * MAT);    // 2 x 32 KB
-    __shared__ __align__(8) uint64_t load_bar, mma_bar;
+    unsigned char* sEx = smem;                                  // 4 x 32 KB
+    unsigned char* sA = smem + 4 * MAT;                         // STAGES x (hi, lo) chunks of 16 KB
+    __shared__ __align__(8) uint64_t ex_bar, full[STAGES], empty[STAGES], tfull[2], tempty[2], done_bar;
     __shared__ uint32_t taddr_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        bar_init(&load_bar, 1);
-        bar_init(&mma_bar, 1);
+        bar_init(&ex_bar, 1);
+        for (int s = 0; s < STAGES; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            bar_init(&tfull[a], 1);
+            bar_init(&tempty[a], 8);
+        }
+        bar_init(&done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
-                     "r"(256));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tD = taddr_s;                 // columns [0,128): Re, [128,256): Im
-    uint32_t lphase = 0, mphase = 0;
-    bool ok = true;
+    const uint32_t tacc = taddr_s;                              // pair a: Re at 256 a, Im at 256 a + 128
 
-    if (tid == 0) {
-        expect_tx(&load_bar, 4 * MAT);
-        for (int q = 0; q < 4; ++q) bulk_load(sEx + q * (MAT / 2), Ex + q * (MAT / 2), MAT, &load_bar);
-    }
-    ok = __syncthreads_and(bar_wait(&load_bar, lphase));
-    lphase ^= 1;
-
-    const uint32_t idesc = idesc_bf16(128);
-    for (int n = blockIdx.x; n < G.Nt && ok; n += gridDim.x) {
-        if (tid == 0) {
-            expect_tx(&load_bar, 2 * MAT);
-            bulk_load(sA, At + (size_t)n * 2 * (ROWS * K), 2 * MAT, &load_bar);
-        }
-        ok = __syncthreads_and(bar_wait(&load_bar, lphase));
-        lphase ^= 1;
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            const uint32_t ex = smem_u32(sEx), a = smem_u32(sA);
-            for (int c = 0; c < 2; ++c)
-                for (int s = 0; s < KC / 16; ++s) {
-                    const uint32_t off = c * CHUNK + s * 256;
-                    const uint64_t rh = sdesc(ex + 0 * MAT + off), rl = sdesc(ex + 1 * MAT + off);
-                    const uint64_t ih = sdesc(ex + 2 * MAT + off), il = sdesc(ex + 3 * MAT + off);
-                    const uint64_t ah = sdesc(a + 0 * MAT + off), al = sdesc(a + 1 * MAT + off);
-                    const uint32_t acc = (c | s) ? 1u : 0u;
-                    mma(tD, rh, ah, idesc, acc);
-                    mma(tD, rl, ah, idesc, 1u);
-                    mma(tD, rh, al, idesc, 1u);
-                    mma(tD + 128, ih, ah, idesc, acc);
-                    mma(tD + 128, il, ah, idesc, 1u);
-                    mma(tD + 128, ih, al, idesc, 1u);
+    if (warp == 0) {
+        if (lane == 0) {
+            expect_tx(&ex_bar, 4 * MAT);
+            for (int q = 0; q < 4; ++q) bulk_load(sEx + q * MAT, Ex + (size_t)q * (MAT / 2), MAT, &ex_bar);
+            int u = 0, last = -1;
+            bool ok = true;
+            for (int n = blockIdx.x; n < G.Nt && ok; n += gridDim.x) {
+                const __nv_bfloat16* an = At + (size_t)n * 2 * (ROWS * K);
+                for (int c = 0; c < 2; ++c, ++u) {
+                    const int s = u % STAGES;
+                    if (!bar_wait(&empty[s], ((u / STAGES) & 1) ^ 1)) {
+                        atomicExch(err, 1);
+                        ok = false;
+                        break;
+                    }
+                    expect_tx(&full[s], 2 * CHUNK);
+                    bulk_load(sA + s * 2 * CHUNK, an + c * (ROWS * KC), CHUNK, &full[s]);
+                    bulk_load(sA + s * 2 * CHUNK + CHUNK, an + ROWS * K + c * (ROWS * KC), CHUNK, &full[s]);
+                    last = u;
                 }
-            mma_commit(&mma_bar);
-        }
-        ok = __syncthreads_and(bar_wait(&mma_bar, mphase));
-        mphase ^= 1;
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: row jx = 32 warp + lane; columns b
-        const int jx = warp * 32 + lane;
-        const int ntn = G.Nt / TN, nr = n % TN;
-        __nv_bfloat16* out = Dt + ((size_t)jx * ntn + n / TN) * (DT_TILE / 2);
-        const float2* eyp = eyf + (size_t)G.ny * K;          // Ey row jy = +ny/2
-        float gr = 0.f, gi = 0.f;
-        for (int c0 = 0; c0 < 128; c0 += 32) {
-            uint32_t vr[32], vi[32];
-            tmem_ld32(tD + ((uint32_t)(warp * 32) << 16) + c0, vr);
-            tmem_ld32(tD + ((uint32_t)(warp * 32) << 16) + 128 + c0, vi);
-#pragma unroll
-            for (int g8 = 0; g8 < 4; ++g8) {
-                __align__(16) __nv_bfloat16 rh[8], rl[8], ih[8], il[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float dr = __uint_as_float(vr[g8 * 8 + j]), di = __uint_as_float(vi[g8 * 8 + j]);
-                    split_bf16(dr, rh[j], rl[j]);
-                    split_bf16(di, ih[j], il[j]);
-                    const float2 e = __ldg(&eyp[c0 + g8 * 8 + j]);
-                    gr = fmaf(e.x, dr, fmaf(-e.y, di, gr));
-                    gi = fmaf(e.x, di, fmaf(e.y, dr, gi));
-                }
-                const int off = tile_off(nr, c0 + g8 * 8, TN);
-                *reinterpret_cast<uint4*>(out + 0 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(rh);
-                *reinterpret_cast<uint4*>(out + 1 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(rl);
-                *reinterpret_cast<uint4*>(out + 2 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(ih);
-                *reinterpret_cast<uint4*>(out + 3 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(il);
             }
+            if (last >= 0) bar_wait(&full[last % STAGES], (last / STAGES) & 1);
+            bar_wait(&ex_bar, 0);
         }
-        Ghat[((size_t)jx * G.nyp + G.ny) * G.Nt + n] = make_float2(gr, gi);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    if (!ok) {
-        // a wait ran out: flag it, give the copies and MMAs in flight one more bounded wait
-        if (lane == 0) atomicExch(err, 1);
-        bar_wait(&load_bar, lphase);
-        bar_wait(&mma_bar, mphase);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = bar_wait(&ex_bar, 0);
+            const uint32_t id = idesc_bf16(128);
+            const uint64_t x0 = sdesc(smem_u32(sEx)), x1 = x0 + (MAT >> 4), x2 = x0 + 2 * (MAT >> 4),
+                           x3 = x0 + 3 * (MAT >> 4);
+            const uint64_t abase = sdesc(smem_u32(sA));
+            int q = 0, u = 0;
+            for (int n = blockIdx.x; n < G.Nt && ok; n += gridDim.x, ++q) {
+                const int a = q & 1;
+                if (!bar_wait(&tempty[a], ((q >> 1) & 1) ^ 1)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t tre = tacc + 256 * a, tim = tre + 128;
+                for (int c = 0; c < 2; ++c, ++u) {
+                    const int s = u % STAGES;
+                    if (!bar_wait(&full[s], (u / STAGES) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t ah = abase + (uint64_t)((s * 2 * CHUNK) >> 4), al = ah + (CHUNK >> 4);
+#pragma unroll
+                    for (int k = 0; k < KC / 16; ++k) {
+                        const uint64_t ox = (c * CHUNK + k * 256) >> 4, oa = (k * 256) >> 4;
+                        const uint32_t acc = (c | k) ? 1u : 0u;
+                        mma(tre, x0 + ox, ah + oa, id, acc);
+                        mma(tre, x1 + ox, ah + oa, id, 1u);
+                        mma(tre, x0 + ox, al + oa, id, 1u);
+                        mma(tim, x2 + ox, ah + oa, id, acc);
+                        mma(tim, x3 + ox, ah + oa, id, 1u);
+                        mma(tim, x2 + ox, al + oa, id, 1u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&tfull[a]);
+            }
+            if (!ok) atomicExch(err, 1);
+            mma_commit(&done_bar);
+            bar_wait(&done_bar, 0);
+        }
+    } else {
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        const int jx = quarter * 32 + lane;
+        const int ntn = G.Nt / TN;
+        const float2* eyp = eyf + (size_t)G.ny * K;             // Ey row jy = +ny/2
+        int q = 0;
+        for (int n = blockIdx.x; n < G.Nt; n += gridDim.x, ++q) {
+            const int a = q & 1;
+            if (!__all_sync(0xffffffffu, bar_wait(&tfull[a], (q >> 1) & 1))) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t trow = tacc + ((uint32_t)(quarter * 32) << 16) + 256 * a;
+            const int nr = n % TN;
+            __nv_bfloat16* out = Dt + ((size_t)jx * ntn + n / TN) * (DT_TILE / 2);
+            float gr = 0.f, gi = 0.f;
+            for (int c0 = 0; c0 < 128; c0 += 32) {
+                const bool mine = (c0 >> 6) == half;
+                if (!mine && half == 1) continue;               // warps 6-9: their own 64 columns only
+                uint32_t vr[32], vi[32];
+                tmem_ld32(trow + c0, vr);
+                tmem_ld32(trow + 128 + c0, vi);
+                if (half == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float dr = __uint_as_float(vr[j]), di = __uint_as_float(vi[j]);
+                        const float2 e = __ldg(&eyp[c0 + j]);
+                        gr = fmaf(e.x, dr, fmaf(-e.y, di, gr));
+                        gi = fmaf(e.x, di, fmaf(e.y, dr, gi));
+                    }
+                }
+                if (!mine) continue;
+#pragma unroll
+                for (int g8 = 0; g8 < 4; ++g8) {
+                    __align__(16) __nv_bfloat16 rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        split_bf16(__uint_as_float(vr[g8 * 8 + j]), rh[j], rl[j]);
+                        split_bf16(__uint_as_float(vi[g8 * 8 + j]), ih[j], il[j]);
+                    }
+                    {
+                        const int off = tile_off(nr, c0 + g8 * 8, TN);
+                        *reinterpret_cast<uint4*>(out + 0 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(rh);
+                        *reinterpret_cast<uint4*>(out + 1 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(rl);
+                        *reinterpret_cast<uint4*>(out + 2 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(ih);
+                        *reinterpret_cast<uint4*>(out + 3 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(il);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&tempty[a]);
+            if (half == 0) Ghat[((size_t)jx * G.nyp + G.ny) * G.Nt + n] = make_float2(gr, gi);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tD), "r"(256));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(512));
 }
 
 // ---------------------------------------------------------------------------
@@ -482,7 +538,7 @@ size_t tp_work_bytes(int Nt) {
     return (size_t)Nt * (2 + 4) * tp::MAT + (size_t)Nt * tp::K * sizeof(float2);
 }
 
-size_t tp_gemm1_smem() { return 6 * tp::MAT; }
+size_t tp_gemm1_smem() { return 4 * tp::MAT + tp::STAGES * 2 * tp::CHUNK; }
 size_t tp_gemm2_smem() { return 4 * tp::MAT + tp::STAGES * tp::DT_TILE; }
 
 cudaError_t configure_tp_kernels() {
@@ -499,7 +555,7 @@ cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, 
     __nv_bfloat16* Dt = At + (size_t)G.Nt * 2 * (tp::ROWS * tp::K);
     float2* tl = reinterpret_cast<float2*>(Dt + (size_t)G.Nt * 4 * (tp::ROWS * tp::K));
     tp::k_tp_prep<<<dim3((G.Nt + 15) / 16, tp::K / 4), 256, 0, s>>>(G, g, p.t.sens_fac, p.tp.exn, At, tl);
-    tp::k_tp_gemm1<<<std::min(G.Nt, p.tp.sms), 128, tp_gemm1_smem(), s>>>(
+    tp::k_tp_gemm1<<<std::min(G.Nt, p.tp.sms), 320, tp_gemm1_smem(), s>>>(
         G, reinterpret_cast<const __nv_bfloat16*>(p.tp.ex), At, p.tp.eyf, Dt, Ghat, p.tp.err);
     tp::k_tp_gemm2<<<2 * std::max(1, p.tp.sms / 2), 192, tp_gemm2_smem(), s>>>(
         G, Dt, reinterpret_cast<const __nv_bfloat16*>(p.tp.ey), Ghat, p.tp.err);
