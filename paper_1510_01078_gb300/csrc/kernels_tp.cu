@@ -9,9 +9,9 @@
 // i.e. two dense complex contractions, evaluated exactly (no window, no
 // oversampled grid) on the tensor cores:
 //   GEMM 1 (per n):       D[jx, b] = sum_a Ex[jx, a] A[b, a, n]     M = jx, N = b, K = a
-//   GEMM 2 (per jx):      G[jy, n] = sum_b Ey[jy, b] D[jx, b, n]    M = jy, N = n, K = b
-// GEMM 2 takes n as its N dimension so that every output row jy is a run of
-// contiguous time samples of Ghat.  Operands are BF16 with a hi + lo split of
+//   GEMM 2 (per jx):      G[jy, n] = sum_b D[jx, b, n] Ey[jy, b]    M = n, N = jy, K = b
+// GEMM 2 takes n as its M dimension so that every output column jy is a run
+// of contiguous time samples of Ghat.  Operands are BF16 with a hi + lo split of
 // every real factor (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)); each real
 // product is formed as hi*hi + lo*hi + hi*lo with FP32 accumulation in tensor
 // memory.  Shapes handled: nxs = nys = 128 sensors per axis, nx = ny = 256
@@ -42,11 +42,11 @@ constexpr int KC = 64;                 // K chunk
 constexpr int ROWS = 128;              // M and N of the main tiles
 constexpr uint32_t CHUNK = ROWS * KC * 2;          // 16 KB per (128-row matrix, chunk)
 constexpr uint32_t MAT = ROWS * K * 2;             // 32 KB per 128-row matrix
-constexpr int TN = 32;                              // time samples per GEMM 2 tile (its N)
-constexpr uint32_t DT_CHUNK = TN * KC * 2;          // 4 KB per (32-row matrix, chunk)
-constexpr uint32_t DT_MAT = TN * K * 2;             // 8 KB per 32-row matrix
-constexpr uint32_t DT_TILE = 4 * DT_MAT;            // D tile of one (jx, n tile): Re hi, Re lo, Im hi, Im lo
-constexpr int STAGES = 3;                           // GEMM 2 operand ring
+constexpr int TM = 128;                             // time samples per GEMM 2 tile (its M)
+constexpr int KA = 32;                              // K chunk of the GEMM 2 D tiles
+constexpr uint32_t DT_BLK = TM * KA * 2;            // 8 KB: one matrix of a D tile, one K chunk
+constexpr uint32_t DT_STAGE = 4 * DT_BLK;           // Re hi, Re lo, Im hi, Im lo of one K chunk
+constexpr int STAGES = 3;                           // operand ring of both GEMMs
 constexpr int WAIT_LIMIT = 1 << 26;    // iterations of a bounded mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -57,11 +57,14 @@ __device__ __forceinline__ int tile_off(int r, int k, int rows) {
     return c * rows * KC + (((r >> 3) * (KC >> 3) + (kk >> 3)) << 6) + ((r & 7) << 3) + (kk & 7);
 }
 
-// shared-memory matrix descriptor: K-major, no swizzle, LBO 128 B (along K), SBO 1024 B (8-row groups)
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+// shared-memory matrix descriptor: K-major, no swizzle, LBO 128 B (along K), SBO between 8-row groups
+__device__ __forceinline__ uint64_t sdesc_sbo(uint32_t saddr, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
            ((uint64_t)1 << 46);
 }
+
+// the same for K chunks of 64 (8-row groups 1024 B apart)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) { return sdesc_sbo(saddr, 1024); }
 
 // instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = n
 __host__ __device__ constexpr uint32_t idesc_bf16(int n) {
@@ -181,8 +184,8 @@ __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __res
 // 16 into one of two accumulator pairs (D_re, D_im; 256 columns each) in
 // tensor memory; warps 2-9 read a pair back (lane quarter = warp % 4, row
 // jx; warps 2-5 take b = 0..63, warps 6-9 b = 64..127) and write D as BF16
-// hi/lo into the GEMM 2 operand tiles (per jx and n tile: rows n, K = b).
-// Warps 2-5 also sum the row jy = +ny/2 of G in FP32:
+// hi/lo into the GEMM 2 operand tiles (per jx and tile of 128 time samples:
+// rows n, K = b, in K chunks of 32).  Warps 2-5 also sum the row jy = +ny/2 of G in FP32:
 //   G[jx, +ny/2, n] = sum_b Ey[+ny/2, b] D[jx, b].
 // Waits are bounded as in GEMM 2.
 // ---------------------------------------------------------------------------
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
     } else {
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         const int jx = quarter * 32 + lane;
-        const int ntn = G.Nt / TN;
+        const int ntn = G.Nt / TM;
         const float2* eyp = eyf + (size_t)G.ny * K;             // Ey row jy = +ny/2
         int q = 0;
         for (int n = blockIdx.x; n < G.Nt; n += gridDim.x, ++q) {
@@ -301,8 +304,8 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t trow = tacc + ((uint32_t)(quarter * 32) << 16) + 256 * a;
-            const int nr = n % TN;
-            __nv_bfloat16* out = Dt + ((size_t)jx * ntn + n / TN) * (DT_TILE / 2);
+            const int nr = n % TM;
+            __nv_bfloat16* out = Dt + ((size_t)jx * ntn + n / TM) * (4 * DT_STAGE / 2);
             float gr = 0.f, gi = 0.f;
             for (int c0 = 0; c0 < 128; c0 += 32) {
                 const bool mine = (c0 >> 6) == half;
@@ -329,11 +332,14 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
                         split_bf16(__uint_as_float(vi[g8 * 8 + j]), ih[j], il[j]);
                     }
                     {
-                        const int off = tile_off(nr, c0 + g8 * 8, TN);
-                        *reinterpret_cast<uint4*>(out + 0 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(rh);
-                        *reinterpret_cast<uint4*>(out + 1 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(rl);
-                        *reinterpret_cast<uint4*>(out + 2 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(ih);
-                        *reinterpret_cast<uint4*>(out + 3 * (DT_MAT / 2) + off) = *reinterpret_cast<uint4*>(il);
+                        // (row n, b) in K chunk b / 32: ((n / 8) * 4 + (b % 32) / 8) * 64 + (n % 8) * 8 + b % 8
+                        const int bb = c0 + g8 * 8;
+                        const int off = (bb >> 5) * (DT_STAGE / 2) + (((nr >> 3) * 4 + ((bb & 31) >> 3)) << 6) +
+                                        ((nr & 7) << 3);
+                        *reinterpret_cast<uint4*>(out + off + 0 * (DT_BLK / 2)) = *reinterpret_cast<uint4*>(rh);
+                        *reinterpret_cast<uint4*>(out + off + 1 * (DT_BLK / 2)) = *reinterpret_cast<uint4*>(rl);
+                        *reinterpret_cast<uint4*>(out + off + 2 * (DT_BLK / 2)) = *reinterpret_cast<uint4*>(ih);
+                        *reinterpret_cast<uint4*>(out + off + 3 * (DT_BLK / 2)) = *reinterpret_cast<uint4*>(il);
                     }
                 }
             }
@@ -350,19 +356,26 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
 }
 
 // ---------------------------------------------------------------------------
-// GEMM 2: persistent and warp-specialised.  A CTA owns one M tile of jy
+// GEMM 2: persistent and warp-specialised, with the time samples as M:
+//   G[jy, n] = sum_b D[jx, b, n] Ey[jy, b]   as   C[n, jy] = sum_b A[n, b] B[jy, b],
+// A = the D tile of (jx, 128 time samples), B = Ey, so that each MMA is
+// M 128 x N 128 x K 16 (a narrower N spends more shared-memory bandwidth on
+// re-reading the operands than on arithmetic) and each output column jy is
+// a run of contiguous time samples of Ghat.  A CTA owns one tile of jy
 // (blockIdx.x even: jy = -128..-1, odd: 0..127) and keeps that tile of Ey
 // (Re hi, Re lo, Im hi, Im lo; rows jy, K = b; 128 KB) in shared memory; it
-// loops over work items (jx, n tile of 32) shared out among the CTAs of its
-// tile.  Warp 0 streams the items' D tiles (32 KB, rows n) into a ring of
-// STAGES buffers; warp 1 issues 12 MMAs (M 128, N 32) per K step of 16:
-//   G_re = Ey_re D_re - Ey_im D_im,  G_im = Ey_re D_im + Ey_im D_re
+// loops over work items (jx, n tile) shared out among the CTAs of its tile.
+// Warp 0 streams each item's D tile in four K chunks of 32 (32 KB each, the
+// four matrices of a chunk contiguous) through a ring of STAGES buffers;
+// warp 1 issues 12 MMAs per K step of 16:
+//   G_re = D_re Ey_re - D_im Ey_im,  G_im = D_re Ey_im + D_im Ey_re
 // (the minus by the instruction's negate-A bit) into one of two accumulator
-// pairs in tensor memory; warps 2-5 read an accumulator pair back (lane
-// quarter = warp % 4, row jy) and write 32 contiguous time samples of Ghat
-// per row.  Every wait is bounded: a wait that runs out sets *err and the
-// role stops; the others then run out too, and the CTA waits for its own
-// copies and MMAs in flight before it frees tensor memory.
+// pairs in tensor memory (256 columns each); warps 2-5 read a pair back
+// (lane quarter = warp % 4 = time sample) and write, for every jy, 32
+// consecutive time samples per warp store.  Every wait is bounded: a wait
+// that runs out sets *err and the role stops; the others then run out too,
+// and the CTA waits for its own copies and MMAs in flight before it frees
+// tensor memory.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfloat16* __restrict__ Dt,
                                                      const __nv_bfloat16* __restrict__ Ey,
@@ -375,7 +388,7 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x & 1;
     const int slot = blockIdx.x >> 1, nslots = gridDim.x >> 1;
-    const int ntn = G.Nt / TN;
+    const int ntn = G.Nt / TM;
     const int items = K * ntn;                                  // jx = 0..127 x n tiles
 
     if (tid == 0) {
@@ -393,76 +406,87 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
-                     "r"(128));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tacc = taddr_s;                              // pair a: Re at 64 a, Im at 64 a + 32
+    const uint32_t tacc = taddr_s;                              // pair a: Re at 256 a, Im at 256 a + 128
 
     if (warp == 0) {
         if (lane == 0) {
             expect_tx(&ey_bar, 4 * MAT);
             for (int q = 0; q < 4; ++q)
                 bulk_load(sEy + q * MAT, Ey + (size_t)(tile * 4 + q) * (MAT / 2), MAT, &ey_bar);
-            int q = 0, last = -1;
-            for (int it = slot; it < items; it += nslots, ++q) {
-                const int s = q % STAGES;
-                if (!bar_wait(&empty[s], ((q / STAGES) & 1) ^ 1)) {
-                    atomicExch(err, 1);
-                    break;
+            int u = 0, last = -1;
+            bool ok = true;
+            for (int it = slot; it < items && ok; it += nslots) {
+                const __nv_bfloat16* src = Dt + (size_t)it * (4 * DT_STAGE / 2);   // item = jx * ntn + nt
+                for (int c = 0; c < 4; ++c, ++u) {
+                    const int s = u % STAGES;
+                    if (!bar_wait(&empty[s], ((u / STAGES) & 1) ^ 1)) {
+                        atomicExch(err, 1);
+                        ok = false;
+                        break;
+                    }
+                    expect_tx(&full[s], DT_STAGE);
+                    bulk_load(sD + s * DT_STAGE, src + c * (DT_STAGE / 2), DT_STAGE, &full[s]);
+                    last = u;
                 }
-                const int jx = it / ntn, nt = it - jx * ntn;
-                expect_tx(&full[s], DT_TILE);
-                bulk_load(sD + s * DT_TILE, Dt + ((size_t)jx * ntn + nt) * (DT_TILE / 2), DT_TILE, &full[s]);
-                last = q;
             }
-            // the copies issued last have landed before the CTA exits
             if (last >= 0) bar_wait(&full[last % STAGES], (last / STAGES) & 1);
             bar_wait(&ey_bar, 0);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = bar_wait(&ey_bar, 0);
-            const uint32_t id = idesc_bf16(TN), idn = id | (1u << 13);     // N = 32; negate A
+            const uint32_t id = idesc_bf16(128), idn = id | (1u << 13);    // M = N = 128; negate A
             // descriptors of the operand bases; a K step adds its byte offset / 16
             // to the start-address field (no carry: shared addresses < 2^18)
             const uint64_t e0 = sdesc(smem_u32(sEy)), e1 = e0 + (MAT >> 4), e2 = e0 + 2 * (MAT >> 4),
                            e3 = e0 + 3 * (MAT >> 4);
-            const uint64_t dbase = sdesc(smem_u32(sD));
-            int q = 0;
+            const uint64_t dbase = sdesc_sbo(smem_u32(sD), 512);
+            int q = 0, u = 0;
             for (int it = slot; it < items && ok; it += nslots, ++q) {
-                const int s = q % STAGES, a = q & 1;
-                if (!bar_wait(&tempty[a], ((q >> 1) & 1) ^ 1) || !bar_wait(&full[s], (q / STAGES) & 1)) {
+                const int a = q & 1;
+                if (!bar_wait(&tempty[a], ((q >> 1) & 1) ^ 1)) {
                     ok = false;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t d0 = dbase + (uint64_t)((s * DT_TILE) >> 4);
-                const uint32_t tre = tacc + 64 * a, tim = tre + 32;
-#pragma unroll
-                for (int c = 0; c < 2; ++c)
-#pragma unroll
-                    for (int k = 0; k < KC / 16; ++k) {
-                        const uint64_t oa = (c * CHUNK + k * 256) >> 4, ob = (c * DT_CHUNK + k * 256) >> 4;
-                        const uint64_t erh = e0 + oa, erl = e1 + oa, eih = e2 + oa, eil = e3 + oa;
-                        const uint64_t drh = d0 + ob, drl = d0 + (DT_MAT >> 4) + ob;
-                        const uint64_t dih = d0 + 2 * (DT_MAT >> 4) + ob, dil = d0 + 3 * (DT_MAT >> 4) + ob;
-                        const uint32_t acc = (c | k) ? 1u : 0u;
-                        mma(tre, erh, drh, id, acc);
-                        mma(tre, erl, drh, id, 1u);
-                        mma(tre, erh, drl, id, 1u);
-                        mma(tre, eih, dih, idn, 1u);
-                        mma(tre, eil, dih, idn, 1u);
-                        mma(tre, eih, dil, idn, 1u);
-                        mma(tim, erh, dih, id, acc);
-                        mma(tim, erl, dih, id, 1u);
-                        mma(tim, erh, dil, id, 1u);
-                        mma(tim, eih, drh, id, 1u);
-                        mma(tim, eil, drh, id, 1u);
-                        mma(tim, eih, drl, id, 1u);
+                const uint32_t tre = tacc + 256 * a, tim = tre + 128;
+                for (int c = 0; c < 4; ++c, ++u) {
+                    const int s = u % STAGES;
+                    if (!bar_wait(&full[s], (u / STAGES) & 1)) {
+                        ok = false;
+                        break;
                     }
-                mma_commit(&empty[s]);
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t d0 = dbase + (uint64_t)((s * DT_STAGE) >> 4);
+#pragma unroll
+                    for (int k = 0; k < KA / 16; ++k) {
+                        const int b0 = c * KA + k * 16;                         // first b of the K step
+                        const uint64_t oe = (uint64_t)(((b0 >> 6) * CHUNK + (b0 & 63) * 16) >> 4);
+                        const uint64_t od = (uint64_t)((k * 256) >> 4);
+                        const uint64_t drh = d0 + od, drl = d0 + (DT_BLK >> 4) + od;
+                        const uint64_t dih = d0 + 2 * (DT_BLK >> 4) + od, dil = d0 + 3 * (DT_BLK >> 4) + od;
+                        const uint64_t erh = e0 + oe, erl = e1 + oe, eih = e2 + oe, eil = e3 + oe;
+                        const uint32_t acc = (c | k) ? 1u : 0u;
+                        mma(tre, drh, erh, id, acc);
+                        mma(tre, drl, erh, id, 1u);
+                        mma(tre, drh, erl, id, 1u);
+                        mma(tre, dih, eih, idn, 1u);
+                        mma(tre, dil, eih, idn, 1u);
+                        mma(tre, dih, eil, idn, 1u);
+                        mma(tim, drh, eih, id, acc);
+                        mma(tim, drl, eih, id, 1u);
+                        mma(tim, drh, eil, id, 1u);
+                        mma(tim, dih, erh, id, 1u);
+                        mma(tim, dil, erh, id, 1u);
+                        mma(tim, dih, erl, id, 1u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
                 mma_commit(&tfull[a]);
             }
             if (!ok) atomicExch(err, 1);
@@ -472,7 +496,7 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
         }
     } else {
         const int quarter = warp & 3;                           // TMEM lanes 32 quarter .. + 31
-        const int b = tile * K + quarter * 32 + lane;           // Ghat row: jy + ny/2
+        const int row = quarter * 32 + lane;                    // time sample within the tile
         int q = 0;
         for (int it = slot; it < items; it += nslots, ++q) {
             const int a = q & 1;
@@ -481,25 +505,26 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint32_t vr[32], vi[32];
-            const uint32_t ta = tacc + ((uint32_t)(quarter * 32) << 16) + 64 * a;
-            tmem_ld32(ta, vr);
-            tmem_ld32(ta + 32, vi);
+            const int jx = it / ntn, nt = it - jx * ntn;
+            float2* o = Ghat + ((size_t)jx * G.nyp + tile * K) * G.Nt + nt * TM + row;   // column jy: + jy * Nt
+            const uint32_t ta = tacc + ((uint32_t)(quarter * 32) << 16) + 256 * a;
+            for (int j0 = 0; j0 < 128; j0 += 32) {
+                uint32_t vr[32], vi[32];
+                tmem_ld32(ta + j0, vr);
+                tmem_ld32(ta + 128 + j0, vi);
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    o[(size_t)(j0 + j) * G.Nt] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+            }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(&tempty[a]);
-            const int jx = it / ntn, nt = it - jx * ntn;
-            float4* o = reinterpret_cast<float4*>(Ghat + ((size_t)jx * G.nyp + b) * G.Nt + nt * TN);
-#pragma unroll
-            for (int j = 0; j < TN / 2; ++j)
-                o[j] = make_float4(__uint_as_float(vr[2 * j]), __uint_as_float(vi[2 * j]), __uint_as_float(vr[2 * j + 1]),
-                                   __uint_as_float(vi[2 * j + 1]));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(128));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(512));
 }
 
 // ---------------------------------------------------------------------------
@@ -539,7 +564,7 @@ size_t tp_work_bytes(int Nt) {
 }
 
 size_t tp_gemm1_smem() { return 4 * tp::MAT + tp::STAGES * 2 * tp::CHUNK; }
-size_t tp_gemm2_smem() { return 4 * tp::MAT + tp::STAGES * tp::DT_TILE; }
+size_t tp_gemm2_smem() { return 4 * tp::MAT + tp::STAGES * tp::DT_STAGE; }
 
 cudaError_t configure_tp_kernels() {
     cudaError_t e;

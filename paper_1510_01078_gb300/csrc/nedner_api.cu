@@ -97,7 +97,7 @@ nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
                 return NEDNER_EINVAL;
         }
     const size_t MATE = (size_t)NS * NS;               // elements of a 128-row matrix
-    if (G.Nt < 32) return NEDNER_EINVAL;                // GEMM 2 tiles hold 32 time samples
+    if (G.Nt < 128) return NEDNER_EINVAL;               // GEMM 2 tiles hold 128 time samples
     std::vector<uint16_t> ex(4 * MATE), ey(2 * 4 * MATE, 0);
     for (int jx = 0; jx < NS; ++jx)
         for (int a = 0; a < NS; ++a) {
