@@ -137,26 +137,27 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __restrict__ g,
                                                  const float* __restrict__ fac, const float2* __restrict__ exn,
-                                                 __nv_bfloat16* __restrict__ At, float2* __restrict__ t) {
+                                                 __nv_bfloat16* __restrict__ At, float2* __restrict__ t, int nb,
+                                                 int ne) {
     __shared__ float tile[4 * K][17];
-    const int n0 = blockIdx.x * 16;
+    const int n0 = nb + blockIdx.x * 16;
     const int b0 = blockIdx.y * 4;
     for (int i = threadIdx.x; i < 4 * K * 16; i += blockDim.x) {
         const int r = i >> 4, c = i & 15;                   // r = (b - b0) * K + a
         const int m = (b0 + (r >> 7)) * K + (r & 127);
-        tile[r][c] = (n0 + c < G.Nt) ? fac[m] * g[(size_t)m * G.Nt + n0 + c] : 0.f;
+        tile[r][c] = (n0 + c < ne) ? fac[m] * g[(size_t)m * G.Nt + n0 + c] : 0.f;
     }
     __syncthreads();
     // items: 16 n x 4 b x 16 groups of 8 a
     for (int it = threadIdx.x; it < 16 * 4 * 16; it += blockDim.x) {
         const int c = it >> 6, rb = (it >> 4) & 3, ag = it & 15;
         const int n = n0 + c;
-        if (n >= G.Nt) continue;
+        if (n >= ne) continue;
         __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) split_bf16(tile[rb * K + ag * 8 + j][c], hi[j], lo[j]);
         const int off = tile_off(b0 + rb, ag * 8, ROWS);
-        __nv_bfloat16* base = At + (size_t)n * 2 * (ROWS * K);
+        __nv_bfloat16* base = At + (size_t)(n - nb) * 2 * (ROWS * K);
         *reinterpret_cast<uint4*>(base + off) = *reinterpret_cast<uint4*>(hi);
         *reinterpret_cast<uint4*>(base + ROWS * K + off) = *reinterpret_cast<uint4*>(lo);
     }
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __res
             sacc.x = fmaf(e.x, v, sacc.x);
             sacc.y = fmaf(e.y, v, sacc.y);
         }
-        if (n < G.Nt) t[(size_t)(b0 + rb) * G.Nt + n] = sacc;
+        if (n < ne) t[(size_t)(b0 + rb) * G.Nt + n] = sacc;
     }
 }
 
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
                                                      const __nv_bfloat16* __restrict__ At,
                                                      const float2* __restrict__ eyf,
                                                      __nv_bfloat16* __restrict__ Dt, float2* __restrict__ Ghat,
-                                                     int* __restrict__ err) {
+                                                     int* __restrict__ err, int nb, int ne) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sEx = smem;                                  // 4 x 32 KB
     unsigned char* sA = smem + 4 * MAT;                         // STAGES x (hi, lo) chunks of 16 KB
@@ -229,8 +230,8 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
             for (int q = 0; q < 4; ++q) bulk_load(sEx + q * MAT, Ex + (size_t)q * (MAT / 2), MAT, &ex_bar);
             int u = 0, last = -1;
             bool ok = true;
-            for (int n = blockIdx.x; n < G.Nt && ok; n += gridDim.x) {
-                const __nv_bfloat16* an = At + (size_t)n * 2 * (ROWS * K);
+            for (int n = nb + blockIdx.x; n < ne && ok; n += gridDim.x) {
+                const __nv_bfloat16* an = At + (size_t)(n - nb) * 2 * (ROWS * K);
                 for (int c = 0; c < 2; ++c, ++u) {
                     const int s = u % STAGES;
                     if (!bar_wait(&empty[s], ((u / STAGES) & 1) ^ 1)) {
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
                            x3 = x0 + 3 * (MAT >> 4);
             const uint64_t abase = sdesc(smem_u32(sA));
             int q = 0, u = 0;
-            for (int n = blockIdx.x; n < G.Nt && ok; n += gridDim.x, ++q) {
+            for (int n = nb + blockIdx.x; n < ne && ok; n += gridDim.x, ++q) {
                 const int a = q & 1;
                 if (!bar_wait(&tempty[a], ((q >> 1) & 1) ^ 1)) {
                     ok = false;
@@ -293,10 +294,10 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
     } else {
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         const int jx = quarter * 32 + lane;
-        const int ntn = G.Nt / TM;
+        const int ntn = (ne - nb) / TM;
         const float2* eyp = eyf + (size_t)G.ny * K;             // Ey row jy = +ny/2
         int q = 0;
-        for (int n = blockIdx.x; n < G.Nt; n += gridDim.x, ++q) {
+        for (int n = nb + blockIdx.x; n < ne; n += gridDim.x, ++q) {
             const int a = q & 1;
             if (!__all_sync(0xffffffffu, bar_wait(&tfull[a], (q >> 1) & 1))) {
                 if (lane == 0) atomicExch(err, 1);
@@ -304,8 +305,8 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t trow = tacc + ((uint32_t)(quarter * 32) << 16) + 256 * a;
-            const int nr = n % TM;
-            __nv_bfloat16* out = Dt + ((size_t)jx * ntn + n / TM) * (4 * DT_STAGE / 2);
+            const int nr = (n - nb) % TM;
+            __nv_bfloat16* out = Dt + ((size_t)jx * ntn + (n - nb) / TM) * (4 * DT_STAGE / 2);
             float gr = 0.f, gi = 0.f;
             for (int c0 = 0; c0 < 128; c0 += 32) {
                 const bool mine = (c0 >> 6) == half;
@@ -379,7 +380,8 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfloat16* __restrict__ Dt,
                                                      const __nv_bfloat16* __restrict__ Ey,
-                                                     float2* __restrict__ Ghat, int* __restrict__ err) {
+                                                     float2* __restrict__ Ghat, int* __restrict__ err, int nb,
+                                                     int ne) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sEy = smem;                                  // 4 x 32 KB
     unsigned char* sD = smem + 4 * MAT;                         // STAGES x 32 KB
@@ -388,8 +390,8 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x & 1;
     const int slot = blockIdx.x >> 1, nslots = gridDim.x >> 1;
-    const int ntn = G.Nt / TM;
-    const int items = K * ntn;                                  // jx = 0..127 x n tiles
+    const int ntn = (ne - nb) / TM;
+    const int items = K * ntn;                                  // jx = 0..127 x n tiles of [nb, ne)
 
     if (tid == 0) {
         bar_init(&ey_bar, 1);
@@ -506,7 +508,7 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int jx = it / ntn, nt = it - jx * ntn;
-            float2* o = Ghat + ((size_t)jx * G.nyp + tile * K) * G.Nt + nt * TM + row;   // column jy: + jy * Nt
+            float2* o = Ghat + ((size_t)jx * G.nyp + tile * K) * G.Nt + nb + nt * TM + row;   // column jy: + jy * Nt
             const uint32_t ta = tacc + ((uint32_t)(quarter * 32) << 16) + 256 * a;
             for (int j0 = 0; j0 < 128; j0 += 32) {
                 uint32_t vr[32], vi[32];
@@ -558,9 +560,14 @@ __global__ void __launch_bounds__(256) k_tp_nyq_g(const Geo G, const float2* __r
 
 }  // namespace tp
 
+// time samples per pass of the tensor-product stage: the GEMM 2 operand
+// tiles of one pass (128 KB per time sample) stay in L2 between the GEMMs
+int tp_chunk(int Nt) { return Nt < 512 ? Nt : 512; }
+
 size_t tp_work_bytes(int Nt) {
-    // data operands (hi, lo) + GEMM 1 output (4 matrices) per n, plus the Nyquist-line partial sums
-    return (size_t)Nt * (2 + 4) * tp::MAT + (size_t)Nt * tp::K * sizeof(float2);
+    // data operands (hi, lo) + GEMM 1 output (4 matrices) per time sample of a
+    // pass, plus the Nyquist-line partial sums of all time samples
+    return (size_t)tp_chunk(Nt) * (2 + 4) * tp::MAT + (size_t)Nt * tp::K * sizeof(float2);
 }
 
 size_t tp_gemm1_smem() { return 4 * tp::MAT + tp::STAGES * 2 * tp::CHUNK; }
@@ -577,13 +584,17 @@ cudaError_t configure_tp_kernels() {
 cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, cudaStream_t s) {
     const Geo& G = p.geo;
     __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(p.tp.work);
-    __nv_bfloat16* Dt = At + (size_t)G.Nt * 2 * (tp::ROWS * tp::K);
-    float2* tl = reinterpret_cast<float2*>(Dt + (size_t)G.Nt * 4 * (tp::ROWS * tp::K));
-    tp::k_tp_prep<<<dim3((G.Nt + 15) / 16, tp::K / 4), 256, 0, s>>>(G, g, p.t.sens_fac, p.tp.exn, At, tl);
-    tp::k_tp_gemm1<<<std::min(G.Nt, p.tp.sms), 320, tp_gemm1_smem(), s>>>(
-        G, reinterpret_cast<const __nv_bfloat16*>(p.tp.ex), At, p.tp.eyf, Dt, Ghat, p.tp.err);
-    tp::k_tp_gemm2<<<2 * std::max(1, p.tp.sms / 2), 192, tp_gemm2_smem(), s>>>(
-        G, Dt, reinterpret_cast<const __nv_bfloat16*>(p.tp.ey), Ghat, p.tp.err);
+    const int ch = tp_chunk(G.Nt);
+    __nv_bfloat16* Dt = At + (size_t)ch * 2 * (tp::ROWS * tp::K);
+    float2* tl = reinterpret_cast<float2*>(Dt + (size_t)ch * 4 * (tp::ROWS * tp::K));
+    for (int nb = 0; nb < G.Nt; nb += ch) {
+        const int ne = nb + ch;
+        tp::k_tp_prep<<<dim3(ch / 16, tp::K / 4), 256, 0, s>>>(G, g, p.t.sens_fac, p.tp.exn, At, tl, nb, ne);
+        tp::k_tp_gemm1<<<std::min(ch, p.tp.sms), 320, tp_gemm1_smem(), s>>>(
+            G, reinterpret_cast<const __nv_bfloat16*>(p.tp.ex), At, p.tp.eyf, Dt, Ghat, p.tp.err, nb, ne);
+        tp::k_tp_gemm2<<<2 * std::max(1, p.tp.sms / 2), 192, tp_gemm2_smem(), s>>>(
+            G, Dt, reinterpret_cast<const __nv_bfloat16*>(p.tp.ey), Ghat, p.tp.err, nb, ne);
+    }
     tp::k_tp_nyq_g<<<dim3((G.Nt + 31) / 32, 4), 256, 0, s>>>(G, tl, p.tp.eyf, Ghat);
     return cudaGetLastError();
 }
