@@ -595,7 +595,7 @@ cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, 
         tp::k_tp_gemm2<<<2 * std::max(1, p.tp.sms / 2), 192, tp_gemm2_smem(), s>>>(
             G, Dt, reinterpret_cast<const __nv_bfloat16*>(p.tp.ey), Ghat, p.tp.err, nb, ne);
     }
-    tp::k_tp_nyq_g<<<dim3((G.Nt + 31) / 32, 4), 256, 0, s>>>(G, tl, p.tp.eyf, Ghat);
+    tp::k_tp_nyq_g<<<dim3((G.Nt + 31) / 32, (G.nyp + 7) / 8), 256, 0, s>>>(G, tl, p.tp.eyf, Ghat);
     return cudaGetLastError();
 }
 
