@@ -37,10 +37,12 @@ struct Chunks {
     int tpl1;      // time samples per lane in the spread stage (1 or 2)
     int ca;        // time samples per CTA in the transposed interpolation stage
     int smax;      // sensors per task in the transposed interpolation stage
+    int per_adj;   // values per thread in its in-place row FFT (16 or 32)
+    int tp_adj;    // time samples per pass of the transposed gather (its entry buffer holds M w tp_adj floats)
     int lpc;       // line groups per CTA in the NER stage
     int threads3;  // threads per CTA in the NER stage
     size_t smem1, smem2, smem2f, smem3, smem4, smem5;
-    size_t smem_interp, smem_grad, smem3a;
+    size_t smem_adj, smem_grad, smem3a;
 };
 
 constexpr int kRowBlock = 16;   // grid rows per block of the transposed interpolation
@@ -80,6 +82,12 @@ struct DevTables {
     int* xent_m = nullptr;        // [E'] sensor
     float* xent_wx = nullptr;     // [E'][spread_taps(w)] taps from column xent_bx on (x tap times y tap times sensor factor)
     int* xent_bx = nullptr;       // [E'] first x column rounded down to a multiple of 4
+    float* xent_gx = nullptr;     // [E'][spread_taps(w)] x-tap derivative times y tap times sensor factor
+    float* xent_gy = nullptr;     // [E'][spread_taps(w)] x tap times y-tap derivative times sensor factor
+    int* xent_loc = nullptr;      // [E'] index of the entry's sensor in its row block's band
+    int* xrow_first = nullptr;    // [Ly] first entry of the row that is not a wrapped entry's second copy
+    int* xent_rc = nullptr;       // [E'] the entry's index in the row CSR
+    int* sens_ent = nullptr;      // [M][w] row-CSR index of each of the sensor's y taps
     int4* seg = nullptr;          // [Ly][groups1] column range [x, y) and entry range [z, w)
     // transposed interpolation: sensors touching each block of kRowBlock rows
     int* band_m = nullptr;        // [B] sensor
@@ -137,10 +145,9 @@ cudaError_t launch_img_xr2c_adj(const nedner_plan_s& p, const float* p0, float2*
 cudaError_t launch_img_yfft_adj(const nedner_plan_s& p, const float2* Y, float2* V, cudaStream_t s);
 cudaError_t launch_ner_lines_adj(const nedner_plan_s& p, const float2* V, float2* Ghat, cudaStream_t s);
 cudaError_t launch_ned_yfft_adj(const nedner_plan_s& p, const float2* Ghat, float2* R, cudaStream_t s);
-cudaError_t launch_ned_interp_adj(const nedner_plan_s& p, const float2* R, float* P, cudaStream_t s);
-cudaError_t launch_adj_finish(const nedner_plan_s& p, const float* P, float* g, cudaStream_t s);
-cudaError_t launch_ned_grad(const nedner_plan_s& p, const float2* R, const float* g, float2* Q, cudaStream_t s);
-cudaError_t launch_grad_finish(const nedner_plan_s& p, const float2* Q, float* dxy, cudaStream_t s);
+cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E, float* g, cudaStream_t s);
+cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const float* g, float2* Qe, float* dxy,
+                               cudaStream_t s);
 cudaError_t configure_adj_kernels(const nedner_plan_s& p);
 
 // tensor-product NED (kernels_tp.cu)

@@ -259,209 +259,225 @@ __global__ void __launch_bounds__(256) k_ned_yfft_adj(Geo G, int C, const float2
 }
 
 // ---------------------------------------------------------------------------
-// Transpose of the x part of ned_spread_xfft for one grid row: the real row
-//   r[gx] = Re sum_{jx=0}^{nx/2} R[jx] exp(+2 pi i jx gx / Lx) / phihat(jx/Lx)
+// Transpose of the x part of the spread stage for one grid row: the real row
+//   r[gx][t] = Re sum_{jx=0}^{nx/2} R[jx][t] exp(+2 pi i jx gx / Lx) / phihat(jx/Lx)
 // for C time samples, as the inverse FFT of the Hermitian part of the
-// zero-extended spectrum (two real columns packed per complex column).
-// Leaves r as floats [Lx][C] in the returned buffer.
+// zero-extended spectrum, two real samples packed per complex column.  Z is
+// the padded [Lx][C/2] complex row (see block_fft_ip); on return the real
+// value (gx, t) is at ((float*)Z)[2 padx(gx C/2 + t/2) + t%2].
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float* row_real_ifft(const Geo& G, int C, const float2* __restrict__ R, int gy, int n0,
-                                                const float* __restrict__ deconv_x, const float2* __restrict__ tw,
-                                                float2* Z, float2* Zs) {
+constexpr int ADJ_ECH = 128;                     // entries staged at a time by the transposed kernels
+#define smax smax
+
+template <int PER>
+__device__ __forceinline__ void row_rebuild(const Geo& G, int C, const float2* __restrict__ R, int gy, int n0,
+                                            const float* __restrict__ deconv_x, const float2* __restrict__ tw,
+                                            float2* Z) {
     const int Lx = G.Lx;
     const int nb = C / 2;
     const int lnb = ilog2(nb);
-    for (int it = threadIdx.x; it < Lx * nb; it += blockDim.x) Z[it] = make_float2(0.f, 0.f);
-    __syncthreads();
-#pragma unroll 4
-    for (int it = threadIdx.x; it < G.nxh * nb; it += blockDim.x) {
-        const int jx = it >> lnb;
+    const int half = G.nx / 2;
+    for (int it = threadIdx.x; it < (Lx << lnb); it += blockDim.x) {
+        const int k = it >> lnb;
         const int b = it & (nb - 1);
-        const float d = __ldg(&deconv_x[jx]);
-        const float2* src = R + ((size_t)jx * G.Ly + gy) * G.Nt + n0 + 2 * b;
-        const float2 y1 = cscale(src[0], d);
-        const float2 y2 = cscale(src[1], d);
-        if (jx == 0) {
-            Z[b] = make_float2(y1.x, y2.x);                       // Re Y1[0] + i Re Y2[0]
-        } else {
-            // H[k] = Y[k]/2, H[Lx-k] = conj(Y[k])/2; Z = H1 + i H2
-            Z[jx * nb + b] = cscale(cadd(y1, mul_i(y2, +1)), 0.5f);
-            Z[(Lx - jx) * nb + b] = cscale(cadd(cconj(y1), mul_i(cconj(y2), +1)), 0.5f);
+        float2 z = make_float2(0.f, 0.f);
+        const int jx = (k <= half) ? k : ((k >= Lx - half) ? Lx - k : -1);
+        if (jx >= 0) {
+            const float d = __ldg(&deconv_x[jx]);
+            const float2* src = R + ((size_t)jx * G.Ly + gy) * G.Nt + n0 + 2 * b;
+            const float2 y1 = cscale(src[0], d);
+            const float2 y2 = cscale(src[1], d);
+            if (k == 0) z = make_float2(y1.x, y2.x);                                   // Re Y1[0] + i Re Y2[0]
+            else if (k <= half) z = cscale(cadd(y1, mul_i(y2, +1)), 0.5f);              // H[k] = Y[k] / 2
+            else z = cscale(cadd(cconj(y1), mul_i(cconj(y2), +1)), 0.5f);               // H[Lx-k] = conj Y[k] / 2
+        }
+        Z[padx(it)] = z;
+    }
+    block_fft_ip<PER>(Z, Lx, nb, +1, tw);
+}
+
+// float offset of real sample (column c, time sample ln) in the padded row:
+// 2 padx(c C/2 + ln/2) + ln%2
+__device__ __forceinline__ int rpos(int c, int lnb, int ln) { return 2 * padx((c << lnb) + (ln >> 1)) + (ln & 1); }
+
+// Register window of the rebuilt row for one lane: win[k] = r[(base + k) mod Lx],
+// k < 2 WT.  A lane group walks entries sorted by first column; an entry
+// more than WT columns ahead of base first slides the window by WT.
+template <int WT>
+__device__ __forceinline__ void win_load(float (&win)[2 * WT], const float* Zf, int lnb, int ln, int Lx, int base,
+                                         int k0) {
+#pragma unroll
+    for (int k = 0; k < WT; ++k) win[k0 + k] = Zf[rpos((base + k0 + k) & (Lx - 1), lnb, ln)];
+}
+
+template <int WT>
+__device__ __forceinline__ void win_advance(float (&win)[2 * WT], const float* Zf, int lnb, int ln, int Lx, int& base,
+                                            int bx4) {
+    while (bx4 - base > WT) {
+#pragma unroll
+        for (int k = 0; k < WT; ++k) win[k] = win[k + WT];
+        base += WT;
+        win_load<WT>(win, Zf, lnb, ln, Lx, base, WT);
+    }
+}
+
+// sum_k taps[k] win[D + k] (two tap sets at once when TWO)
+template <int WT, int D, bool TWO>
+__device__ __forceinline__ float2 win_dot(const float (&win)[2 * WT], const float4* ta, const float4* tb) {
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+    for (int k4 = 0; k4 < WT / 4; ++k4) {
+        const float4 t4 = ta[k4];
+        a0 = fmaf(t4.x, win[D + 4 * k4 + 0], a0);
+        a1 = fmaf(t4.y, win[D + 4 * k4 + 1], a1);
+        a0 = fmaf(t4.z, win[D + 4 * k4 + 2], a0);
+        a1 = fmaf(t4.w, win[D + 4 * k4 + 3], a1);
+        if (TWO) {
+            const float4 u4 = tb[k4];
+            b0 = fmaf(u4.x, win[D + 4 * k4 + 0], b0);
+            b1 = fmaf(u4.y, win[D + 4 * k4 + 1], b1);
+            b0 = fmaf(u4.z, win[D + 4 * k4 + 2], b0);
+            b1 = fmaf(u4.w, win[D + 4 * k4 + 3], b1);
         }
     }
-    return reinterpret_cast<float*>(block_fft(Z, Zs, Lx, nb, nb, +1, tw));
+    return make_float2(a0 + a1, b0 + b1);
+}
+
+// the entry at bx4 = base + 4 d, d = 0 .. WT/4 (uniform across the lane group)
+template <int WT, bool TWO>
+__device__ __forceinline__ float2 win_entry(const float (&win)[2 * WT], int d, const float4* ta, const float4* tb) {
+    if (d == 0) return win_dot<WT, 0, TWO>(win, ta, tb);
+    if (d == 1) return win_dot<WT, 4, TWO>(win, ta, tb);
+    if (d == 2) return win_dot<WT, (WT >= 8 ? 8 : 0), TWO>(win, ta, tb);
+    if (WT >= 12 && d == 3) return win_dot<WT, (WT >= 12 ? 12 : 0), TWO>(win, ta, tb);
+    if (WT >= 16 && d == 4) return win_dot<WT, (WT >= 16 ? 16 : 0), TWO>(win, ta, tb);
+    return win_dot<WT, (WT >= 20 ? 20 : 0), TWO>(win, ta, tb);
 }
 
 // ---------------------------------------------------------------------------
-// Transposed interpolation: one CTA per (task, C time samples).  A task is a
-// block of kRowBlock grid rows and a slice [s0, s1) of the sensors touching
-// it.  For each row the CTA rebuilds the real row r (row_real_ifft), then for
-// every (sensor, y tap) entry of the row whose sensor is in the slice adds
-//   row_w * sum_k wx[m][k] r[(bx_m + k) mod Lx]
-// to that sensor's accumulator.  A sensor's rows span at most two blocks; the
-// partial of each block goes to P[slot][m][n] (slot 0 = block of its first
-// row) and adj_finish adds them.
+// Transposed interpolation (the transpose of the spread stage's x and y
+// parts) and the position gradient, one CTA per (grid row gy, C time
+// samples) as in the forward spread.  The CTA rebuilds the real row r
+// (row_rebuild), stages the row's entries (sorted by first column, without
+// the second copies of wrapped entries) in chunks, and each lane group
+// sweeps a contiguous run of a chunk with a register window of the row (the
+// forward sweep, transposed): every entry gets
+//   v[t] = sum_k tap[k] r[(bx4 + k) mod Lx][t]
+// with the forward spread's taps (x tap times y tap times w_m, from a
+// 4-aligned column).
+//   adjoint:  E[e][t - nb] = v[t], e the entry's index in the row CSR, for the
+//             pass of time samples [nb, nb + Tp); adj_sum adds each sensor's
+//             w entries (no atomics, fixed order).
+//   gradient: the two derivative tap sets give v_x, v_y; the entry's
+//             sum_t g[m][t] (v_x[t], v_y[t]) over the C samples goes to
+//             Qe[e][time chunk]; grad_sum adds entries and chunks per sensor.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ned_interp_adj(Geo G, int C, int smax, const float2* __restrict__ R,
-                                                        const int4* __restrict__ tasks,
-                                                        const int* __restrict__ row_ptr,
-                                                        const int* __restrict__ row_m,
-                                                        const float* __restrict__ row_w,
-                                                        const int* __restrict__ row_local,
-                                                        const int* __restrict__ band_m,
-                                                        const int* __restrict__ band_slot,
-                                                        const int* __restrict__ sens_bx,
-                                                        const float* __restrict__ sens_wx,
-                                                        const float* __restrict__ deconv_x,
-                                                        const float2* __restrict__ tw, float* __restrict__ P) {
+template <int WT, int PER, bool GRAD>
+__global__ void __launch_bounds__(256, 2) k_ned_gather_rows(Geo G, int C, int nb, int Tp,
+                                                            const float2* __restrict__ R,
+                                                            const float* __restrict__ g,
+                                                            const int* __restrict__ xrow_ptr,
+                                                            const int* __restrict__ xrow_first,
+                                                            const int* __restrict__ xent_m,
+                                                            const int* __restrict__ xent_bx,
+                                                            const int* __restrict__ xent_rc,
+                                                            const float* __restrict__ taps_a,
+                                                            const float* __restrict__ taps_b,
+                                                            const float* __restrict__ deconv_x,
+                                                            const float2* __restrict__ tw, float* __restrict__ E,
+                                                            float2* __restrict__ Qe) {
     extern __shared__ float4 smem4[];
-    float2* Z = reinterpret_cast<float2*>(smem4);            // [Lx][C/2]
-    float2* Zs = Z + (size_t)G.Lx * (C / 2);                 // [Lx][C/2]
-    float* acc = reinterpret_cast<float*>(Zs + (size_t)G.Lx * (C / 2));   // [smax][C]
-    const int4 tk = tasks[blockIdx.x];                       // block, s0, s1, band start of block
-    const int n0 = blockIdx.y * C;
-    const int nloc = tk.z - tk.y;
-    const int off = tk.y - tk.w;                             // first local index of this slice
-    const int lc = ilog2(C);
+    float2* Z = reinterpret_cast<float2*>(smem4);                    // padded [Lx][C/2]
+    const float* Zf = reinterpret_cast<const float*>(Z);
+    float4* s_ta = reinterpret_cast<float4*>(Z + ((padded_len(G.Lx * (C / 2)) + 1) & ~1));   // [ADJ_ECH][WT/4]
+    float4* s_tb = s_ta + ADJ_ECH * (WT / 4);                         // [ADJ_ECH][WT/4] (GRAD)
+    float* s_g = reinterpret_cast<float*>(s_tb + (GRAD ? ADJ_ECH * (WT / 4) : 0));   // [ADJ_ECH][C] (GRAD)
+    int* s_bx = reinterpret_cast<int*>(s_g + (GRAD ? ADJ_ECH * C : 0));              // [ADJ_ECH]
+    int* s_rc = s_bx + ADJ_ECH;                                                        // [ADJ_ECH]
+    const int gy = blockIdx.x;
+    const int n0 = nb + blockIdx.y * C;
+    const int lc = ilog2(C), lnb = lc - 1;
     const int groups = blockDim.x >> lc;
     const int q = threadIdx.x >> lc;
     const int ln = threadIdx.x & (C - 1);
     const int Lx = G.Lx;
+    const unsigned gmask = (C >= 32) ? 0xffffffffu : (((1u << C) - 1u) << ((threadIdx.x & 31) - ln));
+    const int nch = G.Nt / C;
 
-    for (int i = threadIdx.x; i < nloc * C; i += blockDim.x) acc[i] = 0.f;
-    for (int rr = 0; rr < kRowBlock; ++rr) {
-        const int gy = tk.x * kRowBlock + rr;
-        const float* r = row_real_ifft(G, C, R, gy, n0, deconv_x, tw, Z, Zs);
-        for (int e = row_ptr[gy] + q; e < row_ptr[gy + 1]; e += groups) {
-            const int loc = row_local[e] - off;
-            if (loc < 0 || loc >= nloc) continue;
-            const int m = row_m[e];
-            const int bx = sens_bx[m];
-            const float* wx = sens_wx + (size_t)m * G.w;
-            float t = 0.f;
-            for (int k = 0; k < G.w; ++k) t = fmaf(__ldg(&wx[k]), r[((bx + k) & (Lx - 1)) * C + ln], t);
-            acc[loc * C + ln] = fmaf(row_w[e], t, acc[loc * C + ln]);
+    row_rebuild<PER>(G, C, R, gy, n0, deconv_x, tw, Z);
+    for (int c0 = xrow_first[gy], e_end = xrow_ptr[gy + 1]; c0 < e_end; c0 += ADJ_ECH) {
+        const int ne = min(ADJ_ECH, e_end - c0);
+        for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+            s_bx[i] = __ldg(&xent_bx[c0 + i]);
+            s_rc[i] = __ldg(&xent_rc[c0 + i]);
+        }
+        const float4* sa = reinterpret_cast<const float4*>(taps_a + (size_t)c0 * WT);
+        const float4* sb = reinterpret_cast<const float4*>(taps_b + (size_t)c0 * WT);
+        for (int i = threadIdx.x; i < ne * (WT / 4); i += blockDim.x) {
+            s_ta[i] = __ldg(&sa[i]);
+            if (GRAD) s_tb[i] = __ldg(&sb[i]);
+        }
+        if (GRAD) {
+            for (int i = threadIdx.x; i < (ne << lc); i += blockDim.x) {
+                const int j = i >> lc, c = i & (C - 1);
+                s_g[i] = __ldg(&g[(size_t)__ldg(&xent_m[c0 + j]) * G.Nt + n0 + c]);
+            }
         }
         __syncthreads();
-    }
-    for (int i = threadIdx.x; i < nloc * C; i += blockDim.x) {
-        const int loc = i >> lc;
-        const int c = i & (C - 1);
-        const int b = tk.y + loc;
-        P[((size_t)band_slot[b] * G.M + band_m[b]) * G.Nt + n0 + c] = acc[i];
-    }
-}
-
-__global__ void k_adj_finish(Geo G, const float* __restrict__ P, const unsigned char* __restrict__ two,
-                             float* __restrict__ g) {
-    const size_t total = (size_t)G.M * G.Nt;
-    const int lnt = ilog2(G.Nt);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int m = (int)(i >> lnt);
-        float v = P[i];
-        if (two[m]) v += P[total + i];
-        g[i] = v;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Position gradient (Eq. disc_rec differentiated in x_m, y_m):
-//   dL/dx_m = sum_n g[m][n] sum_rows wy*fac * sum_k dwx[m][k] r[..][n]
-//   dL/dy_m = sum_n g[m][n] sum_rows dwy*fac * sum_k wx[m][k]  r[..][n]
-// with r the transposed stages applied to dL/dp0.  Same task layout as
-// ned_interp_adj; each entry's contribution is reduced over its C time
-// samples with shuffles, accumulated per sensor, and written to
-// Q[slot][time chunk][m]; grad_finish sums chunks and slots.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ned_grad(Geo G, int C, int smax, const float2* __restrict__ R,
-                                                  const float* __restrict__ g,
-                                                  const int4* __restrict__ tasks,
-                                                  const int* __restrict__ row_ptr,
-                                                  const int* __restrict__ row_m,
-                                                  const float* __restrict__ row_w,
-                                                  const float* __restrict__ row_dw,
-                                                  const int* __restrict__ row_local,
-                                                  const int* __restrict__ band_m,
-                                                  const int* __restrict__ band_slot,
-                                                  const int* __restrict__ sens_bx,
-                                                  const float* __restrict__ sens_wx,
-                                                  const float* __restrict__ sens_dwx,
-                                                  const float* __restrict__ deconv_x,
-                                                  const float2* __restrict__ tw, float2* __restrict__ Q) {
-    extern __shared__ float4 smem4[];
-    float2* Z = reinterpret_cast<float2*>(smem4);
-    float2* Zs = Z + (size_t)G.Lx * (C / 2);
-    float2* acc = Zs + (size_t)G.Lx * (C / 2);               // [smax] (d/dx, d/dy)
-    const int4 tk = tasks[blockIdx.x];
-    const int n0 = blockIdx.y * C;
-    const int nloc = tk.z - tk.y;
-    const int off = tk.y - tk.w;
-    const int lc = ilog2(C);
-    const int groups = blockDim.x >> lc;
-    const int q = threadIdx.x >> lc;
-    const int ln = threadIdx.x & (C - 1);
-    const int Lx = G.Lx;
-
-    for (int i = threadIdx.x; i < nloc; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
-    for (int rr = 0; rr < kRowBlock; ++rr) {
-        const int gy = tk.x * kRowBlock + rr;
-        const float* r = row_real_ifft(G, C, R, gy, n0, deconv_x, tw, Z, Zs);
-        const int e_beg = row_ptr[gy], e_end = row_ptr[gy + 1];
-        // every lane of a group walks the same entries so the shuffles stay converged
-        for (int e0 = e_beg; e0 < e_end; e0 += groups) {
-            const int e = e0 + q;
-            float sx = 0.f, sy = 0.f;
-            int loc = -1;
-            if (e < e_end) {
-                loc = row_local[e] - off;
-                if (loc >= 0 && loc < nloc) {
-                    const int m = row_m[e];
-                    const int bx = sens_bx[m];
-                    const float* wx = sens_wx + (size_t)m * G.w;
-                    const float* dwx = sens_dwx + (size_t)m * G.w;
-                    float tx = 0.f, ty = 0.f;
-                    for (int k = 0; k < G.w; ++k) {
-                        const float rv = r[((bx + k) & (Lx - 1)) * C + ln];
-                        tx = fmaf(__ldg(&dwx[k]), rv, tx);
-                        ty = fmaf(__ldg(&wx[k]), rv, ty);
-                    }
-                    const float gv = __ldg(&g[(size_t)m * G.Nt + n0 + ln]);
-                    sx = row_w[e] * tx * gv;
-                    sy = row_dw[e] * ty * gv;
+        const int j0 = (q * ne) / groups, j1 = ((q + 1) * ne) / groups;
+        if (j0 < j1) {                                                 // uniform across the lane group
+            float win[2 * WT];
+            int base = s_bx[j0];
+            win_load<WT>(win, Zf, lnb, ln, Lx, base, 0);
+            win_load<WT>(win, Zf, lnb, ln, Lx, base, WT);
+            for (int j = j0; j < j1; ++j) {
+                const int bx4 = s_bx[j];
+                win_advance<WT>(win, Zf, lnb, ln, Lx, base, bx4);
+                const float2 v = win_entry<WT, GRAD>(win, (bx4 - base) >> 2, s_ta + j * (WT / 4), s_tb + j * (WT / 4));
+                if (!GRAD) {
+                    E[(size_t)s_rc[j] * Tp + (n0 - nb) + ln] = v.x;
                 } else {
-                    loc = -1;
+                    const float gv = s_g[(j << lc) + ln];
+                    float sx = gv * v.x, sy = gv * v.y;
+                    for (int o = C / 2; o > 0; o >>= 1) {
+                        sx += __shfl_xor_sync(gmask, sx, o);
+                        sy += __shfl_xor_sync(gmask, sy, o);
+                    }
+                    if (ln == 0) Qe[(size_t)s_rc[j] * nch + n0 / C] = make_float2(sx, sy);
                 }
             }
-            for (int o = C / 2; o > 0; o >>= 1) {
-                sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            }
-            if (ln == 0 && loc >= 0) {
-                float2 a = acc[loc];
-                acc[loc] = make_float2(a.x + sx, a.y + sy);
-            }
         }
         __syncthreads();
     }
-    const int nchunk = G.Nt / C;
-    for (int i = threadIdx.x; i < nloc; i += blockDim.x) {
-        const int b = tk.y + i;
-        Q[((size_t)band_slot[b] * nchunk + blockIdx.y) * G.M + band_m[b]] = acc[i];
+}
+
+// g[m][nb + t] = sum_k E[sens_ent[m][k]][t], t < Tp: the sensor's w entries (one per y tap)
+__global__ void k_adj_sum(Geo G, int nb, int Tp, const float* __restrict__ E, const int* __restrict__ sens_ent,
+                          float* __restrict__ g) {
+    const size_t total = (size_t)G.M * Tp;
+    const int ltp = ilog2(Tp);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i >> ltp), t = (int)(i & (Tp - 1));
+        float v = 0.f;
+        for (int k = 0; k < G.w; ++k) v += E[(size_t)__ldg(&sens_ent[(size_t)m * G.w + k]) * Tp + t];
+        g[(size_t)m * G.Nt + nb + t] = v;
     }
 }
 
-__global__ void k_grad_finish(Geo G, int nchunk, const float2* __restrict__ Q, const unsigned char* __restrict__ two,
-                              float* __restrict__ dxy) {
+// dL/d(x_m, y_m) = sum over the sensor's w entries and the time chunks of Qe
+__global__ void k_grad_sum(Geo G, int nch, const float2* __restrict__ Qe, const int* __restrict__ sens_ent,
+                           float* __restrict__ dxy) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= G.M) return;
     float sx = 0.f, sy = 0.f;
-    const int nslot = two[m] ? 2 : 1;
-    for (int sl = 0; sl < nslot; ++sl)
-        for (int ch = 0; ch < nchunk; ++ch) {
-            const float2 v = Q[((size_t)sl * nchunk + ch) * G.M + m];
+    for (int k = 0; k < G.w; ++k) {
+        const float2* q = Qe + (size_t)__ldg(&sens_ent[(size_t)m * G.w + k]) * nch;
+        for (int ch = 0; ch < nch; ++ch) {
+            const float2 v = q[ch];
             sx += v.x;
             sy += v.y;
         }
+    }
     dxy[2 * m] = sx;
     dxy[2 * m + 1] = sy;
 }
@@ -483,8 +499,11 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
     NEDNER_ATTR_NER(12, 10) NEDNER_ATTR_NER(14, 12) NEDNER_ATTR_NER(16, 12)
 #undef NEDNER_ATTR_NER
     if ((e = cudaFuncSetAttribute(k_ned_yfft_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem2))) return e;
-    if ((e = cudaFuncSetAttribute(k_ned_interp_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_interp))) return e;
-    if ((e = cudaFuncSetAttribute(k_ned_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_grad))) return e;
+#define NEDNER_ATTR_GATHER(WT, PER)                                                                         \
+    if ((e = cudaFuncSetAttribute(k_ned_gather_rows<WT, PER, false>, (cudaFuncAttribute)a, (int)c.smem_adj))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ned_gather_rows<WT, PER, true>, (cudaFuncAttribute)a, (int)c.smem_grad))) return e;
+    NEDNER_ATTR_GATHER(8, 16) NEDNER_ATTR_GATHER(12, 16) NEDNER_ATTR_GATHER(16, 16) NEDNER_ATTR_GATHER(20, 16)
+#undef NEDNER_ATTR_GATHER
     return cudaSuccess;
 }
 
@@ -525,37 +544,47 @@ cudaError_t launch_ned_yfft_adj(const nedner_plan_s& p, const float2* Ghat, floa
     return cudaGetLastError();
 }
 
-cudaError_t launch_ned_interp_adj(const nedner_plan_s& p, const float2* R, float* P, cudaStream_t s) {
-    const Geo& G = p.geo;
-    if (p.t.ntasks == 0) return cudaSuccess;
-    k_ned_interp_adj<<<dim3(p.t.ntasks, G.Nt / p.ch.ca), 256, p.ch.smem_interp, s>>>(
-        G, p.ch.ca, p.ch.smax, R, p.t.tasks, p.t.row_ptr, p.t.row_m, p.t.row_w, p.t.row_local, p.t.band_m,
-        p.t.band_slot, p.t.sens_bx, p.t.sens_wx, p.t.deconv_x, p.t.tw, P);
-    return cudaGetLastError();
-}
+// the transposed gather kernel, by tap count
+#define NEDNER_GATHER_SWITCH(CALL)      \
+    switch (spread_taps(G.w)) {         \
+        case 8: CALL(8); break;         \
+        case 12: CALL(12); break;       \
+        case 16: CALL(16); break;       \
+        default: CALL(20); break;       \
+    }
 
-cudaError_t launch_adj_finish(const nedner_plan_s& p, const float* P, float* g, cudaStream_t s) {
+cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E, float* g, cudaStream_t s) {
     const Geo& G = p.geo;
-    if (G.M == 0) return cudaSuccess;
-    const size_t total = (size_t)G.M * G.Nt;
+    const int C = p.ch.ca, Tp = p.ch.tp_adj;
+    const size_t total = (size_t)G.M * Tp;
     const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
-    k_adj_finish<<<blocks, 256, 0, s>>>(G, P, p.t.two_blocks, g);
+    for (int nb = 0; nb < G.Nt; nb += Tp) {
+        const dim3 grid(G.Ly, Tp / C);
+#define NEDNER_ADJ(WT)                                                                                            \
+    k_ned_gather_rows<WT, 16, false><<<grid, 256, p.ch.smem_adj, s>>>(G, C, nb, Tp, R, nullptr, p.t.xrow_ptr,       \
+                                                                      p.t.xrow_first, p.t.xent_m, p.t.xent_bx,      \
+                                                                      p.t.xent_rc, p.t.xent_wx, p.t.xent_wx,        \
+                                                                      p.t.deconv_x, p.t.tw, E, nullptr)
+        NEDNER_GATHER_SWITCH(NEDNER_ADJ)
+#undef NEDNER_ADJ
+        k_adj_sum<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_ned_grad(const nedner_plan_s& p, const float2* R, const float* g, float2* Q, cudaStream_t s) {
+cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const float* g, float2* Qe, float* dxy,
+                               cudaStream_t s) {
     const Geo& G = p.geo;
-    if (p.t.ntasks == 0) return cudaSuccess;
-    k_ned_grad<<<dim3(p.t.ntasks, G.Nt / p.ch.ca), 256, p.ch.smem_grad, s>>>(
-        G, p.ch.ca, p.ch.smax, R, g, p.t.tasks, p.t.row_ptr, p.t.row_m, p.t.row_w, p.t.row_dw, p.t.row_local,
-        p.t.band_m, p.t.band_slot, p.t.sens_bx, p.t.sens_wx, p.t.sens_dwx, p.t.deconv_x, p.t.tw, Q);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_grad_finish(const nedner_plan_s& p, const float2* Q, float* dxy, cudaStream_t s) {
-    const Geo& G = p.geo;
-    if (G.M == 0) return cudaSuccess;
-    k_grad_finish<<<(G.M + 255) / 256, 256, 0, s>>>(G, G.Nt / p.ch.ca, Q, p.t.two_blocks, dxy);
+    const int C = p.ch.ca;
+    const dim3 grid(G.Ly, G.Nt / C);
+#define NEDNER_GRAD(WT)                                                                                          \
+    k_ned_gather_rows<WT, 16, true><<<grid, 256, p.ch.smem_grad, s>>>(G, C, 0, G.Nt, R, g, p.t.xrow_ptr,           \
+                                                                      p.t.xrow_first, p.t.xent_m, p.t.xent_bx,     \
+                                                                      p.t.xent_rc, p.t.xent_gx, p.t.xent_gy,       \
+                                                                      p.t.deconv_x, p.t.tw, nullptr, Qe)
+    NEDNER_GATHER_SWITCH(NEDNER_GRAD)
+#undef NEDNER_GRAD
+    k_grad_sum<<<(G.M + 255) / 256, 256, 0, s>>>(G, G.Nt / C, Qe, p.t.sens_ent, dxy);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,8 @@ void free_sensor_tables(DevTables& t) {
     cudaFree(t.sens_dwx); cudaFree(t.sens_dwy); cudaFree(t.sens_fac);
     cudaFree(t.row_ptr); cudaFree(t.row_m); cudaFree(t.row_w); cudaFree(t.row_dw); cudaFree(t.row_local);
     cudaFree(t.xrow_ptr); cudaFree(t.xent_m); cudaFree(t.xent_wx); cudaFree(t.xent_bx); cudaFree(t.seg);
+    cudaFree(t.xent_gx); cudaFree(t.xent_gy); cudaFree(t.xent_loc); cudaFree(t.xrow_first);
+    cudaFree(t.xent_rc); cudaFree(t.sens_ent);
     cudaFree(t.band_m); cudaFree(t.band_slot); cudaFree(t.tasks); cudaFree(t.two_blocks);
     t.sens_bx = t.sens_by = nullptr;
     t.sens_wx = t.sens_wy = t.sens_dwx = t.sens_dwy = t.sens_fac = nullptr;
@@ -49,6 +51,8 @@ void free_sensor_tables(DevTables& t) {
     t.row_w = t.row_dw = nullptr;
     t.xrow_ptr = t.xent_m = t.xent_bx = nullptr;
     t.xent_wx = nullptr;
+    t.xent_gx = t.xent_gy = nullptr;
+    t.xent_loc = t.xrow_first = t.xent_rc = t.sens_ent = nullptr;
     t.seg = nullptr;
     t.band_m = t.band_slot = nullptr;
     t.tasks = nullptr;
@@ -221,30 +225,31 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     for (int r = 0; r < G.Ly; ++r) row_ptr[r + 1] += row_ptr[r];
     std::vector<int> fill(row_ptr.begin(), row_ptr.end() - 1);
     const size_t E = (size_t)M * w;
-    std::vector<int> row_m(E);
+    std::vector<int> row_m(E), sens_ent(E);
     std::vector<float> row_w(E), row_dw(E);
     for (int64_t m = 0; m < M; ++m)
         for (int k = 0; k < w; ++k) {
             int r = (by[m] + k) & (G.Ly - 1);
             int e = fill[r]++;
+            sens_ent[m * w + k] = e;
             row_m[e] = (int)m;
             row_w[e] = wy[m * w + k] * fac[m];
             row_dw[e] = dwy[m * w + k] * fac[m];
         }
 
     // spreading view: sorted by first x column, wrapped entries repeated
-    struct XE { int bx, m; float w; };
+    struct XE { int bx, m; float w, dw; int e; };
     std::vector<int> xrow_ptr(G.Ly + 1, 0);
-    std::vector<int> xent_m, xent_bx;
-    std::vector<float> xent_wx;
+    std::vector<int> xent_m, xent_bx, xent_e;
+    std::vector<float> xent_wx, xent_gx, xent_gy;
     std::vector<int4> seg((size_t)G.Ly * C.groups1);
     std::vector<XE> tmp;
     for (int r = 0; r < G.Ly; ++r) {
         tmp.clear();
         for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
             int m = row_m[e];
-            tmp.push_back({bx[m], m, row_w[e]});
-            if (bx[m] > G.Lx - w) tmp.push_back({bx[m] - G.Lx, m, row_w[e]});
+            tmp.push_back({bx[m], m, row_w[e], row_dw[e], e});
+            if (bx[m] > G.Lx - w) tmp.push_back({bx[m] - G.Lx, m, row_w[e], row_dw[e], e});
         }
         std::stable_sort(tmp.begin(), tmp.end(), [](const XE& a, const XE& b) { return a.bx < b.bx; });
         const int base = (int)xent_m.size();
@@ -254,9 +259,14 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
             const int off = x.bx - bx4;
             xent_m.push_back(x.m);
             xent_bx.push_back(bx4);
+            xent_e.push_back(x.e);
             for (int k = 0; k < WT; ++k) {
                 const int t = k - off;
-                xent_wx.push_back(t >= 0 && t < w ? x.w * wx[(size_t)x.m * w + t] : 0.f);
+                const bool in = t >= 0 && t < w;
+                xent_wx.push_back(in ? x.w * wx[(size_t)x.m * w + t] : 0.f);
+                // position gradient: d/dx_m (x-tap derivative) and d/dy_m (y-tap derivative)
+                xent_gx.push_back(in ? x.w * dwx[(size_t)x.m * w + t] : 0.f);
+                xent_gy.push_back(in ? x.dw * wx[(size_t)x.m * w + t] : 0.f);
             }
         }
         xrow_ptr[r + 1] = (int)xent_m.size();
@@ -327,6 +337,16 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
             int m = row_m[e];
             row_local[e] = (r / kRowBlock == b0[m]) ? pos0[m] : pos1[m];
         }
+    // the same index for the sorted entries (the transposed kernels walk those),
+    // and per row the first entry that is not the second copy of a wrapped one
+    std::vector<int> xent_loc(xent_e.size());
+    for (size_t i = 0; i < xent_e.size(); ++i) xent_loc[i] = row_local[xent_e[i]];
+    std::vector<int> xrow_first(G.Ly);
+    for (int r = 0; r < G.Ly; ++r) {
+        int i = xrow_ptr[r];
+        while (i < xrow_ptr[r + 1] && xent_bx[i] < 0) ++i;
+        xrow_first[r] = i;
+    }
     std::vector<int4> tasks;
     for (int b = 0; b < nblk; ++b)
         for (int s0 = band_ptr[b]; s0 < band_ptr[b + 1]; s0 += C.smax)
@@ -351,6 +371,12 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = upload(&p.t.xent_m, xent_m, s);
     if (!e) e = upload(&p.t.xent_wx, xent_wx, s);
     if (!e) e = upload(&p.t.xent_bx, xent_bx, s);
+    if (!e) e = upload(&p.t.xent_gx, xent_gx, s);
+    if (!e) e = upload(&p.t.xent_gy, xent_gy, s);
+    if (!e) e = upload(&p.t.xent_loc, xent_loc, s);
+    if (!e) e = upload(&p.t.xrow_first, xrow_first, s);
+    if (!e) e = upload(&p.t.xent_rc, xent_e, s);
+    if (!e) e = upload(&p.t.sens_ent, sens_ent, s);
     if (!e) e = upload(&p.t.seg, seg, s);
     if (!e) e = upload(&p.t.band_m, band_m, s);
     if (!e) e = upload(&p.t.band_slot, band_slot, s);
@@ -418,7 +444,8 @@ void choose_chunks(nedner_plan_s& p) {
     // row fits in 128 KB of shared memory, smaller groups beyond
     c.c1 = std::min<long>(32, std::max<long>(2, pow2_floor((128L * 1024) / (8L * G.Lx))));
     c.c1 = std::min(c.c1, G.Nt);
-    c.ca = c.c1;
+    // transposed gather: time samples per CTA such that its row FFT has 16 values per thread
+    c.ca = (int)std::min<long>(c.c1, std::max<long>(2, 8192 / G.Lx));
     c.threads1 = 256;
     c.tpl1 = 1;
     {
@@ -452,8 +479,16 @@ void choose_chunks(nedner_plan_s& p) {
         }
     }
     c.smax = (int)std::max<long>(32, budget / (4L * c.ca));
-    c.smem_interp = (size_t)G.Lx * c.ca * 8 + (size_t)c.smax * c.ca * 4;
-    c.smem_grad = (size_t)G.Lx * c.ca * 8 + (size_t)c.smax * 8;
+    {
+        // transposed gather: padded complex row [Lx][ca/2] (16-byte rounded), then the
+        // staged entries (128 at a time): taps, first column, row-CSR index (and the
+        // second tap set and the samples of g for the gradient)
+        const size_t zb = (size_t)((padded((long)G.Lx * c.ca / 2) + 1) & ~1L) * 8;
+        const size_t wt = (size_t)spread_taps(G.w);
+        c.smem_adj = zb + 128 * (wt + 2) * 4;
+        c.smem_grad = zb + 128 * (2 * wt + c.ca + 2) * 4;
+        c.per_adj = 16;
+    }
     c.c2 = std::min<long>(16, std::max<long>(1, pow2_floor(budget / (16L * G.Ly))));
     c.c2 = std::min(c.c2, G.Nt);
     c.smem2 = (size_t)G.Ly * c.c2 * 16;
@@ -565,8 +600,14 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     size_t v_bytes = (size_t)G.nxh * G.ny * G.nz * 8;
     size_t gh_bytes = (size_t)G.nxh * G.nyp * Nt * 8;
     // region B also holds the transposed stage's per-slot partial sums
-    size_t pa_bytes = (size_t)2 * M * Nt * 4;
-    size_t q_bytes = (size_t)2 * (Nt / p->ch.ca) * M * 8;
+    // the transposed gather's entry buffer: M w floats per time sample of a pass,
+    // passes as long as fit in max(region B, 256 MB); the gradient's per-entry sums
+    const size_t ents = (size_t)M * G.w;
+    const size_t cap = std::max(std::max(gh_bytes, v_bytes), (size_t)256 << 20);
+    p->ch.tp_adj = Nt;
+    while (p->ch.tp_adj > p->ch.ca && ents * p->ch.tp_adj * 4 > cap) p->ch.tp_adj /= 2;
+    size_t pa_bytes = ents * p->ch.tp_adj * 4;
+    size_t q_bytes = ents * (Nt / p->ch.ca) * 8;
     p->region_a = (std::max(r_bytes, v_bytes) + 255) / 256 * 256;
     p->ws_bytes = p->region_a + std::max(std::max(gh_bytes, v_bytes), std::max(pa_bytes, q_bytes));
     if (o.max_workspace_bytes && p->ws_bytes > o.max_workspace_bytes) { delete p; return NEDNER_ENOMEM; }
@@ -686,9 +727,8 @@ nedner_status nedner_adjoint(nedner_plan_t p, const float* p0, float* g, void* s
     cudaError_t e;
     if ((e = transposed_to_R(p, p0, s))) return run(e);
     float2* A = (float2*)p->ws;
-    float* P = (float*)((char*)p->ws + p->region_a);
-    if ((e = launch_ned_interp_adj(*p, A, P, s))) return run(e);
-    return run(launch_adj_finish(*p, P, g, s));
+    float* Eb = (float*)((char*)p->ws + p->region_a);
+    return run(launch_adj_gather(*p, A, Eb, g, s));
 }
 
 nedner_status nedner_grad_positions(nedner_plan_t p, const float* g, const float* dL_dp0, float* dL_dxy,
@@ -701,8 +741,7 @@ nedner_status nedner_grad_positions(nedner_plan_t p, const float* g, const float
     if ((e = transposed_to_R(p, dL_dp0, s))) return run(e);
     float2* A = (float2*)p->ws;
     float2* Q = (float2*)((char*)p->ws + p->region_a);
-    if ((e = launch_ned_grad(*p, A, g, Q, s))) return run(e);
-    return run(launch_grad_finish(*p, Q, dL_dxy, s));
+    return run(launch_grad_gather(*p, A, g, Q, dL_dxy, s));
 }
 
 nedner_status nedner_device_status(nedner_plan_t p, int* flags) {
