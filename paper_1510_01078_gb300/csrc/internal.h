@@ -27,8 +27,7 @@ struct Geo {
 // Work-split choices made once per plan.
 struct Chunks {
     int c1;   // time samples per CTA in the spread + x-FFT stage
-    int c2;   // time samples per CTA in the transposed y-FFT stage
-    int c2f;  // time samples per CTA in the y-FFT stage
+    int c2f;  // time samples per CTA in the y-FFT stage and its transpose
     int c4;   // depth planes per CTA in the y-IFFT stage
     int c5;   // image rows per CTA in the x-c2r stage
     int groups1;   // lane groups (column segments) per CTA in the spread stage
@@ -36,16 +35,14 @@ struct Chunks {
     int per1;      // values per thread in the spread stage's in-place x-FFT (16 or 32)
     int tpl1;      // time samples per lane in the spread stage (1 or 2)
     int ca;        // time samples per CTA in the transposed interpolation stage
-    int smax;      // sensors per task in the transposed interpolation stage
     int per_adj;   // values per thread in its in-place row FFT (16 or 32)
     int tp_adj;    // time samples per pass of the transposed gather (its entry buffer holds M w tp_adj floats)
     int lpc;       // line groups per CTA in the NER stage
     int threads3;  // threads per CTA in the NER stage
-    size_t smem1, smem2, smem2f, smem3, smem4, smem5;
+    size_t smem1, smem2f, smem3, smem4, smem5;
     size_t smem_adj, smem_grad, smem3a;
 };
 
-constexpr int kRowBlock = 16;   // grid rows per block of the transposed interpolation
 
 // Monomial coefficients of the NER interpolation taps, passed by value to the
 // NER kernels so that they are read as constant-bank operands.
@@ -76,7 +73,6 @@ struct DevTables {
     int* row_m = nullptr;         // [M w] sensor of each entry
     float* row_w = nullptr;       // [M w] y tap times sensor factor
     float* row_dw = nullptr;      // [M w] y-tap derivative (per metre) times sensor factor
-    int* row_local = nullptr;     // [M w] index of the entry's sensor in its row block's band
     // spreading: per row, entries sorted by first x column, wrapped ones repeated at bx - Lx
     int* xrow_ptr = nullptr;      // [Ly+1]
     int* xent_m = nullptr;        // [E'] sensor
@@ -84,17 +80,10 @@ struct DevTables {
     int* xent_bx = nullptr;       // [E'] first x column rounded down to a multiple of 4
     float* xent_gx = nullptr;     // [E'][spread_taps(w)] x-tap derivative times y tap times sensor factor
     float* xent_gy = nullptr;     // [E'][spread_taps(w)] x tap times y-tap derivative times sensor factor
-    int* xent_loc = nullptr;      // [E'] index of the entry's sensor in its row block's band
     int* xrow_first = nullptr;    // [Ly] first entry of the row that is not a wrapped entry's second copy
     int* xent_rc = nullptr;       // [E'] the entry's index in the row CSR
     int* sens_ent = nullptr;      // [M][w] row-CSR index of each of the sensor's y taps
     int4* seg = nullptr;          // [Ly][groups1] column range [x, y) and entry range [z, w)
-    // transposed interpolation: sensors touching each block of kRowBlock rows
-    int* band_m = nullptr;        // [B] sensor
-    int* band_slot = nullptr;     // [B] 0 = block of the sensor's first row, 1 = the next block
-    int4* tasks = nullptr;        // [ntasks] (block, band begin, band end, first band index of block)
-    unsigned char* two_blocks = nullptr;  // [M] 1 if the sensor's rows span two blocks
-    int ntasks = 0;
 };
 
 // Tensor-product NED state (tcgen05 GEMM path).

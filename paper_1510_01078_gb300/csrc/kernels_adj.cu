@@ -232,29 +232,29 @@ __global__ void __launch_bounds__(256) k_ner_lines_adj(Geo G, const __grid_const
 // ---------------------------------------------------------------------------
 // Transpose of ned_yfft: R[jx][gy][n] = sum_jy exp(+2 pi i jy gy / Ly) Ghat[jx][jy][n] / phihat(jy/Ly).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ned_yfft_adj(Geo G, int C, const float2* __restrict__ Ghat,
-                                                      const float* __restrict__ deconv_y,
-                                                      const float2* __restrict__ tw, float2* __restrict__ R) {
+__global__ void __launch_bounds__(256, 3) k_ned_yfft_adj(Geo G, int C, const float2* __restrict__ Ghat,
+                                                         const float* __restrict__ deconv_y,
+                                                         const float2* __restrict__ tw, float2* __restrict__ R) {
     extern __shared__ float4 smem4[];
-    float2* A = reinterpret_cast<float2*>(smem4);
-    float2* B = A + (size_t)G.Ly * C;
+    float2* A = reinterpret_cast<float2*>(smem4);   // [Ly][C], padded
     const int jx = blockIdx.x;
     const int n0 = blockIdx.y * C;
     const int lc = ilog2(C);
-    for (int it = threadIdx.x; it < G.Ly * C; it += blockDim.x) A[it] = make_float2(0.f, 0.f);
-    __syncthreads();
+    // jy = b - ny/2 sits at q = (jy mod Ly); the other Ly - (ny + 1) points are zero
 #pragma unroll 8
-    for (int it = threadIdx.x; it < G.nyp * C; it += blockDim.x) {
-        const int b = it >> lc;
+    for (int it = threadIdx.x; it < G.Ly * C; it += 256) {
+        const int q = it >> lc;
         const int c = it & (C - 1);
-        const int q = (b - G.ny / 2 + G.Ly) & (G.Ly - 1);
-        A[q * C + c] = cscale(Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c], __ldg(&deconv_y[b]));
+        const int b = (q <= G.ny / 2) ? q + G.ny / 2 : ((q >= G.Ly - G.ny / 2) ? q - G.Ly + G.ny / 2 : -1);
+        A[padx(it)] = (b >= 0) ? cscale(Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c], __ldg(&deconv_y[b]))
+                               : make_float2(0.f, 0.f);
     }
-    float2* res = block_fft(A, B, G.Ly, C, C, +1, tw);
-    for (int it = threadIdx.x; it < G.Ly * C; it += blockDim.x) {
+    block_fft_ip<16>(A, G.Ly, C, +1, tw);
+#pragma unroll 8
+    for (int it = threadIdx.x; it < G.Ly * C; it += 256) {
         const int gy = it >> lc;
         const int c = it & (C - 1);
-        R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c] = res[it];
+        R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c] = A[padx(it)];
     }
 }
 
@@ -267,7 +267,6 @@ __global__ void __launch_bounds__(256) k_ned_yfft_adj(Geo G, int C, const float2
 // value (gx, t) is at ((float*)Z)[2 padx(gx C/2 + t/2) + t%2].
 // ---------------------------------------------------------------------------
 constexpr int ADJ_ECH = 128;                     // entries staged at a time by the transposed kernels
-#define smax smax
 
 template <int PER>
 __device__ __forceinline__ void row_rebuild(const Geo& G, int C, const float2* __restrict__ R, int gy, int n0,
@@ -391,9 +390,9 @@ __global__ void __launch_bounds__(256, 2) k_ned_gather_rows(Geo G, int C, int nb
     const float* Zf = reinterpret_cast<const float*>(Z);
     float4* s_ta = reinterpret_cast<float4*>(Z + ((padded_len(G.Lx * (C / 2)) + 1) & ~1));   // [ADJ_ECH][WT/4]
     float4* s_tb = s_ta + ADJ_ECH * (WT / 4);                         // [ADJ_ECH][WT/4] (GRAD)
-    float* s_g = reinterpret_cast<float*>(s_tb + (GRAD ? ADJ_ECH * (WT / 4) : 0));   // [ADJ_ECH][C] (GRAD)
-    int* s_bx = reinterpret_cast<int*>(s_g + (GRAD ? ADJ_ECH * C : 0));              // [ADJ_ECH]
+    int* s_bx = reinterpret_cast<int*>(s_tb + (GRAD ? ADJ_ECH * (WT / 4) : 0));      // [ADJ_ECH]
     int* s_rc = s_bx + ADJ_ECH;                                                        // [ADJ_ECH]
+    int* s_m = s_rc + ADJ_ECH;                                                         // [ADJ_ECH] (GRAD)
     const int gy = blockIdx.x;
     const int n0 = nb + blockIdx.y * C;
     const int lc = ilog2(C), lnb = lc - 1;
@@ -410,18 +409,13 @@ __global__ void __launch_bounds__(256, 2) k_ned_gather_rows(Geo G, int C, int nb
         for (int i = threadIdx.x; i < ne; i += blockDim.x) {
             s_bx[i] = __ldg(&xent_bx[c0 + i]);
             s_rc[i] = __ldg(&xent_rc[c0 + i]);
+            if (GRAD) s_m[i] = __ldg(&xent_m[c0 + i]);
         }
         const float4* sa = reinterpret_cast<const float4*>(taps_a + (size_t)c0 * WT);
         const float4* sb = reinterpret_cast<const float4*>(taps_b + (size_t)c0 * WT);
         for (int i = threadIdx.x; i < ne * (WT / 4); i += blockDim.x) {
             s_ta[i] = __ldg(&sa[i]);
             if (GRAD) s_tb[i] = __ldg(&sb[i]);
-        }
-        if (GRAD) {
-            for (int i = threadIdx.x; i < (ne << lc); i += blockDim.x) {
-                const int j = i >> lc, c = i & (C - 1);
-                s_g[i] = __ldg(&g[(size_t)__ldg(&xent_m[c0 + j]) * G.Nt + n0 + c]);
-            }
         }
         __syncthreads();
         const int j0 = (q * ne) / groups, j1 = ((q + 1) * ne) / groups;
@@ -430,14 +424,16 @@ __global__ void __launch_bounds__(256, 2) k_ned_gather_rows(Geo G, int C, int nb
             int base = s_bx[j0];
             win_load<WT>(win, Zf, lnb, ln, Lx, base, 0);
             win_load<WT>(win, Zf, lnb, ln, Lx, base, WT);
+            float gnext = GRAD ? __ldg(&g[(size_t)s_m[j0] * G.Nt + n0 + ln]) : 0.f;
             for (int j = j0; j < j1; ++j) {
                 const int bx4 = s_bx[j];
+                const float gv = gnext;                                // the entry's sample of g
+                if (GRAD && j + 1 < j1) gnext = __ldg(&g[(size_t)s_m[j + 1] * G.Nt + n0 + ln]);
                 win_advance<WT>(win, Zf, lnb, ln, Lx, base, bx4);
                 const float2 v = win_entry<WT, GRAD>(win, (bx4 - base) >> 2, s_ta + j * (WT / 4), s_tb + j * (WT / 4));
                 if (!GRAD) {
                     E[(size_t)s_rc[j] * Tp + (n0 - nb) + ln] = v.x;
                 } else {
-                    const float gv = s_g[(j << lc) + ln];
                     float sx = gv * v.x, sy = gv * v.y;
                     for (int o = C / 2; o > 0; o >>= 1) {
                         sx += __shfl_xor_sync(gmask, sx, o);
@@ -465,21 +461,27 @@ __global__ void k_adj_sum(Geo G, int nb, int Tp, const float* __restrict__ E, co
 }
 
 // dL/d(x_m, y_m) = sum over the sensor's w entries and the time chunks of Qe
+// (one warp per sensor, lanes over (entry, chunk) pairs, fixed order)
 __global__ void k_grad_sum(Geo G, int nch, const float2* __restrict__ Qe, const int* __restrict__ sens_ent,
                            float* __restrict__ dxy) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (m >= G.M) return;
     float sx = 0.f, sy = 0.f;
-    for (int k = 0; k < G.w; ++k) {
-        const float2* q = Qe + (size_t)__ldg(&sens_ent[(size_t)m * G.w + k]) * nch;
-        for (int ch = 0; ch < nch; ++ch) {
-            const float2 v = q[ch];
-            sx += v.x;
-            sy += v.y;
-        }
+    for (int i = lane; i < G.w * nch; i += 32) {
+        const int k = i / nch, ch = i - k * nch;
+        const float2 v = Qe[(size_t)__ldg(&sens_ent[(size_t)m * G.w + k]) * nch + ch];
+        sx += v.x;
+        sy += v.y;
     }
-    dxy[2 * m] = sx;
-    dxy[2 * m + 1] = sy;
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) {
+        dxy[2 * m] = sx;
+        dxy[2 * m + 1] = sy;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -498,7 +500,7 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
     NEDNER_ATTR_NER(4, 10) NEDNER_ATTR_NER(6, 10) NEDNER_ATTR_NER(8, 10) NEDNER_ATTR_NER(10, 10)
     NEDNER_ATTR_NER(12, 10) NEDNER_ATTR_NER(14, 12) NEDNER_ATTR_NER(16, 12)
 #undef NEDNER_ATTR_NER
-    if ((e = cudaFuncSetAttribute(k_ned_yfft_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem2))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_yfft_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem2f))) return e;
 #define NEDNER_ATTR_GATHER(WT, PER)                                                                         \
     if ((e = cudaFuncSetAttribute(k_ned_gather_rows<WT, PER, false>, (cudaFuncAttribute)a, (int)c.smem_adj))) return e; \
     if ((e = cudaFuncSetAttribute(k_ned_gather_rows<WT, PER, true>, (cudaFuncAttribute)a, (int)c.smem_grad))) return e;
@@ -540,7 +542,7 @@ cudaError_t launch_ner_lines_adj(const nedner_plan_s& p, const float2* V, float2
 
 cudaError_t launch_ned_yfft_adj(const nedner_plan_s& p, const float2* Ghat, float2* R, cudaStream_t s) {
     const Geo& G = p.geo;
-    k_ned_yfft_adj<<<dim3(G.nxh, G.Nt / p.ch.c2), 256, p.ch.smem2, s>>>(G, p.ch.c2, Ghat, p.t.deconv_y, p.t.tw, R);
+    k_ned_yfft_adj<<<dim3(G.nxh, G.Nt / p.ch.c2f), 256, p.ch.smem2f, s>>>(G, p.ch.c2f, Ghat, p.t.deconv_y, p.t.tw, R);
     return cudaGetLastError();
 }
 
@@ -584,7 +586,7 @@ cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const fl
                                                                       p.t.deconv_x, p.t.tw, nullptr, Qe)
     NEDNER_GATHER_SWITCH(NEDNER_GRAD)
 #undef NEDNER_GRAD
-    k_grad_sum<<<(G.M + 255) / 256, 256, 0, s>>>(G, G.Nt / C, Qe, p.t.sens_ent, dxy);
+    k_grad_sum<<<(G.M + 7) / 8, 256, 0, s>>>(G, G.Nt / C, Qe, p.t.sens_ent, dxy);
     return cudaGetLastError();
 }
 

@@ -40,24 +40,19 @@ cudaError_t upload(T** dptr, const std::vector<T>& h, cudaStream_t s) {
 void free_sensor_tables(DevTables& t) {
     cudaFree(t.sens_bx); cudaFree(t.sens_by); cudaFree(t.sens_wx); cudaFree(t.sens_wy);
     cudaFree(t.sens_dwx); cudaFree(t.sens_dwy); cudaFree(t.sens_fac);
-    cudaFree(t.row_ptr); cudaFree(t.row_m); cudaFree(t.row_w); cudaFree(t.row_dw); cudaFree(t.row_local);
+    cudaFree(t.row_ptr); cudaFree(t.row_m); cudaFree(t.row_w); cudaFree(t.row_dw);
     cudaFree(t.xrow_ptr); cudaFree(t.xent_m); cudaFree(t.xent_wx); cudaFree(t.xent_bx); cudaFree(t.seg);
-    cudaFree(t.xent_gx); cudaFree(t.xent_gy); cudaFree(t.xent_loc); cudaFree(t.xrow_first);
+    cudaFree(t.xent_gx); cudaFree(t.xent_gy); cudaFree(t.xrow_first);
     cudaFree(t.xent_rc); cudaFree(t.sens_ent);
-    cudaFree(t.band_m); cudaFree(t.band_slot); cudaFree(t.tasks); cudaFree(t.two_blocks);
     t.sens_bx = t.sens_by = nullptr;
     t.sens_wx = t.sens_wy = t.sens_dwx = t.sens_dwy = t.sens_fac = nullptr;
-    t.row_ptr = t.row_m = t.row_local = nullptr;
+    t.row_ptr = t.row_m = nullptr;
     t.row_w = t.row_dw = nullptr;
     t.xrow_ptr = t.xent_m = t.xent_bx = nullptr;
     t.xent_wx = nullptr;
     t.xent_gx = t.xent_gy = nullptr;
-    t.xent_loc = t.xrow_first = t.xent_rc = t.sens_ent = nullptr;
+    t.xrow_first = t.xent_rc = t.sens_ent = nullptr;
     t.seg = nullptr;
-    t.band_m = t.band_slot = nullptr;
-    t.tasks = nullptr;
-    t.two_blocks = nullptr;
-    t.ntasks = 0;
 }
 
 void free_tp(TPState& tp) {
@@ -193,8 +188,8 @@ nedner_status check_positions(const nedner_plan_s& p, const double* xy) {
 //    around x = Lx repeated at bx - Lx, and each row cut into groups1 column
 //    segments of about equal entry count (spreading: every lane group of a CTA
 //    owns one segment and writes it without atomics);
-//  - per block of kRowBlock rows, the sensors touching it (at most two blocks
-//    per sensor since w <= kRowBlock), split into tasks of at most smax sensors.
+//  - per sensor, the row-CSR indices of its w entries (the transposed kernels
+//    write one value per entry and then sum each sensor's entries).
 nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     const Geo& G = p.geo;
     const Chunks& C = p.ch;
@@ -301,59 +296,16 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
         }
     }
 
-    // transposed-interpolation view: row blocks, bands and tasks
-    const int nblk = G.Ly / kRowBlock;
-    std::vector<int> b0(M), b1(M);
-    std::vector<unsigned char> two(M);
-    for (int64_t m = 0; m < M; ++m) {
-        b0[m] = by[m] / kRowBlock;
-        b1[m] = ((by[m] + w - 1) & (G.Ly - 1)) / kRowBlock;
-        two[m] = (unsigned char)(b1[m] != b0[m]);
-    }
-    std::vector<int> band_ptr(nblk + 1, 0);
-    for (int64_t m = 0; m < M; ++m) {
-        band_ptr[b0[m] + 1]++;
-        if (two[m]) band_ptr[b1[m] + 1]++;
-    }
-    for (int b = 0; b < nblk; ++b) band_ptr[b + 1] += band_ptr[b];
-    std::vector<int> bfill(band_ptr.begin(), band_ptr.end() - 1);
-    std::vector<int> band_m(band_ptr[nblk]), band_slot(band_ptr[nblk]);
-    std::vector<int> pos0(M, -1), pos1(M, -1);
-    for (int64_t m = 0; m < M; ++m) {
-        int i = bfill[b0[m]]++;
-        band_m[i] = (int)m;
-        band_slot[i] = 0;
-        pos0[m] = i - band_ptr[b0[m]];
-        if (two[m]) {
-            int j = bfill[b1[m]]++;
-            band_m[j] = (int)m;
-            band_slot[j] = 1;
-            pos1[m] = j - band_ptr[b1[m]];
-        }
-    }
-    std::vector<int> row_local(E);
-    for (int r = 0; r < G.Ly; ++r)
-        for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-            int m = row_m[e];
-            row_local[e] = (r / kRowBlock == b0[m]) ? pos0[m] : pos1[m];
-        }
-    // the same index for the sorted entries (the transposed kernels walk those),
-    // and per row the first entry that is not the second copy of a wrapped one
-    std::vector<int> xent_loc(xent_e.size());
-    for (size_t i = 0; i < xent_e.size(); ++i) xent_loc[i] = row_local[xent_e[i]];
+    // per row the first sorted entry that is not the second copy of a wrapped
+    // one (the transposed kernels read wrapped entries modulo Lx instead)
     std::vector<int> xrow_first(G.Ly);
     for (int r = 0; r < G.Ly; ++r) {
         int i = xrow_ptr[r];
         while (i < xrow_ptr[r + 1] && xent_bx[i] < 0) ++i;
         xrow_first[r] = i;
     }
-    std::vector<int4> tasks;
-    for (int b = 0; b < nblk; ++b)
-        for (int s0 = band_ptr[b]; s0 < band_ptr[b + 1]; s0 += C.smax)
-            tasks.push_back(make_int4(b, s0, std::min(band_ptr[b + 1], s0 + C.smax), band_ptr[b]));
 
     free_sensor_tables(p.t);
-    p.t.ntasks = (int)tasks.size();
     cudaError_t e = cudaSuccess;
     if (!e) e = upload(&p.t.sens_bx, bx, s);
     if (!e) e = upload(&p.t.sens_by, by, s);
@@ -366,22 +318,16 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = upload(&p.t.row_m, row_m, s);
     if (!e) e = upload(&p.t.row_w, row_w, s);
     if (!e) e = upload(&p.t.row_dw, row_dw, s);
-    if (!e) e = upload(&p.t.row_local, row_local, s);
     if (!e) e = upload(&p.t.xrow_ptr, xrow_ptr, s);
     if (!e) e = upload(&p.t.xent_m, xent_m, s);
     if (!e) e = upload(&p.t.xent_wx, xent_wx, s);
     if (!e) e = upload(&p.t.xent_bx, xent_bx, s);
     if (!e) e = upload(&p.t.xent_gx, xent_gx, s);
     if (!e) e = upload(&p.t.xent_gy, xent_gy, s);
-    if (!e) e = upload(&p.t.xent_loc, xent_loc, s);
     if (!e) e = upload(&p.t.xrow_first, xrow_first, s);
     if (!e) e = upload(&p.t.xent_rc, xent_e, s);
     if (!e) e = upload(&p.t.sens_ent, sens_ent, s);
     if (!e) e = upload(&p.t.seg, seg, s);
-    if (!e) e = upload(&p.t.band_m, band_m, s);
-    if (!e) e = upload(&p.t.band_slot, band_slot, s);
-    if (!e) e = upload(&p.t.tasks, tasks, s);
-    if (!e) e = upload(&p.t.two_blocks, two, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e == cudaErrorMemoryAllocation) return NEDNER_ENOMEM;
     return e ? NEDNER_ECUDA : NEDNER_OK;
@@ -439,7 +385,6 @@ int pow2_floor(long v) {
 void choose_chunks(nedner_plan_s& p) {
     Geo& G = p.geo;
     Chunks& c = p.ch;
-    const long budget = 64 * 1024;                     // bytes of shared memory per CTA
     // spread + x-FFT: lane groups of a full warp (32 time samples) while the
     // row fits in 128 KB of shared memory, smaller groups beyond
     c.c1 = std::min<long>(32, std::max<long>(2, pow2_floor((128L * 1024) / (8L * G.Lx))));
@@ -478,7 +423,6 @@ void choose_chunks(nedner_plan_s& p) {
             c.per1 = (long)G.Lx * c.c1 / 2 <= 16L * c.threads1 ? 16 : 32;
         }
     }
-    c.smax = (int)std::max<long>(32, budget / (4L * c.ca));
     {
         // transposed gather: padded complex row [Lx][ca/2] (16-byte rounded), then the
         // staged entries (128 at a time): taps, first column, row-CSR index (and the
@@ -486,12 +430,9 @@ void choose_chunks(nedner_plan_s& p) {
         const size_t zb = (size_t)((padded((long)G.Lx * c.ca / 2) + 1) & ~1L) * 8;
         const size_t wt = (size_t)spread_taps(G.w);
         c.smem_adj = zb + 128 * (wt + 2) * 4;
-        c.smem_grad = zb + 128 * (2 * wt + c.ca + 2) * 4;
+        c.smem_grad = zb + 128 * (2 * wt + 3) * 4;
         c.per_adj = 16;
     }
-    c.c2 = std::min<long>(16, std::max<long>(1, pow2_floor(budget / (16L * G.Ly))));
-    c.c2 = std::min(c.c2, G.Nt);
-    c.smem2 = (size_t)G.Ly * c.c2 * 16;
     c.c2f = (int)std::min<long>(std::min<long>(16, G.Nt), std::max<long>(1, 4096 / G.Ly));
     c.smem2f = (size_t)padded((long)G.Ly * c.c2f) * 8;
     // NER: lines per CTA such that the batched line FFT has Lt * lpc = 4096 points
