@@ -40,7 +40,7 @@ struct Chunks {
     int lpc;       // line groups per CTA in the NER stage
     int threads3;  // threads per CTA in the NER stage
     size_t smem1, smem2f, smem3, smem4, smem5;
-    size_t smem_adj, smem_grad, smem3a;
+    size_t smem_adj, smem_grad;
 };
 
 

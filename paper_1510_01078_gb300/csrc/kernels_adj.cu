@@ -121,111 +121,152 @@ __device__ __forceinline__ FF2 nu_abs2(const Geo& G, float2 axy, int l) {
     return quick_two_sum2(r, resid * (0.5f / r));
 }
 
-// B[(mu0 + k) mod Lt] += P_k(s) v for the W taps (Horner, unrolled)
+// B[(mu0 + k) mod Lt] += P_k(s) v for the W taps, into column col of the padded
+// buffer with 2^lld columns; tap W-1-k is tap k at -s (see ner_gather)
 template <int W, int D>
-__device__ __forceinline__ void ner_scatter(const TapPoly& P, float2* LA, int mu0, float s, int Lt, float2 v) {
+__device__ __forceinline__ void ner_scatter(const TapPoly& P, float2* LA, int mu0, float s, int Lt, int lld, int col,
+                                            float2 v) {
+    constexpr int DE = D & ~1;
+    constexpr int DO = (D & 1) ? D : D - 1;
+    const float u = s * s;
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
-        float p = P.c[k * (D + 1) + D];
+    for (int k = 0; k < W / 2; ++k) {
+        float e = P.c[k * (D + 1) + DE];
 #pragma unroll
-        for (int d = D - 1; d >= 0; --d) p = fmaf(p, s, P.c[k * (D + 1) + d]);
-        float2* dst = &LA[(mu0 + k) & (Lt - 1)];
-        atomicAdd(&dst->x, p * v.x);
-        atomicAdd(&dst->y, p * v.y);
+        for (int d = DE - 2; d >= 0; d -= 2) e = fmaf(e, u, P.c[k * (D + 1) + d]);
+        float o = P.c[k * (D + 1) + DO];
+#pragma unroll
+        for (int d = DO - 2; d >= 1; d -= 2) o = fmaf(o, u, P.c[k * (D + 1) + d]);
+        const float so = s * o;
+        const float pk = e + so, pm = e - so;
+        float2* dk = &LA[padx((((mu0 + k) & (Lt - 1)) << lld) + col)];
+        float2* dm = &LA[padx((((mu0 + W - 1 - k) & (Lt - 1)) << lld) + col)];
+        atomicAdd(&dk->x, pk * v.x);
+        atomicAdd(&dk->y, pk * v.y);
+        atomicAdd(&dm->x, pm * v.x);
+        atomicAdd(&dm->y, pm * v.y);
     }
 }
 
+// coefficient(l) * exp(+i pi nu) * tb spread onto column col of the line's
+// oversampled spectrum (the transpose of ner_value)
 template <int W, int D>
-__global__ void __launch_bounds__(256) k_ner_lines_adj(Geo G, const __grid_constant__ TapPoly P,
-                                                       const float2* __restrict__ V,
-                                                       const float2* __restrict__ axy_tab,
-                                                       const float* __restrict__ deconv_t,
-                                                       const float2* __restrict__ tw, float2* __restrict__ Ghat) {
-    extern __shared__ float4 smem4[];
-    float2* LA = reinterpret_cast<float2*>(smem4);   // [Lt]
-    float2* LB = LA + G.Lt;                          // [Lt]
-    float2* T = LB + G.Lt;                           // [nz + 1]
-    float2* UA = T + (G.nz + 1);                     // [nz]
-    float2* UB = UA + G.nz;                          // [nz]
+__device__ __forceinline__ void ner_spread_value(const Geo& G, const TapPoly& P, float2 axy, bool j0, int l, float2 tb,
+                                                 float2* LA, int lld, int col) {
+    if (tb.x == 0.f && tb.y == 0.f) return;
+    FF2 nu = nu_abs2(G, axy, l);
+    float Wj;
+    if (l == 0) {
+        Wj = j0 ? 2.f : 0.f;
+        nu = {0.f, 0.f};
+    } else {
+        Wj = 2.f * G.sqrt_az * (float)abs(l) / nu.hi;
+        if (l < 0) nu = {-nu.hi, -nu.lo};
+    }
+    float cl = G.apply_weights ? Wj * G.scale : G.scale;
+    if (G.band_mask) {
+        const double nd = (double)nu.hi + (double)nu.lo;
+        if (!(nd >= -0.5 * G.Nt - 1e-9 && nd < 0.5 * G.Nt - 1e-9)) cl = 0.f;
+    }
+    if (cl == 0.f) return;
+    tb = cscale(tb, cl);
+    const float vh = 2.f * nu.hi, vl = 2.f * nu.lo;
+    float fl = floorf(vh);
+    float t = (vh - fl) + vl;
+    if (t < 0.f) { t += 1.f; fl -= 1.f; }
+    if (t >= 1.f) { t -= 1.f; fl += 1.f; }
+    const int ifl = (int)fl;
+    // exp(+i pi nu) = i^floor(v) exp(+i pi t / 2)
+    float sn, cs;
+    sincospif(0.5f * t, &sn, &cs);
+    float2 ph = make_float2(cs, sn);
+    const int q = ifl & 3;
+    if (q == 1) ph = make_float2(-ph.y, ph.x);
+    else if (q == 2) ph = make_float2(-ph.x, -ph.y);
+    else if (q == 3) ph = make_float2(ph.y, -ph.x);
+    ner_scatter<W, D>(P, LA, ifl - W / 2 + 1, 2.f * t - 1.f, G.Lt, lld, col, cmul(ph, tb));
+}
 
-    const int grp = blockIdx.x;
-    const int kx = grp >> ilog2(G.ny);
-    const int ky = (grp & (G.ny - 1)) - G.ny / 2;
-    const int kyb = (ky == -G.ny / 2) ? G.ny / 2 : ky;
+// Transpose of ner_lines for the LPC line groups (kx, k0..k0+LPC-1) of the
+// forward CTA:
+//   Ubar = FFT_nz(sign V[group])                      (transpose of the z-IFFT)
+//   line ky of group c:  Tbar[e] = ca Ubar_c[l] (e < nz) + cb Ubar_c[slot(e)] (e > 0)
+//   the group ky = -ny/2 feeds line -ny/2 through ca only and line +ny/2
+//   through cb (slot(e) = l for e < nz, -nz/2 for e = nz), as the fold reads them;
+// each Tbar[e] is weighted (Jacobian, scale, band mask), multiplied by
+// exp(+i pi nu) and spread with the w taps onto the line's 2Nt grid (shared
+// atomics), the grids are inverse-transformed together, and the centred Nt
+// samples, divided by phihat, are the lines of Ghat.
+template <int W, int D, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines_adj(Geo G, const __grid_constant__ TapPoly P,
+                                                                       int LPC, const float2* __restrict__ V,
+                                                                       const float2* __restrict__ axy_tab,
+                                                                       const float* __restrict__ deconv_t,
+                                                                       const float2* __restrict__ tw,
+                                                                       float2* __restrict__ Ghat) {
+    constexpr int PER = 16;
+    extern __shared__ float4 smem4[];
+    float2* LA = reinterpret_cast<float2*>(smem4);                 // [Lt][LPC], padded
+    float2* UA = LA + padded_len(G.Lt * LPC);                      // [nz][LPC], padded
+
+    const int llpc = ilog2(LPC), lnz = ilog2(G.nz);
+    const int cpk = G.ny >> llpc;
+    const int kx = blockIdx.x / cpk;
+    const int k0 = (blockIdx.x - kx * cpk) * LPC - G.ny / 2;
     const bool nyq_x = (kx == G.nx / 2);
     const float ca = nyq_x ? 0.f : 0.5f;
     const float cb = nyq_x ? 1.f : 0.5f;
     const int half_nz = G.nz / 2;
-    const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
+    const size_t line0 = (size_t)kx * G.nyp + (k0 + G.ny / 2);
 
-    const float2* src = V + ((size_t)kx * G.ny + (ky & (G.ny - 1))) * G.nz;
-#pragma unroll 4
-    for (int q = threadIdx.x; q < G.nz; q += blockDim.x) UA[q] = cscale(src[q], sg);
-    float2* Ub = block_fft(UA, UB, G.nz, 1, 1, -1, tw);
-
-    const int nlines = (nyq_x || ky == kyb) ? 1 : 2;
-    for (int li = 0; li < nlines; ++li) {
-        const int lky = (li == 0 && nlines == 2) ? ky : kyb;
-        const size_t line = (size_t)kx * G.nyp + (lky + G.ny / 2);
-        const float2 axy = __ldg(&axy_tab[line]);
-        const bool is_a = !nyq_x && (lky == ky);
-        const bool is_b = (lky == kyb);
-
-        __syncthreads();
-        for (int p = threadIdx.x; p < G.Lt; p += blockDim.x) LA[p] = make_float2(0.f, 0.f);
-        __syncthreads();
-        for (int e = threadIdx.x; e <= G.nz; e += blockDim.x) {
-            const int l = e - half_nz;
-            float2 tb = make_float2(0.f, 0.f);
-            if (is_a && e < G.nz) tb = cadd(tb, cscale(Ub[l & (G.nz - 1)], ca));
-            if (is_b && e > 0) {
-                // e = +nz/2 feeds slot -nz/2; other e feed slot e
-                const int slot = (e == G.nz) ? (-half_nz & (G.nz - 1)) : (l & (G.nz - 1));
-                tb = cadd(tb, cscale(Ub[slot], cb));
-            }
-            FF2 nu = nu_abs2(G, axy, l);
-            float Wj;
-            if (l == 0) {
-                Wj = (kx == 0 && lky == 0) ? 2.f : 0.f;
-                nu = {0.f, 0.f};
-            } else {
-                Wj = 2.f * G.sqrt_az * (float)abs(l) / nu.hi;
-                if (l < 0) nu = {-nu.hi, -nu.lo};
-            }
-            float cl = G.apply_weights ? Wj * G.scale : G.scale;
-            if (G.band_mask) {
-                const double nd = (double)nu.hi + (double)nu.lo;
-                if (!(nd >= -0.5 * G.Nt - 1e-9 && nd < 0.5 * G.Nt - 1e-9)) cl = 0.f;
-            }
-            tb = cscale(tb, cl);
-            if (tb.x != 0.f || tb.y != 0.f) {
-                const float vh = 2.f * nu.hi, vl = 2.f * nu.lo;
-                float fl = floorf(vh);
-                float t = (vh - fl) + vl;
-                if (t < 0.f) { t += 1.f; fl -= 1.f; }
-                if (t >= 1.f) { t -= 1.f; fl += 1.f; }
-                const int ifl = (int)fl;
-                const int mu0 = ifl - W / 2 + 1;
-                // exp(+i pi nu) = i^floor(v) exp(+i pi t / 2)
-                float sn, cs;
-                sincospif(0.5f * t, &sn, &cs);
-                float2 ph = make_float2(cs, sn);
-                const int q = ifl & 3;
-                if (q == 1) ph = make_float2(-ph.y, ph.x);
-                else if (q == 2) ph = make_float2(-ph.x, -ph.y);
-                else if (q == 3) ph = make_float2(ph.y, -ph.x);
-                ner_scatter<W, D>(P, LA, mu0, 2.f * t - 1.f, G.Lt, cmul(ph, tb));
-            }
-        }
-        float2* z = block_fft(LA, LB, G.Lt, 1, 1, +1, tw);
-        float2* dst = Ghat + line * G.Nt;
-        for (int n = threadIdx.x; n < G.Nt; n += blockDim.x)
-            dst[n] = cscale(z[(n - G.Nt / 2) & (G.Lt - 1)], __ldg(&deconv_t[n]));
+    // Ubar of the LPC groups
+    for (int i = threadIdx.x; i < (G.nz << llpc); i += NT) {
+        const int c = i >> lnz, q = i & (G.nz - 1);
+        const int ky = k0 + c;
+        const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
+        UA[padx((q << llpc) + c)] = cscale(V[((size_t)kx * G.ny + (ky & (G.ny - 1))) * G.nz + q], sg);
     }
-    if (nyq_x && ky == -G.ny / 2) {
-        // the line (nx/2, -ny/2) is not used by the forward map: its transpose is zero
-        float2* dst = Ghat + ((size_t)kx * G.nyp + 0) * G.Nt;
-        for (int n = threadIdx.x; n < G.Nt; n += blockDim.x) dst[n] = make_float2(0.f, 0.f);
+    block_fft_ip<PER>(UA, G.nz, LPC, -1, tw);
+
+    if (k0 == -G.ny / 2) {
+        // the line (kx, +ny/2), fed by group 0 through cb, in column 0
+        for (int p = threadIdx.x; p < padded_len(G.Lt); p += NT) LA[p] = make_float2(0.f, 0.f);
+        __syncthreads();
+        const size_t lx = (size_t)kx * G.nyp + G.ny;
+        const float2 axy = __ldg(&axy_tab[lx]);
+        for (int e = threadIdx.x + 1; e <= G.nz; e += NT) {
+            const int l = e - half_nz;
+            const int slot = (e == G.nz) ? (-half_nz & (G.nz - 1)) : (l & (G.nz - 1));
+            ner_spread_value<W, D>(G, P, axy, false, l, cscale(UA[padx(slot << llpc)], cb), LA, 0, 0);
+        }
+        block_fft_ip<PER>(LA, G.Lt, 1, +1, tw);
+        float2* dst = Ghat + lx * G.Nt;
+        for (int n = threadIdx.x; n < G.Nt; n += NT)
+            dst[n] = cscale(LA[padx((n - G.Nt / 2) & (G.Lt - 1))], __ldg(&deconv_t[n]));
+        __syncthreads();
+    }
+    // the LPC lines (kx, k0 + c)
+    for (int p = threadIdx.x; p < padded_len(G.Lt * LPC); p += NT) LA[p] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ((G.nz + 1) << llpc); i += NT) {
+        const int c = i / (G.nz + 1), e = i - c * (G.nz + 1);
+        const int l = e - half_nz;
+        const int ky = k0 + c;
+        const bool is_b = (ky != -G.ny / 2);                       // group -ny/2 feeds line +ny/2 instead
+        float2 tb = make_float2(0.f, 0.f);
+        if (e < G.nz) tb = cadd(tb, cscale(UA[padx(((l & (G.nz - 1)) << llpc) + c)], ca));
+        if (is_b && e > 0) {
+            const int slot = (e == G.nz) ? (-half_nz & (G.nz - 1)) : (l & (G.nz - 1));
+            tb = cadd(tb, cscale(UA[padx((slot << llpc) + c)], cb));
+        }
+        const float2 axy = __ldg(&axy_tab[line0 + c]);
+        ner_spread_value<W, D>(G, P, axy, kx == 0 && ky == 0, l, tb, LA, llpc, c);
+    }
+    block_fft_ip<PER>(LA, G.Lt, LPC, +1, tw);
+    for (int i = threadIdx.x; i < (G.Nt << llpc); i += NT) {
+        const int c = i >> ilog2(G.Nt), n = i & (G.Nt - 1);
+        Ghat[(line0 + c) * G.Nt + n] = cscale(LA[padx((((n - G.Nt / 2) & (G.Lt - 1)) << llpc) + c)],
+                                              __ldg(&deconv_t[n]));
     }
 }
 
@@ -495,8 +536,9 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
     if ((e = cudaFuncSetAttribute(k_img_xr2c_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_xr2c))) return e;
     if ((e = cudaFuncSetAttribute(k_img_yfft_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem4))) return e;
     const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-#define NEDNER_ATTR_NER(W, D) \
-    if ((e = cudaFuncSetAttribute(k_ner_lines_adj<W, D>, (cudaFuncAttribute)a, (int)c.smem3a))) return e;
+#define NEDNER_ATTR_NER(W, D)                                                                                      \
+    if ((e = cudaFuncSetAttribute(k_ner_lines_adj<W, D, 256>, (cudaFuncAttribute)a, (int)c.smem3))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ner_lines_adj<W, D, 512>, (cudaFuncAttribute)a, (int)c.smem3))) return e;
     NEDNER_ATTR_NER(4, 10) NEDNER_ATTR_NER(6, 10) NEDNER_ATTR_NER(8, 10) NEDNER_ATTR_NER(10, 10)
     NEDNER_ATTR_NER(12, 10) NEDNER_ATTR_NER(14, 12) NEDNER_ATTR_NER(16, 12)
 #undef NEDNER_ATTR_NER
@@ -524,9 +566,14 @@ cudaError_t launch_img_yfft_adj(const nedner_plan_s& p, const float2* Y, float2*
 
 cudaError_t launch_ner_lines_adj(const nedner_plan_s& p, const float2* V, float2* Ghat, cudaStream_t s) {
     const Geo& G = p.geo;
-    const dim3 grid(G.nxh * G.ny);
-#define NEDNER_NER(W, D) \
-    k_ner_lines_adj<W, D><<<grid, 256, p.ch.smem3a, s>>>(G, p.tap, V, p.t.axy, p.t.deconv_t, p.t.tw, Ghat)
+    const dim3 grid(G.nxh * (G.ny / p.ch.lpc));
+#define NEDNER_NER(W, D)                                                                                        \
+    if (p.ch.threads3 <= 256)                                                                                   \
+        k_ner_lines_adj<W, D, 256><<<grid, 256, p.ch.smem3, s>>>(G, p.tap, p.ch.lpc, V, p.t.axy, p.t.deconv_t,  \
+                                                                 p.t.tw, Ghat);                                \
+    else                                                                                                        \
+        k_ner_lines_adj<W, D, 512><<<grid, 512, p.ch.smem3, s>>>(G, p.tap, p.ch.lpc, V, p.t.axy, p.t.deconv_t,  \
+                                                                 p.t.tw, Ghat)
     switch (G.w) {
         case 4: NEDNER_NER(4, 10); break;
         case 6: NEDNER_NER(6, 10); break;

@@ -443,7 +443,6 @@ void choose_chunks(nedner_plan_s& p) {
            (long)G.nz * c.lpc * 2 <= 16L * c.threads3)
         c.lpc *= 2;
     c.smem3 = (size_t)(padded(G.Lt * c.lpc) + (c.lpc + 1) * (G.nz + 1) + padded(G.nz * c.lpc)) * 8;
-    c.smem3a = (size_t)(2 * G.Lt + (G.nz + 1) + 2 * G.nz) * 8;
     c.c4 = 1;
     while (c.c4 * 2 <= 16 && c.c4 * 2 <= G.nz && 2L * G.ny * (c.c4 * 2 + 1) * 8 <= 96 * 1024) c.c4 *= 2;
     c.smem4 = (size_t)2 * G.ny * (c.c4 + 1) * 8;
