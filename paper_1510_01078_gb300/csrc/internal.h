@@ -36,6 +36,7 @@ struct Chunks {
     int tpl1;      // time samples per lane in the spread stage (1 or 2)
     int ca;        // time samples per CTA in the transposed interpolation stage
     int per_adj;   // values per thread in its in-place row FFT (16 or 32)
+    int tpl_adj;   // time samples per lane in the transposed gather (1 or 2; 2 means ca = 64)
     int tp_adj;    // time samples per pass of the transposed gather (its entry buffer holds M w tp_adj floats)
     int lpc;       // line groups per CTA in the NER stage
     int threads3;  // threads per CTA in the NER stage

@@ -488,6 +488,138 @@ __global__ void __launch_bounds__(256, 2) k_ned_gather_rows(Geo G, int C, int nb
     }
 }
 
+// Two time samples per lane (C = 64 per CTA): the lane's samples 2 ln, 2 ln + 1
+// are complex column ln of the packed row, so the window holds float2 pairs
+// and every tap is one packed FMA.
+template <int WT>
+__device__ __forceinline__ void win2_load(float2 (&win)[2 * WT], const float2* Z, int ln, int Lx, int base, int k0) {
+#pragma unroll
+    for (int k = 0; k < WT; ++k) win[k0 + k] = Z[padx((((base + k0 + k) & (Lx - 1)) << 5) + ln)];
+}
+
+template <int WT>
+__device__ __forceinline__ void win2_advance(float2 (&win)[2 * WT], const float2* Z, int ln, int Lx, int& base,
+                                             int bx4) {
+    while (bx4 - base > WT) {
+#pragma unroll
+        for (int k = 0; k < WT; ++k) win[k] = win[k + WT];
+        base += WT;
+        win2_load<WT>(win, Z, ln, Lx, base, WT);
+    }
+}
+
+template <int WT, int D, bool TWO>
+__device__ __forceinline__ void win2_dot(const float2 (&win)[2 * WT], const float4* ta, const float4* tb, float2& va,
+                                         float2& vb) {
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+#pragma unroll
+    for (int k4 = 0; k4 < WT / 4; ++k4) {
+        const float4 t4 = ta[k4];
+        a0 = __ffma2_rn(make_float2(t4.x, t4.x), win[D + 4 * k4 + 0], a0);
+        a1 = __ffma2_rn(make_float2(t4.y, t4.y), win[D + 4 * k4 + 1], a1);
+        a0 = __ffma2_rn(make_float2(t4.z, t4.z), win[D + 4 * k4 + 2], a0);
+        a1 = __ffma2_rn(make_float2(t4.w, t4.w), win[D + 4 * k4 + 3], a1);
+        if (TWO) {
+            const float4 u4 = tb[k4];
+            b0 = __ffma2_rn(make_float2(u4.x, u4.x), win[D + 4 * k4 + 0], b0);
+            b1 = __ffma2_rn(make_float2(u4.y, u4.y), win[D + 4 * k4 + 1], b1);
+            b0 = __ffma2_rn(make_float2(u4.z, u4.z), win[D + 4 * k4 + 2], b0);
+            b1 = __ffma2_rn(make_float2(u4.w, u4.w), win[D + 4 * k4 + 3], b1);
+        }
+    }
+    va = __fadd2_rn(a0, a1);
+    vb = __fadd2_rn(b0, b1);
+}
+
+template <int WT, bool TWO>
+__device__ __forceinline__ void win2_entry(const float2 (&win)[2 * WT], int d, const float4* ta, const float4* tb,
+                                           float2& va, float2& vb) {
+    if (d == 0) win2_dot<WT, 0, TWO>(win, ta, tb, va, vb);
+    else if (d == 1) win2_dot<WT, 4, TWO>(win, ta, tb, va, vb);
+    else if (d == 2) win2_dot<WT, (WT >= 8 ? 8 : 0), TWO>(win, ta, tb, va, vb);
+    else if (WT >= 12 && d == 3) win2_dot<WT, (WT >= 12 ? 12 : 0), TWO>(win, ta, tb, va, vb);
+    else if (WT >= 16 && d == 4) win2_dot<WT, (WT >= 16 ? 16 : 0), TWO>(win, ta, tb, va, vb);
+    else win2_dot<WT, (WT >= 20 ? 20 : 0), TWO>(win, ta, tb, va, vb);
+}
+
+// k_ned_gather_rows with two time samples per lane: C = 64, 256 threads (one
+// lane group per warp), the row FFT with 32 values per thread (2 nx <= 256).
+template <int WT, bool GRAD>
+__global__ void __launch_bounds__(256, 2) k_ned_gather_rows2(Geo G, int nb, int Tp, const float2* __restrict__ R,
+                                                             const float* __restrict__ g,
+                                                             const int* __restrict__ xrow_ptr,
+                                                             const int* __restrict__ xrow_first,
+                                                             const int* __restrict__ xent_m,
+                                                             const int* __restrict__ xent_bx,
+                                                             const int* __restrict__ xent_rc,
+                                                             const float* __restrict__ taps_a,
+                                                             const float* __restrict__ taps_b,
+                                                             const float* __restrict__ deconv_x,
+                                                             const float2* __restrict__ tw, float* __restrict__ E,
+                                                             float2* __restrict__ Qe) {
+    constexpr int C = 64;
+    extern __shared__ float4 smem4[];
+    float2* Z = reinterpret_cast<float2*>(smem4);                    // padded [Lx][32]
+    float4* s_ta = reinterpret_cast<float4*>(Z + ((padded_len(G.Lx * (C / 2)) + 1) & ~1));   // [ADJ_ECH][WT/4]
+    float4* s_tb = s_ta + ADJ_ECH * (WT / 4);                         // [ADJ_ECH][WT/4] (GRAD)
+    int* s_bx = reinterpret_cast<int*>(s_tb + (GRAD ? ADJ_ECH * (WT / 4) : 0));      // [ADJ_ECH]
+    int* s_rc = s_bx + ADJ_ECH;                                                        // [ADJ_ECH]
+    int* s_m = s_rc + ADJ_ECH;                                                         // [ADJ_ECH] (GRAD)
+    const int gy = blockIdx.x;
+    const int n0 = nb + blockIdx.y * C;
+    const int groups = blockDim.x >> 5;
+    const int q = threadIdx.x >> 5;
+    const int ln = threadIdx.x & 31;
+    const int Lx = G.Lx;
+    const int nch = G.Nt / C;
+
+    row_rebuild<32>(G, C, R, gy, n0, deconv_x, tw, Z);
+    for (int c0 = xrow_first[gy], e_end = xrow_ptr[gy + 1]; c0 < e_end; c0 += ADJ_ECH) {
+        const int ne = min(ADJ_ECH, e_end - c0);
+        for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+            s_bx[i] = __ldg(&xent_bx[c0 + i]);
+            s_rc[i] = __ldg(&xent_rc[c0 + i]);
+            if (GRAD) s_m[i] = __ldg(&xent_m[c0 + i]);
+        }
+        const float4* sa = reinterpret_cast<const float4*>(taps_a + (size_t)c0 * WT);
+        const float4* sb = reinterpret_cast<const float4*>(taps_b + (size_t)c0 * WT);
+        for (int i = threadIdx.x; i < ne * (WT / 4); i += blockDim.x) {
+            s_ta[i] = __ldg(&sa[i]);
+            if (GRAD) s_tb[i] = __ldg(&sb[i]);
+        }
+        __syncthreads();
+        const int j0 = (q * ne) / groups, j1 = ((q + 1) * ne) / groups;
+        if (j0 < j1) {
+            float2 win[2 * WT];
+            int base = s_bx[j0];
+            win2_load<WT>(win, Z, ln, Lx, base, 0);
+            win2_load<WT>(win, Z, ln, Lx, base, WT);
+            float2 gnext = GRAD ? __ldg(reinterpret_cast<const float2*>(g + (size_t)s_m[j0] * G.Nt + n0) + ln)
+                                : make_float2(0.f, 0.f);
+            for (int j = j0; j < j1; ++j) {
+                const int bx4 = s_bx[j];
+                const float2 gv = gnext;                               // the entry's samples of g
+                if (GRAD && j + 1 < j1)
+                    gnext = __ldg(reinterpret_cast<const float2*>(g + (size_t)s_m[j + 1] * G.Nt + n0) + ln);
+                win2_advance<WT>(win, Z, ln, Lx, base, bx4);
+                float2 va, vb;
+                win2_entry<WT, GRAD>(win, (bx4 - base) >> 2, s_ta + j * (WT / 4), s_tb + j * (WT / 4), va, vb);
+                if (!GRAD) {
+                    reinterpret_cast<float2*>(E + (size_t)s_rc[j] * Tp + (n0 - nb))[ln] = va;
+                } else {
+                    float sx = fmaf(gv.x, va.x, gv.y * va.y), sy = fmaf(gv.x, vb.x, gv.y * vb.y);
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                    }
+                    if (ln == 0) Qe[(size_t)s_rc[j] * nch + n0 / C] = make_float2(sx, sy);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // g[m][nb + t] = sum_k E[sens_ent[m][k]][t], t < Tp: the sensor's w entries (one per y tap)
 __global__ void k_adj_sum(Geo G, int nb, int Tp, const float* __restrict__ E, const int* __restrict__ sens_ent,
                           float* __restrict__ g) {
@@ -548,6 +680,11 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
     if ((e = cudaFuncSetAttribute(k_ned_gather_rows<WT, PER, true>, (cudaFuncAttribute)a, (int)c.smem_grad))) return e;
     NEDNER_ATTR_GATHER(8, 16) NEDNER_ATTR_GATHER(12, 16) NEDNER_ATTR_GATHER(16, 16) NEDNER_ATTR_GATHER(20, 16)
 #undef NEDNER_ATTR_GATHER
+#define NEDNER_ATTR_GATHER2(WT)                                                                             \
+    if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, false>, (cudaFuncAttribute)a, (int)c.smem_adj))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, true>, (cudaFuncAttribute)a, (int)c.smem_grad))) return e;
+    NEDNER_ATTR_GATHER2(8) NEDNER_ATTR_GATHER2(12) NEDNER_ATTR_GATHER2(16) NEDNER_ATTR_GATHER2(20)
+#undef NEDNER_ATTR_GATHER2
     return cudaSuccess;
 }
 
@@ -610,6 +747,12 @@ cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E,
     for (int nb = 0; nb < G.Nt; nb += Tp) {
         const dim3 grid(G.Ly, Tp / C);
 #define NEDNER_ADJ(WT)                                                                                            \
+    if (p.ch.tpl_adj == 2)                                                                                        \
+        k_ned_gather_rows2<WT, false><<<grid, 256, p.ch.smem_adj, s>>>(G, nb, Tp, R, nullptr, p.t.xrow_ptr,       \
+                                                                       p.t.xrow_first, p.t.xent_m, p.t.xent_bx,    \
+                                                                       p.t.xent_rc, p.t.xent_wx, p.t.xent_wx,      \
+                                                                       p.t.deconv_x, p.t.tw, E, nullptr);          \
+    else                                                                                                          \
     k_ned_gather_rows<WT, 16, false><<<grid, 256, p.ch.smem_adj, s>>>(G, C, nb, Tp, R, nullptr, p.t.xrow_ptr,       \
                                                                       p.t.xrow_first, p.t.xent_m, p.t.xent_bx,      \
                                                                       p.t.xent_rc, p.t.xent_wx, p.t.xent_wx,        \
@@ -627,6 +770,12 @@ cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const fl
     const int C = p.ch.ca;
     const dim3 grid(G.Ly, G.Nt / C);
 #define NEDNER_GRAD(WT)                                                                                          \
+    if (p.ch.tpl_adj == 2)                                                                                        \
+        k_ned_gather_rows2<WT, true><<<grid, 256, p.ch.smem_grad, s>>>(G, 0, G.Nt, R, g, p.t.xrow_ptr,            \
+                                                                       p.t.xrow_first, p.t.xent_m, p.t.xent_bx,    \
+                                                                       p.t.xent_rc, p.t.xent_gx, p.t.xent_gy,      \
+                                                                       p.t.deconv_x, p.t.tw, nullptr, Qe);         \
+    else                                                                                                          \
     k_ned_gather_rows<WT, 16, true><<<grid, 256, p.ch.smem_grad, s>>>(G, C, 0, G.Nt, R, g, p.t.xrow_ptr,           \
                                                                       p.t.xrow_first, p.t.xent_m, p.t.xent_bx,     \
                                                                       p.t.xent_rc, p.t.xent_gx, p.t.xent_gy,       \
