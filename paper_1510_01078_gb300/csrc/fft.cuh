@@ -298,21 +298,26 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, int N, int Ns, int nb, 
 }
 
 template <int PER, int DIR>
-__device__ __forceinline__ void block_fft_ip_dir(float2* buf, int N, int nb, const float2* __restrict__ tw) {
+__device__ __forceinline__ void block_fft_ip_dir(float2* buf, int N, int nb, const float2* __restrict__ tw,
+                                                 bool skip_r2) {
     __syncthreads();
     int Ns = 1;
     int rem = ilog2(N);
     for (; rem >= 4; rem -= 4, Ns <<= 4) fft_pass_ip<16, DIR, PER>(buf, N, Ns, nb, tw);
     if (rem == 3) fft_pass_ip<8, DIR, PER>(buf, N, Ns, nb, tw);
     else if (rem == 2) fft_pass_ip<4, DIR, PER>(buf, N, Ns, nb, tw);
-    else if (rem == 1) fft_pass_ip<2, DIR, PER>(buf, N, Ns, nb, tw);
+    else if (rem == 1 && !skip_r2) fft_pass_ip<2, DIR, PER>(buf, N, Ns, nb, tw);
 }
 
-// In-place transform of nb columns of length N in a padded buffer.
+// In-place transform of nb columns of length N in a padded buffer.  With
+// skip_r2, a final radix-2 pass (log2 N = 1 mod 4) is left to the caller:
+// the buffer then holds s with X[k] = s[k] + w^k s[k + N/2] and
+// X[k + N/2] = s[k] - w^k s[k + N/2], w = exp(DIR 2 pi i / N).
 template <int PER>
-__device__ __forceinline__ void block_fft_ip(float2* buf, int N, int nb, int dir, const float2* __restrict__ tw) {
-    if (dir < 0) block_fft_ip_dir<PER, -1>(buf, N, nb, tw);
-    else block_fft_ip_dir<PER, +1>(buf, N, nb, tw);
+__device__ __forceinline__ void block_fft_ip(float2* buf, int N, int nb, int dir, const float2* __restrict__ tw,
+                                             bool skip_r2 = false) {
+    if (dir < 0) block_fft_ip_dir<PER, -1>(buf, N, nb, tw, skip_r2);
+    else block_fft_ip_dir<PER, +1>(buf, N, nb, tw, skip_r2);
 }
 
 }  // namespace nedner
