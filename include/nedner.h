@@ -76,7 +76,9 @@ typedef struct {
     int apply_weights;            /* 1: h_m/(dx dy) and W s (the reconstruction R);
                                      0: both replaced by 1 */
     int band_mask;                /* 1: zero F where nu is outside [-Nt/2, Nt/2) */
-    size_t max_workspace_bytes;   /* 0 = no limit; plan fails with ENOMEM above it */
+    size_t max_workspace_bytes;   /* 0 = no limit; plan fails with ENOMEM above it.  Under a
+                                     limit the transposed entry points work in shorter passes
+                                     over the time samples where that lets the plan fit. */
     const double* sensor_w;       /* host [M] detector areas h_m (m^2), or NULL for X Y / M */
     int ned_mode;                 /* NEDNER_NED_NUFFT (default) or NEDNER_NED_TENSOR_BF16, see below */
 } nedner_opts;

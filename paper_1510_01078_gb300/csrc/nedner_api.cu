@@ -541,16 +541,21 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     size_t r_bytes = (size_t)G.nxh * G.Ly * Nt * 8;
     size_t v_bytes = (size_t)G.nxh * G.ny * G.nz * 8;
     size_t gh_bytes = (size_t)G.nxh * G.nyp * Nt * 8;
-    // region B also holds the transposed stage's per-slot partial sums
-    // the transposed gather's entry buffer: M w floats per time sample of a pass,
-    // passes as long as fit in max(region B, 256 MB); the gradient's per-entry sums
+    // Region B also holds the transposed gather's entry buffer (M w floats per
+    // time sample of a pass) and the gradient's per-entry sums.  Passes are as
+    // long as fit in max(Ghat / Y, 256 MB), or, under a workspace limit, in what
+    // the limit leaves beside region A.
+    p->region_a = (std::max(r_bytes, v_bytes) + 255) / 256 * 256;
     const size_t ents = (size_t)M * G.w;
-    const size_t cap = std::max(std::max(gh_bytes, v_bytes), (size_t)256 << 20);
+    size_t cap = std::max(gh_bytes, v_bytes);
+    size_t extra = (size_t)256 << 20;
+    if (o.max_workspace_bytes)
+        extra = std::min(extra, o.max_workspace_bytes > p->region_a ? o.max_workspace_bytes - p->region_a : 0);
+    cap = std::max(cap, extra);
     p->ch.tp_adj = Nt;
     while (p->ch.tp_adj > p->ch.ca && ents * p->ch.tp_adj * 4 > cap) p->ch.tp_adj /= 2;
     size_t pa_bytes = ents * p->ch.tp_adj * 4;
     size_t q_bytes = ents * (Nt / p->ch.ca) * 8;
-    p->region_a = (std::max(r_bytes, v_bytes) + 255) / 256 * 256;
     p->ws_bytes = p->region_a + std::max(std::max(gh_bytes, v_bytes), std::max(pa_bytes, q_bytes));
     if (o.max_workspace_bytes && p->ws_bytes > o.max_workspace_bytes) { delete p; return NEDNER_ENOMEM; }
     cudaError_t e = cudaMalloc(&p->ws, p->ws_bytes);

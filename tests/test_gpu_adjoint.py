@@ -130,3 +130,41 @@ def test_autograd_function(nd):
     assert rel_l2(g.grad.cpu().numpy(), want_g) <= TOL
     assert rel_l2(xy.grad.numpy(), want_xy) <= TOL_GRAD
     plan.close()
+
+
+def test_adjoint_and_grad_wide_rows(nd):
+    """2nx = 512 grid columns: the transposed gather with one time sample per
+    lane (16 per CTA), and its gradient."""
+    case = inputs.small_case(256, 16, 8, 200, 64, seed=31, layout="scatter")
+    rng = np.random.default_rng(131)
+    p = rng.standard_normal((case["nz"], case["ny"], case["nx"]))
+    g = rng.standard_normal((case["sensor_xy"].shape[0], case["Nt"]))
+    pr = problem(case)
+    plan = nd.plan_from_config(case)
+    pt = torch.as_tensor(p, dtype=torch.float32, device="cuda")
+    got = plan.adjoint(pt).cpu().numpy()
+    assert rel_l2(got, oracle.adjoint(pr, p)) <= TOL, rel_l2(got, oracle.adjoint(pr, p))
+    gg = plan.grad_positions(torch.as_tensor(g, dtype=torch.float32, device="cuda"), pt).cpu().numpy()
+    want = oracle.grad_positions(pr, g, p)
+    plan.close()
+    assert rel_l2(gg, want) <= TOL_GRAD, rel_l2(gg, want)
+
+
+def test_adjoint_in_passes_under_workspace_limit(nd):
+    """A workspace limit that leaves room for only part of the entry buffer
+    makes the adjoint run in several passes over the time samples; the result
+    is the same as in one pass."""
+    case = inputs.small_case(16, 16, 16, 600, 256, seed=32, layout="scatter")
+    rng = np.random.default_rng(132)
+    p = rng.standard_normal((case["nz"], case["ny"], case["nx"]))
+    pt = torch.as_tensor(p, dtype=torch.float32, device="cuda")
+    full = nd.plan_from_config(case)
+    a = full.adjoint(pt).cpu().numpy()
+    limit = full.workspace_bytes // 3
+    full.close()
+    tight = nd.plan_from_config(case, max_workspace_bytes=limit)
+    assert tight.workspace_bytes <= limit
+    b = tight.adjoint(pt).cpu().numpy()
+    tight.close()
+    assert rel_l2(b, a) <= 1e-6, rel_l2(b, a)
+    assert rel_l2(b, oracle.adjoint(problem(case), p)) <= TOL
