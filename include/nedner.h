@@ -131,6 +131,20 @@ nedner_status nedner_set_positions(nedner_plan_t plan, const double* sensor_xy);
 nedner_status nedner_forward(nedner_plan_t plan, const float* g, float* p0, void* stream);
 
 /*
+ * nedner_forward with host buffers: p0_host = R g_host, one call for the
+ * upload of g, the reconstruction and the download of p0.  g is uploaded in
+ * four contiguous parts (whole sensor rows) on four copy streams at once, and
+ * p0 is downloaded in four blocks of depth planes, each as soon as the last
+ * inverse FFT has written it.  Asynchronous with respect to the host on
+ * `stream` (the stream's work completes when p0_host holds the result);
+ * page-locked host memory is needed for the copies to run asynchronously.
+ *   g_host   host float [M][Nt], read only;  p0_host  host float [nz][ny][nx], written.
+ * The first call allocates the plan's device copies of g and p0 (M Nt + nx ny nz
+ * floats), the copy streams and their events; later calls allocate nothing.
+ */
+nedner_status nedner_forward_host(nedner_plan_t plan, const float* g_host, float* p0_host, void* stream);
+
+/*
  * g = R^T p0: the exact transpose of nedner_forward (same real-linear map,
  * transposed; spreading and interpolation of both NUFFTs swapped).
  *   p0  device float [nz][ny][nx], read only.

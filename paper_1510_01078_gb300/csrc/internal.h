@@ -118,16 +118,27 @@ struct nedner_plan_s {
     size_t ws_bytes = 0;
     size_t region_a = 0;          // bytes of region A (R / V), region B follows (Ghat / Y)
     int device = 0;
+    // nedner_forward_host: device copies of g and p0, copy streams and their
+    // events (created by the first call)
+    float* host_g = nullptr;
+    float* host_p0 = nullptr;
+    cudaStream_t copy_stream[4] = {};
+    cudaEvent_t host_ev[16] = {};
 };
 
 namespace nedner {
 
 // forward-stage launchers (kernels_fwd.cu); return cudaGetLastError()
-cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float2* R, cudaStream_t s);
-cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s);
+// the spread and y-FFT stages for time samples [t0, t0 + nt) (nt < 0: to the
+// end; t0 and nt multiples of 64), the x-c2r stage for depth planes [z0, z0 + nzc)
+cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float2* R, cudaStream_t s, int t0 = 0,
+                                   int nt = -1);
+cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s, int t0 = 0,
+                            int nt = -1);
 cudaError_t launch_ner_lines(const nedner_plan_s& p, const float2* Ghat, float2* V, cudaStream_t s);
 cudaError_t launch_img_yifft(const nedner_plan_s& p, const float2* V, float2* Y, cudaStream_t s);
-cudaError_t launch_img_xc2r(const nedner_plan_s& p, const float2* Y, float* p0, cudaStream_t s);
+cudaError_t launch_img_xc2r(const nedner_plan_s& p, const float2* Y, float* p0, cudaStream_t s, int z0 = 0,
+                            int nzc = -1);
 cudaError_t configure_fwd_kernels(const nedner_plan_s& p);
 
 // transposed-stage launchers (kernels_adj.cu)

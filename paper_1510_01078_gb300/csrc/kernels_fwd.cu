@@ -126,7 +126,7 @@ __device__ __forceinline__ void spread_output(const Geo& G, const float2* Z, int
 }
 
 template <int WT, int PER>
-__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_spread_xfft(Geo G, int C, const float* __restrict__ g,
+__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_spread_xfft(Geo G, int C, int yb, const float* __restrict__ g,
                                                                           const int4* __restrict__ seg,
                                                                           const int* __restrict__ xent_m,
                                                                           const float* __restrict__ xent_wx,
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_spread_xfft(Geo 
     float* Zf = reinterpret_cast<float*>(Z);
     const int zlen = (padded_len(Lx * nb) + 1) & ~1;
     const int gy = blockIdx.x;
-    const int n0 = blockIdx.y * C;
+    const int n0 = (yb + blockIdx.y) * C;
     const int lc = ilog2(C);
     const int groups = NT >> lc;
     const int q = threadIdx.x >> lc;
@@ -268,7 +268,7 @@ __device__ __forceinline__ void sweep_entry2(float2 (&acc)[2 * WT], float2* Z, i
 }
 
 template <int WT, int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo G, const float* __restrict__ g,
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo G, int yb, const float* __restrict__ g,
                                                              const int4* __restrict__ seg,
                                                              const int* __restrict__ xent_m,
                                                              const float* __restrict__ xent_wx,
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
     float2* Z = reinterpret_cast<float2*>(smem4);                  // [Lx][32] complex row, padded
     const int zlen = (padded_len(Lx * NB) + 1) & ~1;
     const int gy = blockIdx.x;
-    const int n0 = blockIdx.y * C;
+    const int n0 = (yb + blockIdx.y) * C;
     const int q = threadIdx.x >> 5;                                // lane group = warp
     const int ln = threadIdx.x & 31;
 
@@ -366,13 +366,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
 // runs in place in a padded buffer, Ly * C <= 256 PER (PER values per thread).
 // ---------------------------------------------------------------------------
 template <int PER>
-__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int C, const float2* __restrict__ R,
+__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int C, int yb, const float2* __restrict__ R,
                                                      const float* __restrict__ deconv_y,
                                                      const float2* __restrict__ tw, float2* __restrict__ Ghat) {
     extern __shared__ float4 smem4[];
     float2* A = reinterpret_cast<float2*>(smem4);   // [Ly][C], padded
     const int jx = blockIdx.x;
-    const int n0 = blockIdx.y * C;
+    const int n0 = (yb + blockIdx.y) * C;
     const int lc = ilog2(C);
 #pragma unroll 8
     for (int it = threadIdx.x; it < G.Ly * C; it += 256) {
@@ -630,7 +630,7 @@ __global__ void __launch_bounds__(256) k_img_yifft(Geo G, int C, const float2* _
 // E = X[k] + conj X[H-k], O = (X[k] - conj X[H-k]) exp(2 pi i k / nx),
 // z = IFFT_H(Z), p0[2p] = Re z[p], p0[2p+1] = Im z[p].
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, const float2* __restrict__ Y,
+__global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, int zb, const float2* __restrict__ Y,
                                                   const float2* __restrict__ tw, float* __restrict__ p0) {
     extern __shared__ float4 smem4[];
     const int H = G.nx / 2;
@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, const float2* __
     float2* X = reinterpret_cast<float2*>(smem4);   // [H+1][ld]
     float2* A = X + (size_t)(H + 1) * ld;           // [H][ld]
     float2* B = A + (size_t)H * ld;                 // [H][ld]
-    const int qz = blockIdx.x;
+    const int qz = zb + blockIdx.x;
     const int y0 = blockIdx.y * C;
     const int lc = ilog2(C), lh = ilog2(H);
 #pragma unroll 8
@@ -700,22 +700,25 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     return cudaSuccess;
 }
 
-cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float2* R, cudaStream_t s) {
+cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float2* R, cudaStream_t s, int t0,
+                                   int nt) {
     const Geo& G = p.geo;
-    dim3 grid(G.Ly, G.Nt / p.ch.c1);
-#define NEDNER_SPREAD(WT)                                                                                   \
-    if (p.ch.tpl1 == 2 && p.ch.threads1 <= 256)                                                             \
-        k_ned_spread2_xfft<WT, 256><<<grid, 256, p.ch.smem1, s>>>(G, g, p.t.seg, p.t.xent_m, p.t.xent_wx,  \
-                                                                  p.t.xent_bx, p.t.deconv_x, p.t.tw, R);    \
-    else if (p.ch.tpl1 == 2)                                                                                \
-        k_ned_spread2_xfft<WT, 512><<<grid, 512, p.ch.smem1, s>>>(G, g, p.t.seg, p.t.xent_m, p.t.xent_wx,  \
-                                                                  p.t.xent_bx, p.t.deconv_x, p.t.tw, R);    \
+    if (nt < 0) nt = G.Nt - t0;
+    const int yb = t0 / p.ch.c1;
+    dim3 grid(G.Ly, nt / p.ch.c1);
+#define NEDNER_SPREAD(WT)                                                                                        \
+    if (p.ch.tpl1 == 2 && p.ch.threads1 <= 256)                                                                  \
+        k_ned_spread2_xfft<WT, 256><<<grid, 256, p.ch.smem1, s>>>(G, yb, g, p.t.seg, p.t.xent_m, p.t.xent_wx,   \
+                                                                  p.t.xent_bx, p.t.deconv_x, p.t.tw, R);         \
+    else if (p.ch.tpl1 == 2)                                                                                     \
+        k_ned_spread2_xfft<WT, 512><<<grid, 512, p.ch.smem1, s>>>(G, yb, g, p.t.seg, p.t.xent_m, p.t.xent_wx,   \
+                                                                  p.t.xent_bx, p.t.deconv_x, p.t.tw, R);         \
     else if (p.ch.per1 <= 16)                                                                                    \
-        k_ned_spread_xfft<WT, 16><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
-                                                                p.t.xent_bx, p.t.deconv_x, p.t.tw, R);      \
-    else                                                                                                    \
-        k_ned_spread_xfft<WT, 32><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, g, p.t.seg, p.t.xent_m, p.t.xent_wx, \
-                                                                p.t.xent_bx, p.t.deconv_x, p.t.tw, R)
+        k_ned_spread_xfft<WT, 16><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, yb, g, p.t.seg, p.t.xent_m,         \
+                                                                p.t.xent_wx, p.t.xent_bx, p.t.deconv_x, p.t.tw, R); \
+    else                                                                                                         \
+        k_ned_spread_xfft<WT, 32><<<grid, 256, p.ch.smem1, s>>>(G, p.ch.c1, yb, g, p.t.seg, p.t.xent_m,         \
+                                                                p.t.xent_wx, p.t.xent_bx, p.t.deconv_x, p.t.tw, R)
     switch (spread_taps(G.w)) {
         case 8: NEDNER_SPREAD(8); break;
         case 12: NEDNER_SPREAD(12); break;
@@ -726,13 +729,15 @@ cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float
     return cudaGetLastError();
 }
 
-cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s) {
+cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s, int t0, int nt) {
     const Geo& G = p.geo;
-    dim3 grid(G.nxh, G.Nt / p.ch.c2f);
+    if (nt < 0) nt = G.Nt - t0;
+    const int yb = t0 / p.ch.c2f;
+    dim3 grid(G.nxh, nt / p.ch.c2f);
     if ((long)G.Ly * p.ch.c2f <= 16L * 256)
-        k_ned_yfft<16><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, R, p.t.deconv_y, p.t.tw, Ghat);
+        k_ned_yfft<16><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, yb, R, p.t.deconv_y, p.t.tw, Ghat);
     else
-        k_ned_yfft<32><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, R, p.t.deconv_y, p.t.tw, Ghat);
+        k_ned_yfft<32><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, yb, R, p.t.deconv_y, p.t.tw, Ghat);
     return cudaGetLastError();
 }
 
@@ -766,10 +771,11 @@ cudaError_t launch_img_yifft(const nedner_plan_s& p, const float2* V, float2* Y,
     return cudaGetLastError();
 }
 
-cudaError_t launch_img_xc2r(const nedner_plan_s& p, const float2* Y, float* p0, cudaStream_t s) {
+cudaError_t launch_img_xc2r(const nedner_plan_s& p, const float2* Y, float* p0, cudaStream_t s, int z0, int nzc) {
     const Geo& G = p.geo;
-    dim3 grid(G.nz, G.ny / p.ch.c5);
-    k_img_xc2r<<<grid, 256, p.ch.smem5, s>>>(G, p.ch.c5, Y, p.t.tw, p0);
+    if (nzc < 0) nzc = G.nz - z0;
+    dim3 grid(nzc, G.ny / p.ch.c5);
+    k_img_xc2r<<<grid, 256, p.ch.smem5, s>>>(G, p.ch.c5, z0, Y, p.t.tw, p0);
     return cudaGetLastError();
 }
 

@@ -706,6 +706,62 @@ nedner_status nedner_device_status(nedner_plan_t p, int* flags) {
 
 size_t nedner_workspace_bytes(nedner_plan_t p) { return p ? p->ws_bytes : 0; }
 
+nedner_status nedner_forward_host(nedner_plan_t p, const float* g_host, float* p0_host, void* stream) {
+    if (!p || !p0_host || (p->M > 0 && !g_host)) return NEDNER_EINVAL;
+    const Geo& G = p->geo;
+    constexpr int NCS = 4;                               // copy streams (several copy engines at once)
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    const size_t gbytes = (size_t)p->M * G.Nt * sizeof(float);
+    const size_t pbytes = (size_t)G.nx * G.ny * G.nz * sizeof(float);
+    if (!p->host_p0) {
+        // first call: device copies of g and p0, the copy streams and their events
+        if (!e && gbytes) e = cudaMalloc((void**)&p->host_g, gbytes);
+        if (!e) e = cudaMalloc((void**)&p->host_p0, pbytes);
+        for (int i = 0; i < NCS && !e; ++i) e = cudaStreamCreateWithFlags(&p->copy_stream[i], cudaStreamNonBlocking);
+        for (int i = 0; i < 16 && !e; ++i) e = cudaEventCreateWithFlags(&p->host_ev[i], cudaEventDisableTiming);
+        if (e) return e == cudaErrorMemoryAllocation ? NEDNER_ENOMEM : NEDNER_ECUDA;
+    }
+    cudaStream_t* cs = p->copy_stream;
+    cudaEvent_t* ev = p->host_ev;
+    float2* A = (float2*)p->ws;
+    float2* B = (float2*)((char*)p->ws + p->region_a);
+    // upload g in NCS contiguous parts (whole sensor rows), one per copy stream,
+    // after the work already queued on the caller's stream
+    if ((e = cudaEventRecord(ev[0], s))) return run(e);
+    const int64_t mp = (p->M + NCS - 1) / NCS;
+    for (int i = 0; i < NCS; ++i) {
+        const int64_t m0 = std::min<int64_t>(p->M, i * mp), m1 = std::min<int64_t>(p->M, m0 + mp);
+        if ((e = cudaStreamWaitEvent(cs[i], ev[0], 0))) return run(e);
+        if (m1 > m0 && (e = cudaMemcpyAsync(p->host_g + m0 * G.Nt, g_host + m0 * G.Nt,
+                                            (size_t)(m1 - m0) * G.Nt * sizeof(float), cudaMemcpyHostToDevice, cs[i])))
+            return run(e);
+        if ((e = cudaEventRecord(ev[1 + i], cs[i])) || (e = cudaStreamWaitEvent(s, ev[1 + i], 0))) return run(e);
+    }
+    if (p->tp.enabled) {
+        if ((e = launch_tp_ned(*p, p->host_g, B, s))) return run(e);
+    } else {
+        if ((e = launch_ned_spread_xfft(*p, p->host_g, A, s))) return run(e);
+        if ((e = launch_ned_yfft(*p, A, B, s))) return run(e);
+    }
+    if ((e = launch_ner_lines(*p, B, A, s))) return run(e);
+    if ((e = launch_img_yifft(*p, A, B, s))) return run(e);
+    // p0 in NCS blocks of depth planes, each downloaded as soon as it is written
+    const int zc = (G.nz + NCS - 1) / NCS;
+    for (int i = 0; i * zc < G.nz; ++i) {
+        const int z0 = i * zc, nzc = std::min(zc, G.nz - z0);
+        if ((e = launch_img_xc2r(*p, B, p->host_p0, s, z0, nzc))) return run(e);
+        if ((e = cudaEventRecord(ev[5 + i], s)) || (e = cudaStreamWaitEvent(cs[i], ev[5 + i], 0))) return run(e);
+        const size_t off = (size_t)z0 * G.ny * G.nx, cnt = (size_t)nzc * G.ny * G.nx * sizeof(float);
+        if ((e = cudaMemcpyAsync(p0_host + off, p->host_p0 + off, cnt, cudaMemcpyDeviceToHost, cs[i]))) return run(e);
+        if ((e = cudaEventRecord(ev[9 + i], cs[i]))) return run(e);
+    }
+    // the caller's stream completes when p0 has arrived
+    for (int i = 0; i * zc < G.nz; ++i)
+        if ((e = cudaStreamWaitEvent(s, ev[9 + i], 0))) return run(e);
+    return NEDNER_OK;
+}
+
 nedner_status nedner_destroy(nedner_plan_t p) {
     if (!p) return NEDNER_OK;
     cudaSetDevice(p->device);
@@ -713,6 +769,12 @@ nedner_status nedner_destroy(nedner_plan_t p) {
     free_tables(p->t);
     free_tp(p->tp);
     cudaFree(p->ws);
+    cudaFree(p->host_g);
+    cudaFree(p->host_p0);
+    for (cudaEvent_t& ev : p->host_ev)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t& cs : p->copy_stream)
+        if (cs) cudaStreamDestroy(cs);
     delete p;
     return NEDNER_OK;
 }

@@ -61,6 +61,7 @@ SIGNATURES = {
     "nedner_forward_profiled": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
     "nedner_ned_stage_static": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "nedner_forward_host": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_device_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "nedner_destroy": (ctypes.c_int, [_P]),
     "nedner_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -102,6 +103,16 @@ def _dev_ptr(t, dtype, shape: Sequence[int], name: str):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s tensor of shape %s (got %s %s)"
+                         % (name, dtype, tuple(shape), t.dtype, tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t, dtype, shape: Sequence[int], name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a host (CPU) tensor" % name)
     if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError("%s must be a contiguous %s tensor of shape %s (got %s %s)"
                          % (name, dtype, tuple(shape), t.dtype, tuple(t.shape)))
@@ -176,6 +187,20 @@ class Plan:
                                     _dev_ptr(out, torch.float32, (self.nz, self.ny, self.nx), "p0"),
                                     _stream_ptr(stream))
         _check(st, "nedner_forward")
+        return out
+
+    def forward_host(self, g, out=None, stream=None):
+        """p0 = R g with host tensors (``nedner_forward_host``): the uploads of g
+        and downloads of p0 overlap the kernels.  g: (M, Nt) float32 CPU tensor
+        (pinned for overlap) -> (nz, ny, nx) CPU tensor, valid once ``stream``
+        has completed (the call returns before)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.nz, self.ny, self.nx), dtype=torch.float32, pin_memory=True)
+        st = _load().nedner_forward_host(self._handle, _host_ptr(g, torch.float32, (self.M, self.Nt), "g"),
+                                         _host_ptr(out, torch.float32, (self.nz, self.ny, self.nx), "p0"),
+                                         _stream_ptr(stream))
+        _check(st, "nedner_forward_host")
         return out
 
     FORWARD_KERNELS = ("ned_spread_xfft", "ned_yfft", "ner_lines", "img_yifft", "img_xc2r")

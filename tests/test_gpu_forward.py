@@ -162,3 +162,36 @@ def test_set_positions_matches_fresh_plan(nd):
     want = oracle.forward(problem(case2), case["g"])
     assert rel_l2(a, want) <= TOL
     plan.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+def test_forward_host_matches_device_call(nd, pinned):
+    """nedner_forward_host (host buffers uploaded on several copy streams, the
+    last stage run per block of depth planes, each downloaded as it is written)
+    gives the device call's result on the C2 geometry."""
+    case = inputs.make_config(1, with_data=False)
+    rng = np.random.default_rng(77)
+    g = rng.standard_normal((case["sensor_xy"].shape[0], case["Nt"])).astype(np.float32)
+    plan = nd.plan_from_config(case)
+    want = plan.forward(torch.as_tensor(g, device="cuda")).cpu().numpy()
+    gh = torch.as_tensor(g)
+    out = torch.empty((case["nz"], case["ny"], case["nx"]), dtype=torch.float32)
+    if pinned:
+        gh, out = gh.pin_memory(), out.pin_memory()
+    for _ in range(2):                                     # the first call sets up, the second reuses
+        out.zero_()
+        plan.forward_host(gh, out=out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.numpy(), want)
+    plan.close()
+
+
+def test_forward_host_small_and_ragged(nd):
+    """Host-buffer call on a small case (fewer depth planes than copy streams would split evenly), against the oracle."""
+    case = inputs.small_case(16, 16, 32, 61, 64, seed=9, layout="disc")
+    g = np.asarray(case["g"], dtype=np.float32)
+    plan = nd.plan_from_config(case)
+    out = plan.forward_host(torch.as_tensor(g).pin_memory())
+    torch.cuda.synchronize()
+    plan.close()
+    assert rel_l2(out.numpy(), oracle.forward(problem(case), g)) <= TOL
