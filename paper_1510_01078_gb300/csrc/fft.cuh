@@ -1,12 +1,12 @@
 // Batched in-shared-memory FFTs used by every stage of the NEDNER path.
 //
 // Each call transforms nb columns (nb a power of two) of length N (a power of
-// two, 2..8192) that sit in shared memory as buf[p * ld + b] (point p,
-// column b).  The whole thread block cooperates; the call begins and ends
-// with __syncthreads().  The algorithm is the self-sorting (Stockham)
+// two, 2..8192) that sit in shared memory, point p of column b at linear
+// index p * nb + b.  The whole thread block cooperates; the call begins and
+// ends with __syncthreads().  The algorithm is the self-sorting (Stockham)
 // formulation: log2(N) is covered by radix-16 passes (4 x 4 decomposition in
-// registers) plus one radix-2, -4 or -8 pass, each pass reading one buffer
-// and writing the other, so no bit-reversal step is needed.
+// registers) plus one radix-2, -4 or -8 pass, so no bit-reversal step is
+// needed.
 //
 //   DIR = -1 : X[k] = sum_p x[p] exp(-2 pi i k p / N)
 //   DIR = +1 : X[k] = sum_p x[p] exp(+2 pi i k p / N)     (unnormalised)
@@ -124,88 +124,9 @@ __device__ __forceinline__ constexpr int out_index(int k) {
     return R == 8 ? 4 * (k & 1) + (k >> 1) : R == 16 ? 4 * (k & 3) + (k >> 2) : k;
 }
 
-// One Stockham pass of radix R over all columns: src -> dst (nb a power of two).
-template <int R, int DIR>
-__device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2* __restrict__ dst, int N,
-                                         int Ns, int nb, int ld, const float2* __restrict__ tw) {
-    const int stride = N / R;
-    const int lnb = ilog2(nb);
-    const int items = stride << lnb;
-    const int step = N / (Ns * R);
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int j = it >> lnb;
-        const int b = it & (nb - 1);
-        const int k = j & (Ns - 1);
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(j + r * stride) * ld + b];
-        if (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, k * r * step, N, DIR));
-        }
-        dft_reg<R, DIR>(v);
-        const int i0 = (j - k) * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) dst[(i0 + r * Ns) * ld + b] = v[out_index<R>(r)];
-    }
-}
-
-template <int DIR>
-__device__ __forceinline__ float2* block_fft_dir(float2* a, float2* b, int N, int nb, int ld,
-                                                 const float2* __restrict__ tw) {
-    __syncthreads();
-    float2* src = a;
-    float2* dst = b;
-    int Ns = 1;
-    int rem = ilog2(N);
-    // first pass: radix 2^(rem mod 4); a single-column transform starts with
-    // radix 4 at most, so that neighbouring threads' first-pass stores
-    // (stride R) stay within few banks
-    int first = rem & 3;
-    if (nb == 1 && first == 0 && rem >= 4) first = 2;
-    if (nb == 1 && first == 3) first = 1;
-    if (first) {
-        if (first == 1) fft_pass<2, DIR>(src, dst, N, Ns, nb, ld, tw);
-        else if (first == 2) fft_pass<4, DIR>(src, dst, N, Ns, nb, ld, tw);
-        else fft_pass<8, DIR>(src, dst, N, Ns, nb, ld, tw);
-        Ns <<= first;
-        rem -= first;
-        __syncthreads();
-        float2* t = src; src = dst; dst = t;
-    }
-    while (rem > 0) {
-        if (rem >= 4) {
-            fft_pass<16, DIR>(src, dst, N, Ns, nb, ld, tw);
-            Ns <<= 4;
-            rem -= 4;
-        } else if (rem == 3) {
-            fft_pass<8, DIR>(src, dst, N, Ns, nb, ld, tw);
-            Ns <<= 3;
-            rem -= 3;
-        } else if (rem == 2) {
-            fft_pass<4, DIR>(src, dst, N, Ns, nb, ld, tw);
-            Ns <<= 2;
-            rem -= 2;
-        } else {
-            fft_pass<2, DIR>(src, dst, N, Ns, nb, ld, tw);
-            Ns <<= 1;
-            rem -= 1;
-        }
-        __syncthreads();
-        float2* t = src; src = dst; dst = t;
-    }
-    return src;
-}
-
-// Transform; returns the buffer (a or b) that holds the result.
-__device__ __forceinline__ float2* block_fft(float2* a, float2* b, int N, int nb, int ld, int dir,
-                                             const float2* __restrict__ tw) {
-    return dir < 0 ? block_fft_dir<-1>(a, b, N, nb, ld, tw) : block_fft_dir<+1>(a, b, N, nb, ld, tw);
-}
-
 // ---------------------------------------------------------------------------
-// In-place variant.  Every thread keeps its share of a pass in registers, so
-// one buffer holds the data throughout; the caller guarantees
+// In place: every thread keeps its share of a pass in registers, so one
+// buffer holds the data throughout; the caller guarantees
 // N * nb <= PER * blockDim.x (PER a multiple of 16).  The buffer is padded:
 // linear index a = p * nb + b (point p, column b) lives at padx(a), one spare
 // slot after every 16 values.  With the radix-16 passes first and the

@@ -24,62 +24,66 @@ namespace nedner {
 // ---------------------------------------------------------------------------
 // Transpose of img_xc2r: Y[kx] = d_kx sum_qx p[qx] exp(-2 pi i kx qx / nx),
 // kx = 0..nx/2, d = 1 at kx = 0, nx/2 and 2 otherwise.  Real-to-complex FFT
-// through the half-length complex transform of z[p] = x[2p] + i x[2p+1].
+// through the half-length complex transform of z[p] = x[2p] + i x[2p+1],
+// in place in a padded buffer, H * C <= 16 NT.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_img_xr2c_adj(Geo G, int C, const float* __restrict__ p0,
-                                                      const float2* __restrict__ tw, float2* __restrict__ Y) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) k_img_xr2c_adj(Geo G, int C, const float* __restrict__ p0,
+                                                             const float2* __restrict__ tw, float2* __restrict__ Y) {
     extern __shared__ float4 smem4[];
     const int H = G.nx / 2;
-    const int ld = C + 1;
-    float2* A = reinterpret_cast<float2*>(smem4);   // [H][ld]
-    float2* B = A + (size_t)H * ld;                 // [H][ld]
+    float2* A = reinterpret_cast<float2*>(smem4);   // [H][C], padded
     const int qz = blockIdx.x;
     const int y0 = blockIdx.y * C;
     const int lc = ilog2(C), lh = ilog2(H);
-#pragma unroll 8
-    for (int it = threadIdx.x; it < H * C; it += blockDim.x) {
+    const float2* src = reinterpret_cast<const float2*>(p0 + ((size_t)qz * G.ny + y0) * G.nx);
+#pragma unroll 4
+    for (int it = threadIdx.x; it < H * C; it += NT) {
         const int c = it >> lh;
         const int pp = it & (H - 1);
-        A[pp * ld + c] = reinterpret_cast<const float2*>(p0 + ((size_t)qz * G.ny + y0 + c) * G.nx)[pp];
+        A[padx(pp * C + c)] = src[it];
     }
-    float2* Z = block_fft(A, B, H, C, ld, -1, tw);
-    for (int it = threadIdx.x; it < (H + 1) * C; it += blockDim.x) {
+    block_fft_ip<16>(A, H, C, -1, tw);
+    const size_t kstride = (size_t)G.nz * G.ny;
+    float2* dst = Y + (size_t)qz * G.ny + y0;
+#pragma unroll 4
+    for (int it = threadIdx.x; it < (H + 1) * C; it += NT) {
         const int k = it >> lc;
         const int c = it & (C - 1);
-        const float2 zk = Z[(k & (H - 1)) * ld + c];
-        const float2 zm = cconj(Z[((H - k) & (H - 1)) * ld + c]);
+        const float2 zk = A[padx(((k & (H - 1)) << lc) + c)];
+        const float2 zm = cconj(A[padx((((H - k) & (H - 1)) << lc) + c)]);
         const float2 E = cscale(cadd(zk, zm), 0.5f);
         const float2 O = cscale(mul_i(csub(zk, zm), -1), 0.5f);     // (zk - zm) / (2i)
         float2 X = cadd(E, cmul(twiddle(tw, k & (G.nx - 1), G.nx, -1), O));
         if (k != 0 && k != H) X = cscale(X, 2.f);
-        Y[((size_t)k * G.nz + qz) * G.ny + y0 + c] = X;
+        dst[k * kstride + c] = X;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Transpose of img_yifft: V[kx][ky][qz] = sum_qy exp(-2 pi i ky qy / ny) Y[kx][qz][qy].
+// Transpose of img_yifft: V[kx][ky][qz] = sum_qy exp(-2 pi i ky qy / ny) Y[kx][qz][qy],
+// in place in a padded buffer, ny * C <= 16 NT.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_img_yfft_adj(Geo G, int C, const float2* __restrict__ Y,
-                                                      const float2* __restrict__ tw, float2* __restrict__ V) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) k_img_yfft_adj(Geo G, int C, const float2* __restrict__ Y,
+                                                             const float2* __restrict__ tw, float2* __restrict__ V) {
     extern __shared__ float4 smem4[];
-    const int ld = C + 1;
-    float2* A = reinterpret_cast<float2*>(smem4);
-    float2* B = A + (size_t)G.ny * ld;
+    float2* A = reinterpret_cast<float2*>(smem4);   // [ny][C], padded
     const int kx = blockIdx.x;
     const int z0 = blockIdx.y * C;
     const int lc = ilog2(C), lny = ilog2(G.ny);
-#pragma unroll 8
-    for (int it = threadIdx.x; it < G.ny * C; it += blockDim.x) {
+    const float2* src = Y + ((size_t)kx * G.nz + z0) * G.ny;
+#pragma unroll 4
+    for (int it = threadIdx.x; it < G.ny * C; it += NT) {
         const int c = it >> lny;
         const int qy = it & (G.ny - 1);
-        A[qy * ld + c] = Y[((size_t)kx * G.nz + z0 + c) * G.ny + qy];
+        A[padx(qy * C + c)] = src[it];
     }
-    float2* res = block_fft(A, B, G.ny, C, ld, -1, tw);
-    for (int it = threadIdx.x; it < G.ny * C; it += blockDim.x) {
-        const int ky = it >> lc;
-        const int c = it & (C - 1);
-        V[((size_t)kx * G.ny + ky) * G.nz + z0 + c] = res[ky * ld + c];
-    }
+    block_fft_ip<16>(A, G.ny, C, -1, tw);
+    float2* dst = V + (size_t)kx * G.ny * G.nz + z0;
+#pragma unroll 8
+    for (int it = threadIdx.x; it < G.ny * C; it += NT)
+        dst[(size_t)(it >> lc) * G.nz + (it & (C - 1))] = A[padx(it)];
 }
 
 // ---------------------------------------------------------------------------
@@ -663,10 +667,11 @@ __global__ void k_grad_sum(Geo G, int nch, const float2* __restrict__ Qe, const 
 cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
     const Chunks& c = p.ch;
     const Geo& G = p.geo;
-    const size_t s_xr2c = (size_t)2 * (G.nx / 2) * (c.c5 + 1) * 8;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_img_xr2c_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_xr2c))) return e;
-    if ((e = cudaFuncSetAttribute(k_img_yfft_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem4))) return e;
+    if ((e = cudaFuncSetAttribute(k_img_xr2c_adj<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem5)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_img_yfft_adj<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem4)))
+        return e;
     const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
 #define NEDNER_ATTR_NER(W, D)                                                                                      \
     if ((e = cudaFuncSetAttribute(k_ner_lines_adj<W, D, 256>, (cudaFuncAttribute)a, (int)c.smem3))) return e; \
@@ -690,14 +695,13 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
 
 cudaError_t launch_img_xr2c_adj(const nedner_plan_s& p, const float* p0, float2* Y, cudaStream_t s) {
     const Geo& G = p.geo;
-    const size_t smem = (size_t)2 * (G.nx / 2) * (p.ch.c5 + 1) * 8;
-    k_img_xr2c_adj<<<dim3(G.nz, G.ny / p.ch.c5), 256, smem, s>>>(G, p.ch.c5, p0, p.t.tw, Y);
+    k_img_xr2c_adj<128><<<dim3(G.nz, G.ny / p.ch.c5), 128, p.ch.smem5, s>>>(G, p.ch.c5, p0, p.t.tw, Y);
     return cudaGetLastError();
 }
 
 cudaError_t launch_img_yfft_adj(const nedner_plan_s& p, const float2* Y, float2* V, cudaStream_t s) {
     const Geo& G = p.geo;
-    k_img_yfft_adj<<<dim3(G.nxh, G.nz / p.ch.c4), 256, p.ch.smem4, s>>>(G, p.ch.c4, Y, p.t.tw, V);
+    k_img_yfft_adj<128><<<dim3(G.nxh, G.nz / p.ch.c4), 128, p.ch.smem4, s>>>(G, p.ch.c4, Y, p.t.tw, V);
     return cudaGetLastError();
 }
 

@@ -597,28 +597,29 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, cons
 
 // ---------------------------------------------------------------------------
 // Stage (d), y part: inverse FFT along ky for one kx and C depth planes,
-// written transposed as Y[kx][qz][qy].
+// written transposed as Y[kx][qz][qy].  In-place padded FFT, ny * C <= 16 NT;
+// with C <= 16 both the column loads and the row stores of the padded buffer
+// are free of bank conflicts.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_img_yifft(Geo G, int C, const float2* __restrict__ V,
-                                                   const float2* __restrict__ tw, float2* __restrict__ Y) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) k_img_yifft(Geo G, int C, const float2* __restrict__ V,
+                                                          const float2* __restrict__ tw, float2* __restrict__ Y) {
     extern __shared__ float4 smem4[];
-    const int ld = C + 1;
-    float2* A = reinterpret_cast<float2*>(smem4);
-    float2* B = A + (size_t)G.ny * ld;
+    float2* A = reinterpret_cast<float2*>(smem4);   // [ny][C], padded
     const int kx = blockIdx.x;
     const int z0 = blockIdx.y * C;
     const int lc = ilog2(C), lny = ilog2(G.ny);
+    const float2* src = V + (size_t)kx * G.ny * G.nz + z0;
 #pragma unroll 8
-    for (int it = threadIdx.x; it < G.ny * C; it += blockDim.x) {
-        const int ky = it >> lc;
-        const int c = it & (C - 1);
-        A[ky * ld + c] = V[((size_t)kx * G.ny + ky) * G.nz + z0 + c];
-    }
-    float2* res = block_fft(A, B, G.ny, C, ld, +1, tw);
-    for (int it = threadIdx.x; it < G.ny * C; it += blockDim.x) {
+    for (int it = threadIdx.x; it < G.ny * C; it += NT)
+        A[padx(it)] = src[(size_t)(it >> lc) * G.nz + (it & (C - 1))];
+    block_fft_ip<16>(A, G.ny, C, +1, tw);
+    float2* dst = Y + ((size_t)kx * G.nz + z0) * G.ny;
+#pragma unroll 4
+    for (int it = threadIdx.x; it < G.ny * C; it += NT) {
         const int c = it >> lny;
         const int qy = it & (G.ny - 1);
-        Y[((size_t)kx * G.nz + z0 + c) * G.ny + qy] = res[qy * ld + c];
+        dst[it] = A[padx(qy * C + c)];
     }
 }
 
@@ -629,30 +630,26 @@ __global__ void __launch_bounds__(256) k_img_yifft(Geo G, int C, const float2* _
 // half-length complex transform: Z[k] = E[k] + i O[k],
 // E = X[k] + conj X[H-k], O = (X[k] - conj X[H-k]) exp(2 pi i k / nx),
 // z = IFFT_H(Z), p0[2p] = Re z[p], p0[2p+1] = Im z[p].
+// The pair (k, H-k) is formed by one thread from one load of each:
+// Z[H-k] = conj E[k] + i conj O[k].  In-place padded FFT, H * C <= 16 NT.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, int zb, const float2* __restrict__ Y,
-                                                  const float2* __restrict__ tw, float* __restrict__ p0) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) k_img_xc2r(Geo G, int C, int zb, const float2* __restrict__ Y,
+                                                         const float2* __restrict__ tw, float* __restrict__ p0) {
     extern __shared__ float4 smem4[];
     const int H = G.nx / 2;
-    const int ld = C + 1;
-    float2* X = reinterpret_cast<float2*>(smem4);   // [H+1][ld]
-    float2* A = X + (size_t)(H + 1) * ld;           // [H][ld]
-    float2* B = A + (size_t)H * ld;                 // [H][ld]
+    float2* A = reinterpret_cast<float2*>(smem4);   // [H][C], padded
     const int qz = zb + blockIdx.x;
     const int y0 = blockIdx.y * C;
     const int lc = ilog2(C), lh = ilog2(H);
-#pragma unroll 8
-    for (int it = threadIdx.x; it < (H + 1) * C; it += blockDim.x) {
-        const int kx = it >> lc;
-        const int c = it & (C - 1);
-        X[kx * ld + c] = Y[((size_t)kx * G.nz + qz) * G.ny + y0 + c];
-    }
-    __syncthreads();
-    for (int it = threadIdx.x; it < H * C; it += blockDim.x) {
+    const size_t kstride = (size_t)G.nz * G.ny;
+    const float2* src = Y + (size_t)qz * G.ny + y0;
+#pragma unroll 4
+    for (int it = threadIdx.x; it < (H / 2 + 1) * C; it += NT) {
         const int k = it >> lc;
         const int c = it & (C - 1);
-        float2 xk = X[k * ld + c];
-        float2 xm = X[(H - k) * ld + c];
+        float2 xk = src[k * kstride + c];
+        float2 xm = src[(H - k) * kstride + c];
         if (k == 0) {
             xk.y = 0.f;
             xm.y = 0.f;
@@ -660,14 +657,16 @@ __global__ void __launch_bounds__(256) k_img_xc2r(Geo G, int C, int zb, const fl
         const float2 xmc = cconj(xm);
         const float2 E = cadd(xk, xmc);
         const float2 O = cmul(csub(xk, xmc), twiddle(tw, k, G.nx, +1));
-        A[k * ld + c] = cadd(E, mul_i(O, +1));
+        A[padx((k << lc) + c)] = cadd(E, mul_i(O, +1));
+        if (k > 0 && k < H / 2) A[padx(((H - k) << lc) + c)] = cadd(cconj(E), mul_i(cconj(O), +1));
     }
-    float2* res = block_fft(A, B, H, C, ld, +1, tw);
-    for (int it = threadIdx.x; it < H * C; it += blockDim.x) {
+    block_fft_ip<16>(A, H, C, +1, tw);
+    float2* dst = reinterpret_cast<float2*>(p0 + ((size_t)qz * G.ny + y0) * G.nx);
+#pragma unroll 4
+    for (int it = threadIdx.x; it < H * C; it += NT) {
         const int c = it >> lh;
         const int pp = it & (H - 1);
-        const float2 z = res[pp * ld + c];
-        reinterpret_cast<float2*>(p0 + ((size_t)qz * G.ny + y0 + c) * G.nx)[pp] = z;
+        dst[it] = A[padx(pp * C + c)];
     }
 }
 
@@ -695,8 +694,10 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     NEDNER_ATTR_NER(4, 10) NEDNER_ATTR_NER(6, 10) NEDNER_ATTR_NER(8, 10) NEDNER_ATTR_NER(10, 10)
     NEDNER_ATTR_NER(12, 10) NEDNER_ATTR_NER(14, 12) NEDNER_ATTR_NER(16, 12)
 #undef NEDNER_ATTR_NER
-    if ((e = cudaFuncSetAttribute(k_img_yifft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem4))) return e;
-    if ((e = cudaFuncSetAttribute(k_img_xc2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem5))) return e;
+    if ((e = cudaFuncSetAttribute(k_img_yifft<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem4)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_img_xc2r<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem5)))
+        return e;
     return cudaSuccess;
 }
 
@@ -767,7 +768,7 @@ cudaError_t launch_ner_lines(const nedner_plan_s& p, const float2* Ghat, float2*
 cudaError_t launch_img_yifft(const nedner_plan_s& p, const float2* V, float2* Y, cudaStream_t s) {
     const Geo& G = p.geo;
     dim3 grid(G.nxh, G.nz / p.ch.c4);
-    k_img_yifft<<<grid, 256, p.ch.smem4, s>>>(G, p.ch.c4, V, p.t.tw, Y);
+    k_img_yifft<128><<<grid, 128, p.ch.smem4, s>>>(G, p.ch.c4, V, p.t.tw, Y);
     return cudaGetLastError();
 }
 
@@ -775,7 +776,7 @@ cudaError_t launch_img_xc2r(const nedner_plan_s& p, const float2* Y, float* p0, 
     const Geo& G = p.geo;
     if (nzc < 0) nzc = G.nz - z0;
     dim3 grid(nzc, G.ny / p.ch.c5);
-    k_img_xc2r<<<grid, 256, p.ch.smem5, s>>>(G, p.ch.c5, z0, Y, p.t.tw, p0);
+    k_img_xc2r<128><<<grid, 128, p.ch.smem5, s>>>(G, p.ch.c5, z0, Y, p.t.tw, p0);
     return cudaGetLastError();
 }
 

@@ -445,13 +445,13 @@ void choose_chunks(nedner_plan_s& p) {
            (long)G.nz * c.lpc * 2 <= 16L * c.threads3)
         c.lpc *= 2;
     c.smem3 = (size_t)(padded(G.Lt * c.lpc) + (c.lpc + 1) * (G.nz + 1) + padded(G.nz * c.lpc)) * 8;
-    c.c4 = 1;
-    while (c.c4 * 2 <= 16 && c.c4 * 2 <= G.nz && 2L * G.ny * (c.c4 * 2 + 1) * 8 <= 96 * 1024) c.c4 *= 2;
-    c.smem4 = (size_t)2 * G.ny * (c.c4 + 1) * 8;
+    // inverse y- and x-FFTs: C <= 16 columns (conflict-free padded loads and
+    // stores), N * C <= 2048 (16 values per thread of 128)
+    c.c4 = (int)std::min<long>(std::min<long>(16, G.nz), 2048 / G.ny);
+    c.smem4 = (size_t)padded((long)G.ny * c.c4) * 8;
     const long H = G.nx / 2;
-    c.c5 = 1;
-    while (c.c5 * 2 <= 16 && c.c5 * 2 <= G.ny && (3 * H + 1) * (c.c5 * 2 + 1) * 8 <= 96 * 1024) c.c5 *= 2;
-    c.smem5 = (size_t)(3 * H + 1) * (c.c5 + 1) * 8;
+    c.c5 = (int)std::min<long>(std::min<long>(16, G.ny), 2048 / H);
+    c.smem5 = (size_t)padded(H * c.c5) * 8;
 }
 
 }  // namespace
