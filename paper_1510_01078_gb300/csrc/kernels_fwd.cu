@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
 // ---------------------------------------------------------------------------
 // Stage (a), part 2: y-FFT of length Ly for one jx and C time samples; keeps
 // jy = -ny/2..ny/2 (both Nyquist rows) divided by phihat(jy/Ly).  The FFT
-// runs in place in a padded buffer, Ly * C <= 256 PER (PER values per thread).
+// runs in place in a padded buffer, Ly * C <= 256 PER (PER values per thread);
+// a last radix-2 pass (log2 Ly = 1 mod 4) is applied to the kept rows only.
 // ---------------------------------------------------------------------------
 template <int PER>
 __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int C, int yb, const float2* __restrict__ R,
@@ -380,13 +381,29 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int 
         const int c = it & (C - 1);
         A[padx(it)] = R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c];
     }
-    block_fft_ip<PER>(A, G.Ly, C, -1, tw);
+    const bool fold = (ilog2(G.Ly) & 3) == 1;
+    block_fft_ip<PER>(A, G.Ly, C, -1, tw, fold);
     const int items = G.nyp * C;
-    for (int it = threadIdx.x; it < items; it += 256) {
-        const int b = it >> lc;                // jy = b - ny/2
-        const int c = it & (C - 1);
-        const int q = (b - G.ny / 2 + G.Ly) & (G.Ly - 1);
-        Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c] = cscale(A[padx(q * C + c)], __ldg(&deconv_y[b]));
+    if (!fold) {
+        for (int it = threadIdx.x; it < items; it += 256) {
+            const int b = it >> lc;                // jy = b - ny/2
+            const int c = it & (C - 1);
+            const int q = (b - G.ny / 2 + G.Ly) & (G.Ly - 1);
+            Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c] = cscale(A[padx(q * C + c)], __ldg(&deconv_y[b]));
+        }
+    } else {
+        // the last radix-2 pass, applied to the nyp kept rows only
+        const int H = G.Ly >> 1;
+        for (int it = threadIdx.x; it < items; it += 256) {
+            const int b = it >> lc;
+            const int c = it & (C - 1);
+            const int q = (b - G.ny / 2 + G.Ly) & (G.Ly - 1);
+            const int k = q & (H - 1);
+            const float2 s0 = A[padx((k << lc) + c)];
+            const float2 t = cmul(twiddle(tw, k, G.Ly, -1), A[padx(((k + H) << lc) + c)]);
+            Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c] = cscale(q < H ? cadd(s0, t) : csub(s0, t),
+                                                                    __ldg(&deconv_y[b]));
+        }
     }
 }
 
@@ -586,12 +603,27 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, cons
         if (!nyq_x) u = cadd(u, cscale(T[c * nz1 + l0], ca));
         UA[padx(((l & (G.nz - 1)) << llpc) + c)] = u;
     }
-    block_fft_ip<PER>(UA, G.nz, LPC, +1, tw);
-    for (int i = threadIdx.x; i < (G.nz << llpc); i += NT) {
-        const int c = i >> lnz, q = i & (G.nz - 1);
-        const int ky = k0 + c;
-        const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
-        V[((size_t)kx * G.ny + (ky & (G.ny - 1))) * G.nz + q] = cscale(UA[padx((q << llpc) + c)], sg);
+    const bool zfold = (lnz & 3) == 1;
+    block_fft_ip<PER>(UA, G.nz, LPC, +1, tw, zfold);
+    if (!zfold) {
+        for (int i = threadIdx.x; i < (G.nz << llpc); i += NT) {
+            const int c = i >> lnz, q = i & (G.nz - 1);
+            const int ky = k0 + c;
+            const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
+            V[((size_t)kx * G.ny + (ky & (G.ny - 1))) * G.nz + q] = cscale(UA[padx((q << llpc) + c)], sg);
+        }
+    } else {
+        // the last radix-2 pass of the z-IFFT, applied per output value
+        const int hz = G.nz >> 1;
+        for (int i = threadIdx.x; i < (G.nz << llpc); i += NT) {
+            const int c = i >> lnz, q = i & (G.nz - 1);
+            const int ky = k0 + c;
+            const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
+            const int k = q & (hz - 1);
+            const float2 s0 = UA[padx((k << llpc) + c)];
+            const float2 t = cmul(twiddle(tw, k, G.nz, +1), UA[padx(((k + hz) << llpc) + c)]);
+            V[((size_t)kx * G.ny + (ky & (G.ny - 1))) * G.nz + q] = cscale(q < hz ? cadd(s0, t) : csub(s0, t), sg);
+        }
     }
 }
 
