@@ -64,6 +64,17 @@ __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2&
     v3 = csub(a1, a3);
 }
 
+// dft4 with v1 = v2 = 0 on entry (the same sums without the zero terms)
+template <int DIR>
+__device__ __forceinline__ void dft4_z12(float2& v0, float2& v1, float2& v2, float2& v3) {
+    const float2 x0 = v0;
+    const float2 a3 = mul_i(make_float2(-v3.x, -v3.y), DIR);
+    v0 = cadd(x0, v3);
+    v2 = csub(x0, v3);
+    v1 = cadd(x0, a3);
+    v3 = csub(x0, a3);
+}
+
 // exp(DIR 2 pi i q / 16), q = 0..15, from the exact values of cos/sin at multiples of pi/8
 template <int DIR>
 __device__ __forceinline__ float2 w16(int q) {
@@ -91,7 +102,8 @@ __device__ __forceinline__ float2 w16(int q) {
 }
 
 // DFT of R points in registers; X[k] ends up in v[out_index<R>(k)].
-template <int R, int DIR>
+// ZP (R = 16): inputs 4..11 are zero
+template <int R, int DIR, bool ZP = false>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
     if constexpr (R == 2) {
         dft2<DIR>(v[0], v[1]);
@@ -108,7 +120,10 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
     } else {
         // R = 16: n = 4 n1 + n2, k = k1 + 4 k2: 4 DFT4 over n1, twiddle W16^(n2 k1), 4 DFT4 over n2
 #pragma unroll
-        for (int n2 = 0; n2 < 4; ++n2) dft4<DIR>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+        for (int n2 = 0; n2 < 4; ++n2) {
+            if constexpr (ZP) dft4_z12<DIR>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+            else dft4<DIR>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+        }
 #pragma unroll
         for (int k1 = 1; k1 < 4; ++k1)
 #pragma unroll
@@ -136,7 +151,10 @@ __device__ __forceinline__ constexpr int out_index(int k) {
 __device__ __forceinline__ int padx(int a) { return a + (a >> 4); }
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
 
-template <int R, int DIR, int PER>
+// ZP (first radix-16 pass only): points N/4 <= p < 3N/4 are zero and are
+// not read, i.e. the input is x zero-padded to twice its length and centred
+// (its first half at p < N/4, its second half at p >= 3N/4).
+template <int R, int DIR, int PER, bool ZP = false>
 __device__ __forceinline__ void fft_pass_ip(float2* buf, int N, int Ns, int nb, const float2* __restrict__ tw) {
     constexpr int IT = PER / R;
     const int stride = N / R;
@@ -155,13 +173,15 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, int N, int Ns, int nb, 
         if (it < items) {
             const int j = it >> lnb, b = it & (nb - 1);
             const int a0 = (j << lnb) + b;
+            constexpr bool zp = ZP && R == 16;
             if (lld >= 16) {
                 const float2* p = buf + padx(a0);
 #pragma unroll
-                for (int r = 0; r < R; ++r, p += dld) v[i][r] = *p;
+                for (int r = 0; r < R; ++r, p += dld) v[i][r] = (zp && r >= 4 && r < 12) ? make_float2(0.f, 0.f) : *p;
             } else {
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[i][r] = buf[padx(a0 + r * lld)];
+                for (int r = 0; r < R; ++r)
+                    v[i][r] = (zp && r >= 4 && r < 12) ? make_float2(0.f, 0.f) : buf[padx(a0 + r * lld)];
             }
         }
     }
@@ -203,7 +223,7 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, int N, int Ns, int nb, 
                     }
                 }
             }
-            dft_reg<R, DIR>(v[i]);
+            dft_reg<R, DIR, ZP && R == 16>(v[i]);
             const int a0 = (((j - k) * R + k) << lnb) + b;
             if (lst >= 16) {
                 float2* p = buf + padx(a0);
@@ -218,12 +238,17 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, int N, int Ns, int nb, 
     __syncthreads();
 }
 
-template <int PER, int DIR>
+template <int PER, int DIR, bool ZP>
 __device__ __forceinline__ void block_fft_ip_dir(float2* buf, int N, int nb, const float2* __restrict__ tw,
                                                  bool skip_r2) {
     __syncthreads();
     int Ns = 1;
     int rem = ilog2(N);
+    if constexpr (ZP) {
+        fft_pass_ip<16, DIR, PER, true>(buf, N, Ns, nb, tw);
+        rem -= 4;
+        Ns <<= 4;
+    }
     for (; rem >= 4; rem -= 4, Ns <<= 4) fft_pass_ip<16, DIR, PER>(buf, N, Ns, nb, tw);
     if (rem == 3) fft_pass_ip<8, DIR, PER>(buf, N, Ns, nb, tw);
     else if (rem == 2) fft_pass_ip<4, DIR, PER>(buf, N, Ns, nb, tw);
@@ -233,12 +258,14 @@ __device__ __forceinline__ void block_fft_ip_dir(float2* buf, int N, int nb, con
 // In-place transform of nb columns of length N in a padded buffer.  With
 // skip_r2, a final radix-2 pass (log2 N = 1 mod 4) is left to the caller:
 // the buffer then holds s with X[k] = s[k] + w^k s[k + N/2] and
-// X[k + N/2] = s[k] - w^k s[k + N/2], w = exp(DIR 2 pi i / N).
-template <int PER>
+// X[k + N/2] = s[k] - w^k s[k + N/2], w = exp(DIR 2 pi i / N).  With ZP
+// (N >= 16) the input is zero at N/4 <= p < 3N/4 and those points are never
+// read, so the caller need not write them.
+template <int PER, bool ZP = false>
 __device__ __forceinline__ void block_fft_ip(float2* buf, int N, int nb, int dir, const float2* __restrict__ tw,
                                              bool skip_r2 = false) {
-    if (dir < 0) block_fft_ip_dir<PER, -1>(buf, N, nb, tw, skip_r2);
-    else block_fft_ip_dir<PER, +1>(buf, N, nb, tw, skip_r2);
+    if (dir < 0) block_fft_ip_dir<PER, -1, ZP>(buf, N, nb, tw, skip_r2);
+    else block_fft_ip_dir<PER, +1, ZP>(buf, N, nb, tw, skip_r2);
 }
 
 }  // namespace nedner

@@ -557,11 +557,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, cons
         const size_t lx = (size_t)kx * G.nyp + G.ny;
         const float2* src = Ghat + lx * G.Nt;
 #pragma unroll 4
-        for (int p = threadIdx.x; p < G.Lt; p += NT) {
-            const int n = (p + G.Nt / 2) & (G.Lt - 1);
-            LA[padx(p)] = (n < G.Nt) ? cscale(src[n], __ldg(&deconv_t[n])) : make_float2(0.f, 0.f);
-        }
-        block_fft_ip<PER>(LA, G.Lt, 1, -1, tw);
+        for (int n = threadIdx.x; n < G.Nt; n += NT)
+            LA[padx((n - G.Nt / 2) & (G.Lt - 1))] = cscale(src[n], __ldg(&deconv_t[n]));
+        block_fft_ip<PER, true>(LA, G.Lt, 1, -1, tw);
         const float2 axy = __ldg(&axy_tab[lx]);
         for (int e = threadIdx.x; e < nz1; e += NT)
             T[LPC * nz1 + e] = ner_value<W, D>(G, P, axy, false, e - half_nz, LA, 0, 0);
@@ -571,13 +569,14 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, cons
     {
         const float2* src = Ghat + line0 * G.Nt;
 #pragma unroll 4
-        for (int i = threadIdx.x; i < (G.Lt << llpc); i += NT) {
-            const int p = i >> llpc, c = i & (LPC - 1);
-            const int n = (p + G.Nt / 2) & (G.Lt - 1);
-            LA[padx(i)] = (n < G.Nt) ? cscale(src[(size_t)c * G.Nt + n], __ldg(&deconv_t[n])) : make_float2(0.f, 0.f);
+        for (int i = threadIdx.x; i < (G.Nt << llpc); i += NT) {
+            const int n = i >> llpc, c = i & (LPC - 1);
+            const int p = (n - G.Nt / 2) & (G.Lt - 1);
+            LA[padx((p << llpc) + c)] = cscale(src[(size_t)c * G.Nt + n], __ldg(&deconv_t[n]));
         }
     }
-    block_fft_ip<PER>(LA, G.Lt, LPC, -1, tw);
+    // Lt = 2 Nt: the centred samples fill p < Nt/2 and p >= 3Nt/2 only
+    block_fft_ip<PER, true>(LA, G.Lt, LPC, -1, tw);
 
     // NER values of the LPC lines at l = -nz/2..nz/2
     for (int i = threadIdx.x; i < (G.nz << llpc) + LPC; i += NT) {
