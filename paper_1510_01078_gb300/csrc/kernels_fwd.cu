@@ -365,6 +365,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
 // jy = -ny/2..ny/2 (both Nyquist rows) divided by phihat(jy/Ly).  The FFT
 // runs in place in a padded buffer, Ly * C <= 256 PER (PER values per thread);
 // a last radix-2 pass (log2 Ly = 1 mod 4) is applied to the kept rows only.
+// blockIdx.x runs over the time chunks, so consecutive CTAs read neighbouring
+// pieces of the same rows.
 // ---------------------------------------------------------------------------
 template <int PER>
 __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int C, int yb, const float2* __restrict__ R,
@@ -372,8 +374,8 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int 
                                                      const float2* __restrict__ tw, float2* __restrict__ Ghat) {
     extern __shared__ float4 smem4[];
     float2* A = reinterpret_cast<float2*>(smem4);   // [Ly][C], padded
-    const int jx = blockIdx.x;
-    const int n0 = (yb + blockIdx.y) * C;
+    const int jx = blockIdx.y;
+    const int n0 = (yb + blockIdx.x) * C;
     const int lc = ilog2(C);
 #pragma unroll 8
     for (int it = threadIdx.x; it < G.Ly * C; it += 256) {
@@ -765,7 +767,7 @@ cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Gha
     const Geo& G = p.geo;
     if (nt < 0) nt = G.Nt - t0;
     const int yb = t0 / p.ch.c2f;
-    dim3 grid(G.nxh, nt / p.ch.c2f);
+    dim3 grid(nt / p.ch.c2f, G.nxh);
     if ((long)G.Ly * p.ch.c2f <= 16L * 256)
         k_ned_yfft<16><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, yb, R, p.t.deconv_y, p.t.tw, Ghat);
     else
