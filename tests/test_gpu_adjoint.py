@@ -168,3 +168,30 @@ def test_adjoint_in_passes_under_workspace_limit(nd):
     tight.close()
     assert rel_l2(b, a) <= 1e-6, rel_l2(b, a)
     assert rel_l2(b, oracle.adjoint(problem(case), p)) <= TOL
+
+
+LIMITS = [
+    dict(nx=2048, ny=8, nz=8, M=20, Nt=16, seed=41, layout="scatter"),
+    dict(nx=8, ny=2048, nz=8, M=20, Nt=16, seed=42, layout="scatter"),
+    dict(nx=8, ny=8, nz=2048, M=12, Nt=4096, seed=43, layout="scatter"),
+]
+
+
+@pytest.mark.parametrize("spec", LIMITS, ids=["{nx}x{ny}x{nz}_Nt{Nt}".format(**c) for c in LIMITS])
+def test_adjoint_and_grad_at_size_limits(nd, spec):
+    """nx, ny or nz at 2048 and Nt at 4096: a transposed gather with two time
+    samples per CTA over a row of 4096 columns, one-column y transforms, and
+    the transposed line FFT of 8192 points."""
+    case = inputs.small_case(**spec)
+    rng = np.random.default_rng(spec["seed"] + 500)
+    p = rng.standard_normal((case["nz"], case["ny"], case["nx"]))
+    pr = problem(case)
+    plan = nd.plan_from_config(case)
+    pt = torch.as_tensor(p, dtype=torch.float32, device="cuda")
+    got = plan.adjoint(pt).cpu().numpy()
+    want = oracle.adjoint(pr, p)
+    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    gg = plan.grad_positions(torch.as_tensor(case["g"], dtype=torch.float32, device="cuda"), pt).cpu().numpy()
+    want_g = oracle.grad_positions(pr, case["g"], p)
+    plan.close()
+    assert rel_l2(gg, want_g) <= TOL_GRAD, rel_l2(gg, want_g)

@@ -110,6 +110,26 @@ def test_forward_c3_full_size_sparse_time(nd):
     assert rel_l2(got, want) <= TOL, rel_l2(got, want)
 
 
+# nx, ny or nz at the plan's maximum of 2048, and Nt at its maximum of 4096: a
+# spread row of 2nx = 4096 columns (4 time samples per spread CTA, 2 columns in the
+# x complex-to-real transform), a y-FFT and y-IFFT of one column, and a line FFT of
+# 2Nt = 8192 points (512 threads) with a z-IFFT of 2048.
+LIMITS = [
+    dict(nx=2048, ny=8, nz=8, M=20, Nt=16, seed=41, layout="scatter"),
+    dict(nx=8, ny=2048, nz=8, M=20, Nt=16, seed=42, layout="scatter"),
+    dict(nx=8, ny=8, nz=2048, M=12, Nt=4096, seed=43, layout="scatter"),
+]
+LIMIT_IDS = ["{nx}x{ny}x{nz}_M{M}_Nt{Nt}".format(**c) for c in LIMITS]
+
+
+@pytest.mark.parametrize("spec", LIMITS, ids=LIMIT_IDS)
+def test_forward_at_size_limits(nd, spec):
+    case = inputs.small_case(**spec)
+    want = oracle.forward(problem(case), case["g"])
+    got = gpu_forward(nd, case)
+    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+
+
 @pytest.mark.parametrize("opt", ["unweighted", "band_mask", "gauss16", "kb8"])
 def test_forward_options(nd, opt):
     case = inputs.small_case(16, 16, 32, 77, 64, seed=11, layout="disc")
