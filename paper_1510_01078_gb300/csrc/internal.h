@@ -37,6 +37,7 @@ struct Chunks {
     int ca;        // time samples per CTA in the transposed interpolation stage
     int per_adj;   // values per thread in its in-place row FFT (16 or 32)
     int tpl_adj;   // time samples per lane in the transposed gather (1 or 2; 2 means ca = 64)
+    int threads_adj;   // threads of the two-sample gather CTA (256, or 512 for 2nx = 512)
     int tp_adj;    // time samples per pass of the transposed gather (its entry buffer holds M w tp_adj floats)
     int lpc;       // line groups per CTA in the NER stage
     int threads3;  // threads per CTA in the NER stage

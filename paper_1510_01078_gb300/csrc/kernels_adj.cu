@@ -548,8 +548,8 @@ __device__ __forceinline__ void win2_entry(const float2 (&win)[2 * WT], int d, c
 
 // k_ned_gather_rows with two time samples per lane: C = 64, 256 threads (one
 // lane group per warp), the row FFT with 32 values per thread (2 nx <= 256).
-template <int WT, bool GRAD>
-__global__ void __launch_bounds__(256, 2) k_ned_gather_rows2(Geo G, int nb, int Tp, const float2* __restrict__ R,
+template <int WT, bool GRAD, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_gather_rows2(Geo G, int nb, int Tp, const float2* __restrict__ R,
                                                              const float* __restrict__ g,
                                                              const int* __restrict__ xrow_ptr,
                                                              const int* __restrict__ xrow_first,
@@ -686,8 +686,10 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
     NEDNER_ATTR_GATHER(8, 16) NEDNER_ATTR_GATHER(12, 16) NEDNER_ATTR_GATHER(16, 16) NEDNER_ATTR_GATHER(20, 16)
 #undef NEDNER_ATTR_GATHER
 #define NEDNER_ATTR_GATHER2(WT)                                                                             \
-    if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, false>, (cudaFuncAttribute)a, (int)c.smem_adj))) return e; \
-    if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, true>, (cudaFuncAttribute)a, (int)c.smem_grad))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, false, 256>, (cudaFuncAttribute)a, (int)c.smem_adj))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, true, 256>, (cudaFuncAttribute)a, (int)c.smem_grad))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, false, 512>, (cudaFuncAttribute)a, (int)c.smem_adj))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, true, 512>, (cudaFuncAttribute)a, (int)c.smem_grad))) return e;
     NEDNER_ATTR_GATHER2(8) NEDNER_ATTR_GATHER2(12) NEDNER_ATTR_GATHER2(16) NEDNER_ATTR_GATHER2(20)
 #undef NEDNER_ATTR_GATHER2
     return cudaSuccess;
@@ -751,11 +753,18 @@ cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E,
     for (int nb = 0; nb < G.Nt; nb += Tp) {
         const dim3 grid(G.Ly, Tp / C);
 #define NEDNER_ADJ(WT)                                                                                            \
-    if (p.ch.tpl_adj == 2)                                                                                        \
-        k_ned_gather_rows2<WT, false><<<grid, 256, p.ch.smem_adj, s>>>(G, nb, Tp, R, nullptr, p.t.xrow_ptr,       \
-                                                                       p.t.xrow_first, p.t.xent_m, p.t.xent_bx,    \
-                                                                       p.t.xent_rc, p.t.xent_wx, p.t.xent_wx,      \
-                                                                       p.t.deconv_x, p.t.tw, E, nullptr);          \
+    if (p.ch.tpl_adj == 2 && p.ch.threads_adj == 512)                                                             \
+        k_ned_gather_rows2<WT, false, 512><<<grid, 512, p.ch.smem_adj, s>>>(G, nb, Tp, R, nullptr, p.t.xrow_ptr,  \
+                                                                            p.t.xrow_first, p.t.xent_m,           \
+                                                                            p.t.xent_bx, p.t.xent_rc, p.t.xent_wx, \
+                                                                            p.t.xent_wx, p.t.deconv_x, p.t.tw, E, \
+                                                                            nullptr);                             \
+    else if (p.ch.tpl_adj == 2)                                                                                   \
+        k_ned_gather_rows2<WT, false, 256><<<grid, 256, p.ch.smem_adj, s>>>(G, nb, Tp, R, nullptr, p.t.xrow_ptr,  \
+                                                                            p.t.xrow_first, p.t.xent_m,           \
+                                                                            p.t.xent_bx, p.t.xent_rc, p.t.xent_wx, \
+                                                                            p.t.xent_wx, p.t.deconv_x, p.t.tw, E, \
+                                                                            nullptr);                             \
     else                                                                                                          \
     k_ned_gather_rows<WT, 16, false><<<grid, 256, p.ch.smem_adj, s>>>(G, C, nb, Tp, R, nullptr, p.t.xrow_ptr,       \
                                                                       p.t.xrow_first, p.t.xent_m, p.t.xent_bx,      \
@@ -774,11 +783,18 @@ cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const fl
     const int C = p.ch.ca;
     const dim3 grid(G.Ly, G.Nt / C);
 #define NEDNER_GRAD(WT)                                                                                          \
-    if (p.ch.tpl_adj == 2)                                                                                        \
-        k_ned_gather_rows2<WT, true><<<grid, 256, p.ch.smem_grad, s>>>(G, 0, G.Nt, R, g, p.t.xrow_ptr,            \
-                                                                       p.t.xrow_first, p.t.xent_m, p.t.xent_bx,    \
-                                                                       p.t.xent_rc, p.t.xent_gx, p.t.xent_gy,      \
-                                                                       p.t.deconv_x, p.t.tw, nullptr, Qe);         \
+    if (p.ch.tpl_adj == 2 && p.ch.threads_adj == 512)                                                             \
+        k_ned_gather_rows2<WT, true, 512><<<grid, 512, p.ch.smem_grad, s>>>(G, 0, G.Nt, R, g, p.t.xrow_ptr,       \
+                                                                            p.t.xrow_first, p.t.xent_m,           \
+                                                                            p.t.xent_bx, p.t.xent_rc, p.t.xent_gx, \
+                                                                            p.t.xent_gy, p.t.deconv_x, p.t.tw,    \
+                                                                            nullptr, Qe);                         \
+    else if (p.ch.tpl_adj == 2)                                                                                   \
+        k_ned_gather_rows2<WT, true, 256><<<grid, 256, p.ch.smem_grad, s>>>(G, 0, G.Nt, R, g, p.t.xrow_ptr,       \
+                                                                            p.t.xrow_first, p.t.xent_m,           \
+                                                                            p.t.xent_bx, p.t.xent_rc, p.t.xent_gx, \
+                                                                            p.t.xent_gy, p.t.deconv_x, p.t.tw,    \
+                                                                            nullptr, Qe);                         \
     else                                                                                                          \
     k_ned_gather_rows<WT, 16, true><<<grid, 256, p.ch.smem_grad, s>>>(G, C, 0, G.Nt, R, g, p.t.xrow_ptr,           \
                                                                       p.t.xrow_first, p.t.xent_m, p.t.xent_bx,     \

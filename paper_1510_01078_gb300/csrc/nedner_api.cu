@@ -390,8 +390,10 @@ void choose_chunks(nedner_plan_s& p) {
     c.c1 = std::min<long>(32, std::max<long>(2, pow2_floor((128L * 1024) / (8L * G.Lx))));
     c.c1 = std::min(c.c1, G.Nt);
     // transposed gather: two time samples per lane (64 per CTA) where the row
-    // FFT has 32 values per thread, else time samples per CTA such that it has 16
-    c.tpl_adj = (G.Lx <= 256 && G.Nt >= 64) ? 2 : 1;
+    // FFT has 32 values per thread (256 threads up to 2nx = 256, one CTA of 512
+    // threads per SM at 2nx = 512), else time samples per CTA such that it has 16
+    c.tpl_adj = (G.Lx <= 512 && G.Nt >= 64) ? 2 : 1;
+    c.threads_adj = G.Lx > 256 ? 512 : 256;
     c.ca = c.tpl_adj == 2 ? 64 : (int)std::min<long>(c.c1, std::max<long>(2, 8192 / G.Lx));
     c.threads1 = 256;
     c.tpl1 = 1;

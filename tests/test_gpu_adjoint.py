@@ -133,8 +133,8 @@ def test_autograd_function(nd):
 
 
 def test_adjoint_and_grad_wide_rows(nd):
-    """2nx = 512 grid columns: the transposed gather with one time sample per
-    lane (16 per CTA), and its gradient."""
+    """2nx = 512 grid columns: the transposed gather with two time samples per
+    lane (64 per CTA of 512 threads), and its gradient."""
     case = inputs.small_case(256, 16, 8, 200, 64, seed=31, layout="scatter")
     rng = np.random.default_rng(131)
     p = rng.standard_normal((case["nz"], case["ny"], case["nx"]))
