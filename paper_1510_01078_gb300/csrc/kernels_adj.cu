@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(256, 3) k_ned_yfft_adj(Geo G, int C, const flo
                                                          const float2* __restrict__ tw, float2* __restrict__ R) {
     extern __shared__ float4 smem4[];
     float2* A = reinterpret_cast<float2*>(smem4);   // [Ly][C], padded
-    const int jx = blockIdx.x;
-    const int n0 = blockIdx.y * C;
+    const int jx = blockIdx.y;                      // time chunks on blockIdx.x: neighbouring CTAs
+    const int n0 = blockIdx.x * C;                  // read neighbouring pieces of the same rows
     const int lc = ilog2(C);
     // jy = b - ny/2 sits at q = (jy mod Ly); the other Ly - (ny + 1) points are zero
 #pragma unroll 8
@@ -732,7 +732,7 @@ cudaError_t launch_ner_lines_adj(const nedner_plan_s& p, const float2* V, float2
 
 cudaError_t launch_ned_yfft_adj(const nedner_plan_s& p, const float2* Ghat, float2* R, cudaStream_t s) {
     const Geo& G = p.geo;
-    k_ned_yfft_adj<<<dim3(G.nxh, G.Nt / p.ch.c2f), 256, p.ch.smem2f, s>>>(G, p.ch.c2f, Ghat, p.t.deconv_y, p.t.tw, R);
+    k_ned_yfft_adj<<<dim3(G.Nt / p.ch.c2f, G.nxh), 256, p.ch.smem2f, s>>>(G, p.ch.c2f, Ghat, p.t.deconv_y, p.t.tw, R);
     return cudaGetLastError();
 }
 
