@@ -142,6 +142,23 @@ def oracle_forward_seconds(cfg, steps: int = 1, want_output: bool = False):
 
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks: the slowest replica sets the step time."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(voxels: int, world: int, ms_step: float) -> float:
+    """Voxels/s of the whole job: every rank reconstructs its own workload of
+    `voxels` voxels in at most `ms_step` milliseconds."""
+    return voxels * world / (ms_step / 1e3)
+
+
 def run_reference(args, cfg, voxels, rank, world):
     if rank != 0:
         return
@@ -234,12 +251,8 @@ def main():
         dist.barrier()
     clk = clocks.stop()
 
-    ms_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = voxels * world / (ms_step / 1e3)
+    ms_step = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
+    value = whole_job_value(voxels, world, ms_step)
 
     # end to end through the public API with host buffers (pinned), copies timed
     g_host = torch.as_tensor(np.asarray(cfg["g"], dtype=np.float32)).pin_memory()
@@ -258,11 +271,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_step = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, dev)
 
     # roofline of the dominant kernel
     abytes = algorithmic_bytes(cfg)
@@ -315,7 +324,7 @@ def main():
                            "parallelism": "independent reconstruction per GPU", "ned_mode": args.ned_mode},
                 "roofline": roofline, "spread_frac_of_peak": spread_frac, "accuracy": accuracy, "kernels": kernels,
                 "cpu_baseline": cpu, "clocks": clk,
-                "e2e": {"value": voxels * world / (e2e_step / 1e3), "unit": "voxels/s",
+                "e2e": {"value": whole_job_value(voxels, world, e2e_step), "unit": "voxels/s",
                         "h2d_bytes_per_step": int(g_host.numel() * 4), "d2h_bytes_per_step": int(p_host.numel() * 4)},
                 "gpu_launches": launches_per_step * args.steps,
                 "wall_s_timed_region": round(wall, 3)}
