@@ -546,8 +546,9 @@ __device__ __forceinline__ void win2_entry(const float2 (&win)[2 * WT], int d, c
     else win2_dot<WT, (WT >= 20 ? 20 : 0), TWO>(win, ta, tb, va, vb);
 }
 
-// k_ned_gather_rows with two time samples per lane: C = 64, 256 threads (one
-// lane group per warp), the row FFT with 32 values per thread (2 nx <= 256).
+// k_ned_gather_rows with two time samples per lane: C = 64, one lane group
+// per warp, the row FFT with 32 values per thread: NT = 256 for 2 nx <= 256,
+// NT = 512 (one CTA per SM) for 2 nx = 512.
 template <int WT, bool GRAD, int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_gather_rows2(Geo G, int nb, int Tp, const float2* __restrict__ R,
                                                              const float* __restrict__ g,
