@@ -232,6 +232,20 @@ nedner_status nedner_device_status(nedner_plan_t plan, int* flags);
 /* Bytes of device workspace held by the plan. */
 size_t nedner_workspace_bytes(nedner_plan_t plan);
 
+/*
+ * The work split a plan of this geometry uses (sigma = 2, window width w),
+ * computed on the host without a device, so that the kernels' size
+ * conditions can be checked for every geometry.  Writes up to nout values to
+ * out, in this order: c1, c2f, c4, c5, groups1, threads1, per1, tpl1, ca,
+ * per_adj, tpl_adj, threads_adj, lpc, threads3 (time samples, depth planes,
+ * rows or lines per CTA, threads per CTA, values per thread and time samples
+ * per lane of the stages), then the dynamic shared memory in bytes of the
+ * spread, y-FFT, NER, y-IFFT, x complex-to-real and transposed gather
+ * (adjoint, gradient) kernels.  Returns the number of values (21), or -1 for
+ * a geometry nedner_plan rejects or a null out.  No paper counterpart.
+ */
+int nedner_work_split(int nx, int ny, int nz, int Nt, int w, int64_t* out, int nout);
+
 /* Free the plan (synchronises its device work first).  NULL is allowed. */
 nedner_status nedner_destroy(nedner_plan_t plan);
 

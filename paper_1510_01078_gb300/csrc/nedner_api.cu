@@ -708,6 +708,30 @@ nedner_status nedner_device_status(nedner_plan_t p, int* flags) {
 
 size_t nedner_workspace_bytes(nedner_plan_t p) { return p ? p->ws_bytes : 0; }
 
+int nedner_work_split(int nx, int ny, int nz, int Nt, int w, int64_t* out, int nout) {
+    if (!out || nout < 0) return -1;
+    if (!is_pow2(Nt) || Nt < 8 || Nt > 4096) return -1;
+    if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz)) return -1;
+    if (nx < 8 || ny < 8 || nz < 8 || nx > 2048 || ny > 2048 || nz > 2048) return -1;
+    if (w < 4 || w > 16 || (w & 1)) return -1;
+    nedner_plan_s p;
+    Geo& G = p.geo;
+    G.Nt = Nt;
+    G.nx = nx; G.ny = ny; G.nz = nz;
+    G.Lx = 2 * nx; G.Ly = 2 * ny; G.Lt = 2 * Nt;
+    G.nxh = nx / 2 + 1; G.nyp = ny + 1;
+    G.w = w;
+    choose_chunks(p);
+    const Chunks& c = p.ch;
+    const int64_t v[] = {c.c1, c.c2f, c.c4, c.c5, c.groups1, c.threads1, c.per1, c.tpl1, c.ca, c.per_adj,
+                         c.tpl_adj, c.threads_adj, c.lpc, c.threads3, (int64_t)c.smem1, (int64_t)c.smem2f,
+                         (int64_t)c.smem3, (int64_t)c.smem4, (int64_t)c.smem5, (int64_t)c.smem_adj,
+                         (int64_t)c.smem_grad};
+    const int n = (int)(sizeof(v) / sizeof(v[0]));
+    for (int i = 0; i < n && i < nout; ++i) out[i] = v[i];
+    return n;
+}
+
 nedner_status nedner_forward_host(nedner_plan_t p, const float* g_host, float* p0_host, void* stream) {
     if (!p || !p0_host || (p->M > 0 && !g_host)) return NEDNER_EINVAL;
     const Geo& G = p->geo;

@@ -61,6 +61,8 @@ SIGNATURES = {
     "nedner_forward_profiled": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
     "nedner_ned_stage_static": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "nedner_work_split": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "nedner_forward_host": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_device_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "nedner_destroy": (ctypes.c_int, [_P]),
@@ -345,6 +347,20 @@ def reconstruct(plan: Plan, g, sensor_xy=None):
     return _RECON.apply(g, sensor_xy, plan)
 
 
+WORK_SPLIT_FIELDS = ("c1", "c2f", "c4", "c5", "groups1", "threads1", "per1", "tpl1", "ca", "per_adj", "tpl_adj",
+                     "threads_adj", "lpc", "threads3", "smem1", "smem2f", "smem3", "smem4", "smem5", "smem_adj",
+                     "smem_grad")
+
+
+def work_split(nx: int, ny: int, nz: int, Nt: int, w: int = 12) -> dict:
+    """The per-stage work split a plan of this geometry uses (host only, no device)."""
+    out = (ctypes.c_int64 * len(WORK_SPLIT_FIELDS))()
+    n = _load().nedner_work_split(nx, ny, nz, Nt, w, out, len(out))
+    if n < 0:
+        raise NednerError(EINVAL, "nedner_work_split (%d x %d x %d, Nt %d, w %d)" % (nx, ny, nz, Nt, w))
+    return dict(zip(WORK_SPLIT_FIELDS, [int(v) for v in out[:n]]))
+
+
 def plan_from_config(cfg, **kw) -> Plan:
     """Plan for a workload dict as produced by ``inputs.make_config``/``small_case``."""
     return Plan(cfg["sensor_xy"], cfg["Nt"], cfg["dt"], cfg["c"],
@@ -352,5 +368,5 @@ def plan_from_config(cfg, **kw) -> Plan:
                 sensor_w=kw.pop("sensor_w", cfg.get("h")), **kw)
 
 
-__all__ = ["Plan", "plan_from_config", "ned_stage_static", "reconstruct", "model", "NednerError", "library", "LIB_PATH", "SIGNATURES",
+__all__ = ["Plan", "plan_from_config", "work_split", "WORK_SPLIT_FIELDS", "ned_stage_static", "reconstruct", "model", "NednerError", "library", "LIB_PATH", "SIGNATURES",
            "WINDOW_KB", "WINDOW_GAUSS"]

@@ -1,0 +1,89 @@
+"""The kernels' size conditions, checked on the host for every geometry a
+plan accepts (nx, ny, nz = 8..2048, Nt = 8..4096, window widths 4..16), from
+the work split the library itself chooses (nedner_work_split, no device).
+
+Each in-place block FFT needs N * columns <= values per thread * threads;
+every chunk must divide its axis; the dynamic shared memory of every kernel
+must fit the 227 KB a CTA can have."""
+import itertools
+
+import pytest
+
+SMEM_MAX = 227 * 1024
+POW2 = [2 ** k for k in range(3, 12)]          # 8 .. 2048
+NTS = [2 ** k for k in range(3, 13)]           # 8 .. 4096
+WIDTHS = [4, 6, 8, 10, 12, 14, 16]
+
+
+@pytest.fixture(scope="module")
+def nd():
+    from paper_1510_01078_gb300 import build as b
+    b.build()
+    from paper_1510_01078_gb300 import nedner
+    return nedner
+
+
+def check(nx, ny, nz, Nt, s):
+    Lx, Ly, Lt = 2 * nx, 2 * ny, 2 * Nt
+    bad = []
+
+    def need(cond, what):
+        if not cond:
+            bad.append(what)
+
+    # spread + x-FFT
+    if s["tpl1"] == 2:
+        need(s["c1"] == 64 and Nt % 64 == 0, "spread2: 64 time samples per CTA")
+        need(s["threads1"] in (256, 512) and s["groups1"] * 32 == s["threads1"], "spread2: one lane group per warp")
+        need(Lx * 32 <= 32 * s["threads1"], "spread2: row FFT fits 32 values per thread")
+    else:
+        need(s["threads1"] == 256 and 2 <= s["c1"] <= 32 and Nt % s["c1"] == 0, "spread: time chunk")
+        need(s["groups1"] * s["c1"] == 256, "spread: lane groups fill the CTA")
+        need(s["per1"] in (16, 32) and Lx * s["c1"] // 2 <= s["per1"] * 256, "spread: row FFT fits")
+    need(s["smem1"] <= SMEM_MAX, "spread: shared memory")
+    # y-FFT (values per thread 16 or 32) and its transpose (16)
+    need(Nt % s["c2f"] == 0 and Ly * s["c2f"] <= 16 * 256, "y-FFT: column FFT fits")
+    need(s["smem2f"] <= SMEM_MAX, "y-FFT: shared memory")
+    # NER and its transpose: line FFT of Lt and z-FFT of nz, 16 values per thread
+    need(s["threads3"] in (256, 512) and ny % s["lpc"] == 0, "NER: line groups")
+    need(Lt * s["lpc"] <= 16 * s["threads3"] and nz * s["lpc"] <= 16 * s["threads3"], "NER: FFTs fit")
+    need(s["smem3"] <= SMEM_MAX, "NER: shared memory")
+    # inverse image FFTs and their transposes: 128 threads, 16 values each
+    need(nz % s["c4"] == 0 and ny * s["c4"] <= 16 * 128, "y-IFFT: fits")
+    need(ny % s["c5"] == 0 and (nx // 2) * s["c5"] <= 16 * 128, "x-c2r: fits")
+    need(max(s["smem4"], s["smem5"]) <= SMEM_MAX, "image FFTs: shared memory")
+    # transposed gather (adjoint and position gradient)
+    if s["tpl_adj"] == 2:
+        need(s["ca"] == 64 and Nt % 64 == 0, "gather2: 64 time samples per CTA")
+        need(s["threads_adj"] in (256, 512) and Lx * 32 <= 32 * s["threads_adj"], "gather2: row FFT fits")
+    else:
+        need(2 <= s["ca"] and Nt % s["ca"] == 0, "gather: time chunk")
+        need(Lx * s["ca"] // 2 <= s["per_adj"] * 256, "gather: row FFT fits")
+    need(s["smem_adj"] <= SMEM_MAX and s["smem_grad"] <= SMEM_MAX, "gather: shared memory")
+    return bad
+
+
+def test_every_accepted_geometry_meets_the_kernel_size_conditions(nd):
+    failures = []
+    for nx, ny, nz, Nt in itertools.product(POW2, POW2, POW2, NTS):
+        for w in WIDTHS:
+            s = nd.work_split(nx, ny, nz, Nt, w)
+            bad = check(nx, ny, nz, Nt, s)
+            if bad:
+                failures.append(((nx, ny, nz, Nt, w), bad))
+    assert not failures, failures[:10]
+
+
+def test_rejected_geometries(nd):
+    from paper_1510_01078_gb300.nedner import NednerError
+    for args in [(4096, 8, 8, 64, 12), (8, 8, 8, 8192, 12), (12, 8, 8, 64, 12), (8, 8, 8, 64, 3), (8, 8, 8, 64, 18)]:
+        with pytest.raises(NednerError):
+            nd.work_split(*args)
+
+
+def test_known_splits(nd):
+    """The splits the timed workloads run with."""
+    c2 = nd.work_split(128, 128, 256, 512, 12)
+    assert (c2["tpl1"], c2["c1"], c2["threads1"], c2["lpc"], c2["tpl_adj"]) == (2, 64, 256, 4, 2)
+    c3 = nd.work_split(256, 256, 512, 2048, 12)
+    assert (c3["tpl1"], c3["threads1"], c3["lpc"], c3["threads_adj"], c3["c4"], c3["c5"]) == (2, 512, 1, 512, 8, 16)
