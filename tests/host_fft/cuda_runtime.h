@@ -1,0 +1,29 @@
+// Host stand-in for the few CUDA names the in-shared-memory FFT header uses,
+// so that the header itself can be compiled with g++ and run on CPU threads
+// (one std::thread per CUDA thread, __syncthreads as a std::barrier).  Test
+// infrastructure only.
+#pragma once
+#include <cmath>
+
+struct float2 {
+    float x, y;
+};
+inline float2 make_float2(float x, float y) { return float2{x, y}; }
+
+struct HostDim3 {
+    unsigned x = 0, y = 0, z = 0;
+};
+extern thread_local HostDim3 threadIdx;
+extern HostDim3 blockDim;
+void __syncthreads();
+
+#define __device__
+#define __host__
+#define __forceinline__ inline
+#define __restrict__ __restrict
+
+template <class T>
+inline T __ldg(const T* p) { return *p; }
+// one packed FP32x2 add: two independent round-to-nearest adds
+inline float2 __fadd2_rn(float2 a, float2 b) { return float2{a.x + b.x, a.y + b.y}; }
+inline int __clz(int v) { return __builtin_clz((unsigned)v); }
