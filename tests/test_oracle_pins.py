@@ -97,6 +97,31 @@ def test_ner_single_tone_is_the_dirichlet_kernel():
     np.testing.assert_allclose(F, ref, atol=1e-10)
 
 
+def test_ner_adj_at_integer_frequencies_is_the_inverse_dft():
+    """At nu = 0..Nt-1 the transposed NER sum sum_l exp(+2 pi i nu_l n/Nt) P_l is
+    Nt times the inverse DFT of P."""
+    Nt = 32
+    pr = _grid_problem(4, 4, 8, Nt)
+    rng = np.random.default_rng(5)
+    P = rng.standard_normal((2, Nt)) + 1j * rng.standard_normal((2, Nt))
+    nus = np.tile(np.arange(Nt, dtype=np.float64), (2, 1))
+    T = oracle.ner_adj(pr, P, nus)
+    np.testing.assert_allclose(T, Nt * np.fft.ifft(P, axis=1), atol=1e-10)
+
+
+def test_ner_adj_is_the_conjugate_transpose_of_ner():
+    """<ner(G), P> = <G, ner_adj(P)> for non-integer frequencies."""
+    Nt = 48
+    pr = _grid_problem(4, 4, 8, Nt)
+    rng = np.random.default_rng(6)
+    G = rng.standard_normal((3, Nt)) + 1j * rng.standard_normal((3, Nt))
+    nus = rng.uniform(-30.0, 30.0, (3, 11))
+    P = rng.standard_normal((3, 11)) + 1j * rng.standard_normal((3, 11))
+    lhs = np.vdot(oracle.ner(pr, G, nus), P)
+    rhs = np.vdot(G, oracle.ner_adj(pr, P, nus))
+    assert abs(lhs - rhs) <= 1e-9 * abs(lhs)
+
+
 def test_kappa_map_and_jacobian_special_values():
     """W(0,0) = 2 and W(j != 0, 0) = 0 (the readings of the 0/0 in 2l/kappa);
     on the j = 0 axis W = 2 for every l; kappa is odd in l and depends on j
