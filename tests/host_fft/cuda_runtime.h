@@ -1,12 +1,15 @@
-// Host stand-in for the few CUDA names the in-shared-memory FFT header uses,
-// so that the header itself can be compiled with g++ and run on CPU threads
-// (one std::thread per CUDA thread, __syncthreads as a std::barrier).  Test
-// infrastructure only.
+// Host stand-in for the few CUDA names that the in-shared-memory FFT header
+// and the spread's register-window header use, so that those headers compile
+// with g++ and run on CPU threads (one std::thread per CUDA thread,
+// __syncthreads as a std::barrier).  Test infrastructure only.
 #pragma once
 #include <cmath>
 
 struct float2 {
     float x, y;
+};
+struct float4 {
+    float x, y, z, w;
 };
 inline float2 make_float2(float x, float y) { return float2{x, y}; }
 
@@ -26,4 +29,8 @@ template <class T>
 inline T __ldg(const T* p) { return *p; }
 // one packed FP32x2 add: two independent round-to-nearest adds
 inline float2 __fadd2_rn(float2 a, float2 b) { return float2{a.x + b.x, a.y + b.y}; }
+// one packed FP32x2 fused multiply-add: two independent fmaf
+inline float2 __ffma2_rn(float2 a, float2 b, float2 c) {
+    return float2{std::fmaf(a.x, b.x, c.x), std::fmaf(a.y, b.y, c.y)};
+}
 inline int __clz(int v) { return __builtin_clz((unsigned)v); }

@@ -1,0 +1,95 @@
+// Runs the spread's register-window helpers (spread_window.cuh) on the host
+// for tests: every lane of one lane group sweeps the entries of a column
+// segment [c0, c1) exactly as the spread kernels do (window base, retirement
+// of the lower WT columns, taps added at offset bx4 - base), writing finished
+// columns into the padded row buffer.  The buffer is returned in linear
+// layout, NaN where the sweep wrote nothing.  Test infrastructure only.
+#include <cmath>
+#include <vector>
+
+#include "spread_window.cuh"
+
+thread_local HostDim3 threadIdx;
+HostDim3 blockDim;
+void __syncthreads() {}
+
+using namespace nedner;
+
+// Two time samples per lane (32 lanes, 64 samples): g is [nent][64].
+template <int WT>
+static void sweep2(int Lx, int c0, int c1, int nent, const int* bx4, const float* taps, const float* g,
+                   float* out) {
+    std::vector<float2> Z((size_t)padded_len(Lx * 32) + 16, make_float2(NAN, NAN));
+    for (int ln = 0; ln < 32; ++ln) {
+        float2 acc[2 * WT];
+        for (int k = 0; k < 2 * WT; ++k) acc[k] = make_float2(0.f, 0.f);
+        int base = (c0 - WT) & ~3;
+        for (int e = 0; e < nent; ++e) {
+            float4 wv[WT / 4];
+            for (int k4 = 0; k4 < WT / 4; ++k4)
+                wv[k4] = float4{taps[e * WT + 4 * k4], taps[e * WT + 4 * k4 + 1], taps[e * WT + 4 * k4 + 2],
+                                taps[e * WT + 4 * k4 + 3]};
+            const float2 g2 = make_float2(g[e * 64 + 2 * ln], g[e * 64 + 2 * ln + 1]);
+            sweep_entry2<WT>(acc, Z.data(), ln, base, c0, c1, bx4[e], wv, g2);
+        }
+        while (base < c1) {
+            flush_lower2<WT>(acc, Z.data(), ln, base, c0, c1);
+            base += WT;
+        }
+    }
+    for (int col = 0; col < Lx; ++col)
+        for (int ln = 0; ln < 32; ++ln) {
+            const float2 v = Z[padx(col * 32 + ln)];
+            out[(col * 32 + ln) * 2] = v.x;
+            out[(col * 32 + ln) * 2 + 1] = v.y;
+        }
+}
+
+// One time sample per lane (C lanes, C a power of two >= 2): g is [nent][C].
+template <int WT>
+static void sweep1(int Lx, int C, int c0, int c1, int nent, const int* bx4, const float* taps, const float* g,
+                   float* out) {
+    const int nb = C / 2, lnb = ilog2(nb);
+    std::vector<float2> Z((size_t)padded_len(Lx * nb) + 16, make_float2(NAN, NAN));
+    float* Zf = reinterpret_cast<float*>(Z.data());
+    for (int hl = 0; hl < C; ++hl) {
+        float acc[2 * WT];
+        for (int k = 0; k < 2 * WT; ++k) acc[k] = 0.f;
+        int base = (c0 - WT) & ~3;
+        for (int e = 0; e < nent; ++e) {
+            float4 wv[WT / 4];
+            for (int k4 = 0; k4 < WT / 4; ++k4)
+                wv[k4] = float4{taps[e * WT + 4 * k4], taps[e * WT + 4 * k4 + 1], taps[e * WT + 4 * k4 + 2],
+                                taps[e * WT + 4 * k4 + 3]};
+            sweep_entry<WT>(acc, Zf, lnb, hl, base, c0, c1, bx4[e], wv, g[e * C + hl]);
+        }
+        while (base < c1) {
+            flush_lower<WT>(acc, Zf, lnb, hl, base, c0, c1);
+            base += WT;
+        }
+    }
+    for (int col = 0; col < Lx; ++col)
+        for (int hl = 0; hl < C; ++hl) out[col * C + hl] = Zf[2 * padx((col << lnb) + (hl >> 1)) + (hl & 1)];
+}
+
+extern "C" int host_sweep(int two, int WT, int Lx, int C, int c0, int c1, int nent, const int* bx4,
+                          const float* taps, const float* g, float* out) {
+    if (c0 < 0 || c1 > Lx || c0 > c1) return -1;
+    if (two) {
+        switch (WT) {
+            case 8: sweep2<8>(Lx, c0, c1, nent, bx4, taps, g, out); return 0;
+            case 12: sweep2<12>(Lx, c0, c1, nent, bx4, taps, g, out); return 0;
+            case 16: sweep2<16>(Lx, c0, c1, nent, bx4, taps, g, out); return 0;
+            case 20: sweep2<20>(Lx, c0, c1, nent, bx4, taps, g, out); return 0;
+        }
+        return -1;
+    }
+    if (C < 2 || (C & (C - 1))) return -1;
+    switch (WT) {
+        case 8: sweep1<8>(Lx, C, c0, c1, nent, bx4, taps, g, out); return 0;
+        case 12: sweep1<12>(Lx, C, c0, c1, nent, bx4, taps, g, out); return 0;
+        case 16: sweep1<16>(Lx, C, c0, c1, nent, bx4, taps, g, out); return 0;
+        case 20: sweep1<20>(Lx, C, c0, c1, nent, bx4, taps, g, out); return 0;
+    }
+    return -1;
+}

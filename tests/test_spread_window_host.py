@@ -1,0 +1,106 @@
+"""The spread's register-window helpers (csrc/spread_window.cuh) compiled with
+g++ and run on the host (tests/host_fft/window_harness.cpp), against a direct
+FP64 accumulation of the same entries: every lane sweeps the entries of a
+column segment [c0, c1) in first-column order, and each column of the
+segment must hold sum_e tap_e[col - bx4_e] g_e once the sweep ends, while no
+column outside the segment is written.  Covers both lane layouts (one and two
+time samples per lane), every tap count WT the kernels instantiate, segments
+at the row's ends (entries repeated at bx - Lx), and empty segments."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_1510_01078_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    out = str(tmp_path_factory.mktemp("host_window") / "libwin.so")
+    cmd = [gxx, "-std=c++20", "-O2", "-shared", "-fPIC", "-Wno-unknown-pragmas", "-I", os.path.join(HERE, "host_fft"),
+           "-I", CSRC, os.path.join(HERE, "host_fft", "window_harness.cpp"), "-o", out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    h = ctypes.CDLL(out)
+    I, F = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)
+    h.host_sweep.argtypes = [ctypes.c_int] * 7 + [I, F, F, F]
+    h.host_sweep.restype = ctypes.c_int
+    return h
+
+
+def taps_for(w):
+    return ((w + 3) + 3) // 4 * 4          # w taps after up to 3 leading zeros, rounded up to 4
+
+
+def entries(rng, w, WT, Lx, c0, c1, n):
+    """Entries reaching into [c0, c1): first column bx in [c0 - w + 1, c1), sorted;
+    bx < 0 stands for an entry wrapped around x = Lx."""
+    lo = c0 - w + 1
+    bx = np.sort(rng.integers(lo, max(lo + 1, c1), n)) if n else np.zeros(0, np.int64)
+    bx4 = bx & ~3
+    taps = np.zeros((n, WT), np.float32)
+    for e in range(n):
+        off = int(bx[e] - bx4[e])
+        taps[e, off:off + w] = rng.uniform(0.1, 1.0, w)
+    return bx4.astype(np.int32), taps
+
+
+def reference(bx4, taps, g, Lx, c0, c1):
+    lanes = g.shape[1]
+    Z = np.zeros((Lx, lanes))
+    for e in range(len(bx4)):
+        for k in range(taps.shape[1]):
+            col = int(bx4[e]) + k
+            if c0 <= col < c1:
+                Z[col] += float(taps[e, k]) * g[e].astype(np.float64)
+    return Z
+
+
+def sweep(lib, two, WT, Lx, C, c0, c1, bx4, taps, g):
+    I, F = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)
+    lanes = 64 if two else C
+    out = np.empty((Lx, lanes), np.float32)
+    bx4 = np.ascontiguousarray(bx4, np.int32)
+    taps = np.ascontiguousarray(taps, np.float32)
+    g = np.ascontiguousarray(g, np.float32)
+    r = lib.host_sweep(int(two), WT, Lx, C, c0, c1, len(bx4), bx4.ctypes.data_as(I), taps.ctypes.data_as(F),
+                       g.ctypes.data_as(F), out.ctypes.data_as(F))
+    assert r == 0
+    return out
+
+
+def segments(Lx):
+    yield 0, Lx // 4                       # starts at the row's first column (wrapped entries)
+    yield Lx // 4, Lx // 4 + 37            # interior, ragged width
+    yield 3 * Lx // 4, Lx                  # ends at the row's last column
+    yield 5, 6                             # one column
+    yield 10, 10                           # empty
+
+
+@pytest.mark.parametrize("two", [True, False], ids=["two_per_lane", "one_per_lane"])
+@pytest.mark.parametrize("w", [4, 6, 8, 10, 12, 14, 16])
+def test_window_sweep_matches_direct_accumulation(lib, two, w):
+    WT = taps_for(w)
+    rng = np.random.default_rng(100 * w + two)
+    for Lx in (64, 512):
+        for C in ((64,) if two else (2, 8, 32)):
+            lanes = 64 if two else C
+            for c0, c1 in segments(Lx):
+                for n in (0, 1, 7, 60):
+                    bx4, taps = entries(rng, w, WT, Lx, c0, c1, n)
+                    g = rng.standard_normal((n, lanes)).astype(np.float32)
+                    got = sweep(lib, two, WT, Lx, C, c0, c1, bx4, taps, g)
+                    inside = got[c0:c1]
+                    assert np.isfinite(inside).all(), (w, Lx, C, c0, c1, n)
+                    want = reference(bx4, taps, g, Lx, c0, c1)[c0:c1]
+                    scale = max(1.0, float(np.abs(want).max()) if want.size else 1.0)
+                    assert float(np.abs(inside - want).max(initial=0.0)) <= 1e-5 * scale, (w, Lx, C, c0, c1, n)
+                    outside = np.concatenate([got[:c0], got[c1:]])
+                    assert np.isnan(outside).all(), (w, Lx, C, c0, c1, n)
