@@ -1,12 +1,18 @@
-// Runs the spread's register-window helpers (spread_window.cuh) on the host
-// for tests: every lane of one lane group sweeps the entries of a column
-// segment [c0, c1) exactly as the spread kernels do (window base, retirement
-// of the lower WT columns, taps added at offset bx4 - base), writing finished
-// columns into the padded row buffer.  The buffer is returned in linear
-// layout, NaN where the sweep wrote nothing.  Test infrastructure only.
+// Runs the register-window helpers of the spread (spread_window.cuh) and of
+// the transposed gather (gather_window.cuh) on the host for tests.
+//  - host_sweep: every lane of one lane group sweeps the entries of a column
+//    segment [c0, c1) exactly as the spread kernels do (window base,
+//    retirement of the lower WT columns, taps added at offset bx4 - base),
+//    writing finished columns into the padded row buffer, returned in linear
+//    layout (NaN where the sweep wrote nothing).
+//  - host_gather: every lane walks a run of entries exactly as the gather
+//    kernels do and returns each entry's two tap-weighted sums of the row
+//    (read modulo Lx).
+// Test infrastructure only.
 #include <cmath>
 #include <vector>
 
+#include "gather_window.cuh"
 #include "spread_window.cuh"
 
 thread_local HostDim3 threadIdx;
@@ -91,5 +97,72 @@ extern "C" int host_sweep(int two, int WT, int Lx, int C, int c0, int c1, int ne
         case 16: sweep1<16>(Lx, C, c0, c1, nent, bx4, taps, g, out); return 0;
         case 20: sweep1<20>(Lx, C, c0, c1, nent, bx4, taps, g, out); return 0;
     }
+    return -1;
+}
+
+// row: [Lx][lanes] real samples (lanes = 64 with two per lane, else C);
+// out_a, out_b: [nent][lanes].
+template <int WT>
+static void gather2(int Lx, int nent, const int* bx4, const float* ta, const float* tb, const float* row,
+                    float* out_a, float* out_b) {
+    std::vector<float2> Z((size_t)padded_len(Lx * 32) + 16, make_float2(NAN, NAN));
+    for (int col = 0; col < Lx; ++col)
+        for (int ln = 0; ln < 32; ++ln) Z[padx(col * 32 + ln)] = make_float2(row[col * 64 + 2 * ln], row[col * 64 + 2 * ln + 1]);
+    for (int ln = 0; ln < 32; ++ln) {
+        float2 win[2 * WT];
+        int base = bx4[0];
+        win2_load<WT>(win, Z.data(), ln, Lx, base, 0);
+        win2_load<WT>(win, Z.data(), ln, Lx, base, WT);
+        for (int j = 0; j < nent; ++j) {
+            win2_advance<WT>(win, Z.data(), ln, Lx, base, bx4[j]);
+            float2 va, vb;
+            win2_entry<WT, true>(win, (bx4[j] - base) >> 2, reinterpret_cast<const float4*>(ta + j * WT),
+                                 reinterpret_cast<const float4*>(tb + j * WT), va, vb);
+            out_a[j * 64 + 2 * ln] = va.x;
+            out_a[j * 64 + 2 * ln + 1] = va.y;
+            out_b[j * 64 + 2 * ln] = vb.x;
+            out_b[j * 64 + 2 * ln + 1] = vb.y;
+        }
+    }
+}
+
+template <int WT>
+static void gather1(int Lx, int C, int nent, const int* bx4, const float* ta, const float* tb, const float* row,
+                    float* out_a, float* out_b) {
+    const int nb = C / 2, lnb = ilog2(nb);
+    std::vector<float2> Z((size_t)padded_len(Lx * nb) + 16, make_float2(NAN, NAN));
+    float* Zf = reinterpret_cast<float*>(Z.data());
+    for (int col = 0; col < Lx; ++col)
+        for (int ln = 0; ln < C; ++ln) Zf[rpos(col, lnb, ln)] = row[col * C + ln];
+    for (int ln = 0; ln < C; ++ln) {
+        float win[2 * WT];
+        int base = bx4[0];
+        win_load<WT>(win, Zf, lnb, ln, Lx, base, 0);
+        win_load<WT>(win, Zf, lnb, ln, Lx, base, WT);
+        for (int j = 0; j < nent; ++j) {
+            win_advance<WT>(win, Zf, lnb, ln, Lx, base, bx4[j]);
+            const float2 v = win_entry<WT, true>(win, (bx4[j] - base) >> 2, reinterpret_cast<const float4*>(ta + j * WT),
+                                                 reinterpret_cast<const float4*>(tb + j * WT));
+            out_a[j * C + ln] = v.x;
+            out_b[j * C + ln] = v.y;
+        }
+    }
+}
+
+extern "C" int host_gather(int two, int WT, int Lx, int C, int nent, const int* bx4, const float* ta, const float* tb,
+                           const float* row, float* out_a, float* out_b) {
+    if (nent < 1 || Lx < 8 || (Lx & (Lx - 1))) return -1;
+    if (!two && (C < 2 || (C & (C - 1)))) return -1;
+#define NEDNER_HOST_GATHER(W)                                                   \
+    if (two) gather2<W>(Lx, nent, bx4, ta, tb, row, out_a, out_b);             \
+    else gather1<W>(Lx, C, nent, bx4, ta, tb, row, out_a, out_b);              \
+    return 0;
+    switch (WT) {
+        case 8: NEDNER_HOST_GATHER(8)
+        case 12: NEDNER_HOST_GATHER(12)
+        case 16: NEDNER_HOST_GATHER(16)
+        case 20: NEDNER_HOST_GATHER(20)
+    }
+#undef NEDNER_HOST_GATHER
     return -1;
 }

@@ -1,11 +1,15 @@
-"""The spread's register-window helpers (csrc/spread_window.cuh) compiled with
-g++ and run on the host (tests/host_fft/window_harness.cpp), against a direct
-FP64 accumulation of the same entries: every lane sweeps the entries of a
-column segment [c0, c1) in first-column order, and each column of the
-segment must hold sum_e tap_e[col - bx4_e] g_e once the sweep ends, while no
-column outside the segment is written.  Covers both lane layouts (one and two
-time samples per lane), every tap count WT the kernels instantiate, segments
-at the row's ends (entries repeated at bx - Lx), and empty segments."""
+"""The register-window helpers of the spread (csrc/spread_window.cuh) and of
+the transposed gather (csrc/gather_window.cuh) compiled with g++ and run on
+the host (tests/host_fft/window_harness.cpp), against direct FP64 sums.
+
+Spread: every lane sweeps the entries of a column segment [c0, c1) in
+first-column order; each column of the segment must hold
+sum_e tap_e[col - bx4_e] g_e once the sweep ends, and no column outside the
+segment may be written.  Gather (its transpose): every entry of a run gets
+sum_k tap[k] r[(bx4 + k) mod Lx] for two tap sets.  Both lane layouts (one
+and two time samples per lane), every tap count WT the kernels instantiate,
+segments at the row's ends (entries repeated at bx - Lx), empty segments,
+and runs that wrap around x = Lx."""
 import ctypes
 import os
 import shutil
@@ -104,3 +108,50 @@ def test_window_sweep_matches_direct_accumulation(lib, two, w):
                     assert float(np.abs(inside - want).max(initial=0.0)) <= 1e-5 * scale, (w, Lx, C, c0, c1, n)
                     outside = np.concatenate([got[:c0], got[c1:]])
                     assert np.isnan(outside).all(), (w, Lx, C, c0, c1, n)
+
+
+def gather(lib, two, WT, Lx, C, bx4, ta, tb, row):
+    I, F = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)
+    lanes = 64 if two else C
+    n = len(bx4)
+    oa = np.empty((n, lanes), np.float32)
+    ob = np.empty((n, lanes), np.float32)
+    bx4 = np.ascontiguousarray(bx4, np.int32)
+    ta = np.ascontiguousarray(ta, np.float32)
+    tb = np.ascontiguousarray(tb, np.float32)
+    row = np.ascontiguousarray(row, np.float32)
+    lib.host_gather.argtypes = [ctypes.c_int] * 5 + [I, F, F, F, F, F]
+    r = lib.host_gather(int(two), WT, Lx, C, n, bx4.ctypes.data_as(I), ta.ctypes.data_as(F), tb.ctypes.data_as(F),
+                        row.ctypes.data_as(F), oa.ctypes.data_as(F), ob.ctypes.data_as(F))
+    assert r == 0
+    return oa, ob
+
+
+@pytest.mark.parametrize("two", [True, False], ids=["two_per_lane", "one_per_lane"])
+@pytest.mark.parametrize("w", [4, 6, 8, 10, 12, 14, 16])
+def test_gather_window_matches_direct_sums(lib, two, w):
+    WT = taps_for(w)
+    rng = np.random.default_rng(200 * w + two)
+    for Lx in (64, 512):
+        for C in ((64,) if two else (2, 16, 32)):
+            lanes = 64 if two else C
+            row = rng.standard_normal((Lx, lanes)).astype(np.float32)
+            for n in (1, 5, 80):
+                # a run of a row's entries, first columns sorted in [0, Lx); taps past
+                # Lx - 1 read the row modulo Lx
+                bx = np.sort(rng.integers(0, Lx, n))
+                bx4 = (bx & ~3).astype(np.int32)
+                ta = np.zeros((n, WT), np.float32)
+                tb = np.zeros((n, WT), np.float32)
+                for e in range(n):
+                    off = int(bx[e] - bx4[e])
+                    ta[e, off:off + w] = rng.uniform(0.1, 1.0, w)
+                    tb[e, off:off + w] = rng.uniform(-1.0, 1.0, w)
+                oa, ob = gather(lib, two, WT, Lx, C, bx4, ta, tb, row)
+                cols = (bx4[:, None] + np.arange(WT)[None, :]) % Lx
+                r64 = row.astype(np.float64)
+                wa = np.einsum("ek,ekt->et", ta.astype(np.float64), r64[cols])
+                wb = np.einsum("ek,ekt->et", tb.astype(np.float64), r64[cols])
+                assert np.isfinite(oa).all() and np.isfinite(ob).all()
+                assert float(np.abs(oa - wa).max()) <= 1e-5 * max(1.0, float(np.abs(wa).max())), (w, Lx, C, n)
+                assert float(np.abs(ob - wb).max()) <= 1e-5 * max(1.0, float(np.abs(wb).max())), (w, Lx, C, n)
