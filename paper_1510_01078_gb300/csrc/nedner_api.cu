@@ -740,12 +740,15 @@ nedner_status nedner_forward_host(nedner_plan_t p, const float* g_host, float* p
     cudaError_t e = cudaSuccess;
     const size_t gbytes = (size_t)p->M * G.Nt * sizeof(float);
     const size_t pbytes = (size_t)G.nx * G.ny * G.nz * sizeof(float);
-    if (!p->host_p0) {
-        // first call: device copies of g and p0, the copy streams and their events
-        if (!e && gbytes) e = cudaMalloc((void**)&p->host_g, gbytes);
-        if (!e) e = cudaMalloc((void**)&p->host_p0, pbytes);
-        for (int i = 0; i < NCS && !e; ++i) e = cudaStreamCreateWithFlags(&p->copy_stream[i], cudaStreamNonBlocking);
-        for (int i = 0; i < 16 && !e; ++i) e = cudaEventCreateWithFlags(&p->host_ev[i], cudaEventDisableTiming);
+    if (!p->host_p0 || !p->host_ev[15]) {
+        // first call: device copies of g and p0, the copy streams and their
+        // events; after a failure, a later call creates only what is missing
+        if (!e && gbytes && !p->host_g) e = cudaMalloc((void**)&p->host_g, gbytes);
+        if (!e && !p->host_p0) e = cudaMalloc((void**)&p->host_p0, pbytes);
+        for (int i = 0; i < NCS && !e; ++i)
+            if (!p->copy_stream[i]) e = cudaStreamCreateWithFlags(&p->copy_stream[i], cudaStreamNonBlocking);
+        for (int i = 0; i < 16 && !e; ++i)
+            if (!p->host_ev[i]) e = cudaEventCreateWithFlags(&p->host_ev[i], cudaEventDisableTiming);
         if (e) return e == cudaErrorMemoryAllocation ? NEDNER_ENOMEM : NEDNER_ECUDA;
     }
     cudaStream_t* cs = p->copy_stream;
