@@ -150,8 +150,11 @@ double win_tap_polys(const Window& W, int D, std::vector<double>& coef) {
         }
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) coef[(size_t)k * n + i] += c[j] * T[j][i];
+        // t in the open interval (0, 1): at t = 0 the last tap sits on the
+        // support edge, where phi is 0 by convention and the polynomial gives
+        // the one-sided limit 1/I0(beta), the window's own truncation step
         for (int i = 0; i <= 400; ++i) {
-            double t = i / 400.0 * 0.999999;
+            double t = (i + 0.5) / 401.0;
             double s = 2.0 * t - 1.0, p = 0.0;
             for (int d = D; d >= 0; --d) p = p * s + coef[(size_t)k * n + d];
             double ref = win_phi(W, t + 0.5 * w - 1.0 - k);

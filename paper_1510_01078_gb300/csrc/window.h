@@ -38,8 +38,8 @@ double win_phihat(const Window& W, double f);  // continuous transform at f (cyc
 // Monomial coefficients, in s = 2 t - 1, of degree-D polynomials P_k with
 // P_k(s) ~ phi(t + w/2 - 1 - k), t in [0, 1), for each tap k = 0..w-1
 // (Chebyshev interpolation in FP64).  Layout coef[k * (D + 1) + d].
-// Returns the largest deviation seen on a fine sample of t, relative to
-// max |phi|.
+// Returns the largest deviation seen on a fine sample of t in (0, 1),
+// relative to max |phi|.
 double win_tap_polys(const Window& W, int D, std::vector<double>& coef);
 
 }  // namespace nedner
