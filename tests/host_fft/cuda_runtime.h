@@ -1,6 +1,6 @@
-// Host stand-in for the few CUDA names that the in-shared-memory FFT header
-// and the spread's register-window header use, so that those headers compile
-// with g++ and run on CPU threads (one std::thread per CUDA thread,
+// Host stand-in for the few CUDA names that the in-shared-memory FFT header,
+// the register-window headers and the NER evaluation header use, so that
+// those headers compile with g++ and run on CPU threads (one std::thread per CUDA thread,
 // __syncthreads as a std::barrier).  Test infrastructure only.
 #pragma once
 #include <cmath>
@@ -11,7 +11,15 @@ struct float2 {
 struct float4 {
     float x, y, z, w;
 };
+struct int4 {
+    int x, y, z, w;
+};
 inline float2 make_float2(float x, float y) { return float2{x, y}; }
+
+// opaque handles and status of the runtime API (declarations only)
+typedef struct HostStream* cudaStream_t;
+typedef struct HostEvent* cudaEvent_t;
+typedef int cudaError_t;
 
 struct HostDim3 {
     unsigned x = 0, y = 0, z = 0;
@@ -34,3 +42,9 @@ inline float2 __ffma2_rn(float2 a, float2 b, float2 c) {
     return float2{std::fmaf(a.x, b.x, c.x), std::fmaf(a.y, b.y, c.y)};
 }
 inline int __clz(int v) { return __builtin_clz((unsigned)v); }
+// sin(pi x) and cos(pi x), through double precision
+inline void sincospif(float x, float* s, float* c) {
+    const double a = 3.14159265358979323846 * (double)x;
+    *s = (float)std::sin(a);
+    *c = (float)std::cos(a);
+}
