@@ -49,38 +49,6 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // real and imaginary part) in a padded buffer, transformed in place along x
 // (PER values per thread), and jx = 0..nx/2 is kept, divided by phihat(jx/Lx).
 // ---------------------------------------------------------------------------
-// Output step of the spread stage: jx = 0..nx/2 of the row, divided by
-// phihat(jx/Lx), for complex column b (real time samples 2b, 2b+1 packed as
-// real and imaginary part), written as the two time samples n0 + 2b, n0 + 2b + 1
-// of R.  With fold, the x-FFT's last radix-2 pass is done here (see block_fft_ip).
-__device__ __forceinline__ void spread_output(const Geo& G, const float2* Z, int lnb, int b, int jx, bool fold,
-                                              const float* __restrict__ deconv_x, const float2* __restrict__ tw,
-                                              int gy, int n0, float2* __restrict__ R) {
-    const int Lx = G.Lx;
-    float2 zk, zm;
-    if (fold) {
-        const int H = Lx >> 1;
-        const float2 a0 = Z[padx((jx << lnb) + b)], a1 = Z[padx(((jx + H) << lnb) + b)];
-        if (jx == 0) {
-            zk = cadd(a0, a1);
-            zm = cconj(zk);
-        } else {
-            const float2 w = __ldg(&tw[Lx + jx]);                       // exp(-2 pi i jx / Lx)
-            const float2 b0 = Z[padx(((H - jx) << lnb) + b)], b1 = Z[padx(((Lx - jx) << lnb) + b)];
-            zk = cadd(a0, cmul(w, a1));
-            zm = cconj(cadd(b0, cmul(cconj(w), b1)));                     // conj X[Lx - jx]
-        }
-    } else {
-        zk = Z[padx((jx << lnb) + b)];
-        zm = cconj(Z[padx((((Lx - jx) & (Lx - 1)) << lnb) + b)]);
-    }
-    // column 2b = (Z[k] + conj Z[-k]) / 2, column 2b+1 = -i (Z[k] - conj Z[-k]) / 2
-    const float d = 0.5f * __ldg(&deconv_x[jx]);
-    const float2 x0 = cscale(cadd(zk, zm), d);
-    const float2 x1 = cscale(mul_i(csub(zk, zm), -1), d);
-    *reinterpret_cast<float4*>(&R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + 2 * b]) = make_float4(x0.x, x0.y, x1.x, x1.y);
-}
-
 template <int WT, int PER>
 __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_spread_xfft(Geo G, int C, int yb, const float* __restrict__ g,
                                                                           const int4* __restrict__ seg,

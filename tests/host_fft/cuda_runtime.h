@@ -15,6 +15,7 @@ struct int4 {
     int x, y, z, w;
 };
 inline float2 make_float2(float x, float y) { return float2{x, y}; }
+inline float4 make_float4(float x, float y, float z, float w) { return float4{x, y, z, w}; }
 
 // opaque handles and status of the runtime API (declarations only)
 typedef struct HostStream* cudaStream_t;

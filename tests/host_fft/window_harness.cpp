@@ -10,6 +10,7 @@
 //    (read modulo Lx).
 // Test infrastructure only.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "gather_window.cuh"
@@ -165,4 +166,36 @@ extern "C" int host_gather(int two, int WT, int Lx, int C, int nent, const int* 
     }
 #undef NEDNER_HOST_GATHER
     return -1;
+}
+
+// The spread stage's output step for one row: Zin is the row after the x-FFT
+// (with fold, before its last radix-2 pass), linear [Lx][nb] interleaved
+// complex; out is R for that row, [nxh][2 nb] complex (time samples 2b, 2b+1).
+extern "C" int host_spread_output(int Lx, int nb, int fold, const float* Zin, const float* deconv_x, float* out) {
+    if (Lx < 8 || (Lx & (Lx - 1)) || nb < 1 || (nb & (nb - 1)) || Lx > TW_N) return -1;
+    std::vector<float2> tw(2 * TW_N);
+    tw[0] = make_float2(1.f, 0.f);
+    for (int N = 1; N <= TW_N; N *= 2)
+        for (int k = 0; k < N; ++k) {
+            const double a = -2.0 * 3.14159265358979323846 * (double)k / N;
+            tw[N + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    Geo G;
+    std::memset(&G, 0, sizeof(G));
+    G.Lx = Lx;
+    G.nx = Lx / 2;
+    G.nxh = Lx / 4 + 1;
+    G.Ly = 1;
+    G.Nt = 2 * nb;
+    std::vector<float2> Z((size_t)padded_len(Lx * nb) + 16);
+    for (int a = 0; a < Lx * nb; ++a) Z[padx(a)] = make_float2(Zin[2 * a], Zin[2 * a + 1]);
+    std::vector<float2> R((size_t)G.nxh * G.Nt);
+    const int lnb = ilog2(nb);
+    for (int jx = 0; jx < G.nxh; ++jx)
+        for (int b = 0; b < nb; ++b) spread_output(G, Z.data(), lnb, b, jx, fold != 0, deconv_x, tw.data(), 0, 0, R.data());
+    for (size_t i = 0; i < R.size(); ++i) {
+        out[2 * i] = R[i].x;
+        out[2 * i + 1] = R[i].y;
+    }
+    return 0;
 }

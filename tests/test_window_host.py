@@ -9,7 +9,8 @@ segment may be written.  Gather (its transpose): every entry of a run gets
 sum_k tap[k] r[(bx4 + k) mod Lx] for two tap sets.  Both lane layouts (one
 and two time samples per lane), every tap count WT the kernels instantiate,
 segments at the row's ends (entries repeated at bx - Lx), empty segments,
-and runs that wrap around x = Lx."""
+and runs that wrap around x = Lx.  Also the spread stage's output step
+(the folded last x-FFT pass and the split of packed time-sample pairs)."""
 import ctypes
 import os
 import shutil
@@ -155,3 +156,32 @@ def test_gather_window_matches_direct_sums(lib, two, w):
                 assert np.isfinite(oa).all() and np.isfinite(ob).all()
                 assert float(np.abs(oa - wa).max()) <= 1e-5 * max(1.0, float(np.abs(wa).max())), (w, Lx, C, n)
                 assert float(np.abs(ob - wb).max()) <= 1e-5 * max(1.0, float(np.abs(wb).max())), (w, Lx, C, n)
+
+
+@pytest.mark.parametrize("Lx,nb", [(64, 4), (256, 32), (512, 32), (512, 1), (4096, 2)])
+@pytest.mark.parametrize("fold", [False, True], ids=["last_pass_done", "last_pass_folded"])
+def test_spread_output_step(lib, Lx, nb, fold):
+    """The spread stage's output step (spread_output in csrc/spread_window.cuh):
+    from the x-transformed row of packed time-sample pairs z = x[2b] + i x[2b+1]
+    (with fold, the row before its last radix-2 pass, s[k] = (X[k] + X[k+N/2])/2,
+    s[k+N/2] = (X[k] - X[k+N/2]) / (2 w^k)), it must write, for jx = 0..Lx/4, the
+    FFT of each real time sample's row times the deconvolution factor."""
+    F = ctypes.POINTER(ctypes.c_float)
+    lib.host_spread_output.argtypes = [ctypes.c_int] * 3 + [F, F, F]
+    rng = np.random.default_rng(Lx + nb + fold)
+    x = rng.standard_normal((Lx, 2 * nb))
+    X = np.fft.fft(x[:, 0::2] + 1j * x[:, 1::2], axis=0)
+    if fold:
+        H = Lx // 2
+        w = np.exp(-2j * np.pi * np.arange(H)[:, None] / Lx)
+        X = np.concatenate([(X[:H] + X[H:]) / 2, (X[:H] - X[H:]) / (2 * w)])
+    Zin = np.empty((Lx, nb, 2), np.float32)
+    Zin[..., 0], Zin[..., 1] = X.real, X.imag
+    nxh = Lx // 4 + 1
+    dec = rng.uniform(0.5, 2.0, nxh).astype(np.float32)
+    out = np.empty((nxh, 2 * nb, 2), np.float32)
+    assert lib.host_spread_output(Lx, nb, int(fold), Zin.ctypes.data_as(F), dec.ctypes.data_as(F),
+                                  out.ctypes.data_as(F)) == 0
+    got = out[..., 0] + 1j * out[..., 1]
+    want = np.fft.fft(x, axis=0)[:nxh] * dec[:, None]
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-6
