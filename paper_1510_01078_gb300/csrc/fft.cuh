@@ -139,6 +139,28 @@ __device__ __forceinline__ constexpr int out_index(int k) {
     return R == 8 ? 4 * (k & 1) + (k >> 1) : R == 16 ? 4 * (k & 3) + (k >> 2) : k;
 }
 
+// Complex-to-real inverse transform of length N from the half spectrum
+// X[0..N/2] through the half-length complex transform (H = N/2): the input of
+// the length-H inverse FFT is Z[k] = E[k] + i O[k], E = X[k] + conj X[H-k],
+// O = (X[k] - conj X[H-k]) exp(2 pi i k / N); the imaginary parts of X[0] and
+// X[H] are dropped (the real part of the full inverse DFT).  For one pair
+// (xk = X[k], xm = X[H-k]), 0 <= k <= H/2, returns zk = Z[k] and
+// zm = Z[H-k] = conj E[k] + i conj O[k] (zm is Z[H/2] again when k = H/2 and
+// unused when k = 0).  Then z = IFFT_H(Z) holds the real samples as
+// x[2p] = Re z[p], x[2p+1] = Im z[p].
+__device__ __forceinline__ void c2r_pair(float2 xk, float2 xm, int k, int N, const float2* __restrict__ tw,
+                                         float2& zk, float2& zm) {
+    if (k == 0) {
+        xk.y = 0.f;
+        xm.y = 0.f;
+    }
+    const float2 xmc = cconj(xm);
+    const float2 E = cadd(xk, xmc);
+    const float2 O = cmul(csub(xk, xmc), twiddle(tw, k, N, +1));
+    zk = cadd(E, mul_i(O, +1));
+    zm = cadd(cconj(E), mul_i(cconj(O), +1));
+}
+
 // ---------------------------------------------------------------------------
 // In place: every thread keeps its share of a pass in registers, so one
 // buffer holds the data throughout; the caller guarantees

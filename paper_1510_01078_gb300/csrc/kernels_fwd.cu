@@ -466,17 +466,10 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_img_xc2r(Geo G, int C, int zb,
     for (int it = threadIdx.x; it < (H / 2 + 1) * C; it += NT) {
         const int k = it >> lc;
         const int c = it & (C - 1);
-        float2 xk = src[k * kstride + c];
-        float2 xm = src[(H - k) * kstride + c];
-        if (k == 0) {
-            xk.y = 0.f;
-            xm.y = 0.f;
-        }
-        const float2 xmc = cconj(xm);
-        const float2 E = cadd(xk, xmc);
-        const float2 O = cmul(csub(xk, xmc), twiddle(tw, k, G.nx, +1));
-        A[padx((k << lc) + c)] = cadd(E, mul_i(O, +1));
-        if (k > 0 && k < H / 2) A[padx(((H - k) << lc) + c)] = cadd(cconj(E), mul_i(cconj(O), +1));
+        float2 zk, zm;
+        c2r_pair(src[k * kstride + c], src[(H - k) * kstride + c], k, G.nx, tw, zk, zm);
+        A[padx((k << lc) + c)] = zk;
+        if (k > 0 && k < H / 2) A[padx(((H - k) << lc) + c)] = zm;
     }
     block_fft_ip<16>(A, H, C, +1, tw);
     float2* dst = reinterpret_cast<float2*>(p0 + ((size_t)qz * G.ny + y0) * G.nx);

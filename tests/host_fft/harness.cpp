@@ -72,3 +72,24 @@ extern "C" int host_block_fft(int N, int nb, int dir, int per, int nt, int skip_
     }
     return 0;
 }
+
+// The complex-to-real pair formation (c2r_pair) for a half spectrum X[0..N/2]
+// (interleaved complex): out is Z[0..N/2-1] (interleaved), formed pair by pair
+// for k = 0..N/4 as the x complex-to-real kernel does.
+extern "C" int host_c2r_pairs(int N, const float* X, float* out) {
+    if (N < 4 || N > TW_N || (N & (N - 1))) return -1;
+    static const std::vector<float2> tw = twiddles();
+    const int H = N / 2;
+    for (int k = 0; k <= H / 2; ++k) {
+        float2 zk, zm;
+        c2r_pair(make_float2(X[2 * k], X[2 * k + 1]), make_float2(X[2 * (H - k)], X[2 * (H - k) + 1]), k, N,
+                 tw.data(), zk, zm);
+        out[2 * k] = zk.x;
+        out[2 * k + 1] = zk.y;
+        if (k > 0 && k < H / 2) {
+            out[2 * (H - k)] = zm.x;
+            out[2 * (H - k) + 1] = zm.y;
+        }
+    }
+    return 0;
+}

@@ -115,3 +115,24 @@ def test_zero_padded_first_pass(lib, N, nb, per, nt):
         y = run(lib, x, d, per, nt, zp=True)
         assert np.isfinite(y).all()
         assert rel(y, dft(x, d)) <= TOL
+
+
+@pytest.mark.parametrize("N", [4, 8, 16, 256, 512, 4096])
+def test_complex_to_real_pairs(lib, N):
+    """c2r_pair (the x complex-to-real stage's input): with Z formed from the
+    half spectrum X[0..N/2] pair by pair, z = IFFT_{N/2}(Z) interleaved
+    (x[2p] = Re z[p], x[2p+1] = Im z[p]) equals N irfft(X), which likewise drops
+    the imaginary parts of X[0] and X[N/2]."""
+    F = ctypes.POINTER(ctypes.c_float)
+    lib.host_c2r_pairs.argtypes = [ctypes.c_int, F, F]
+    rng = np.random.default_rng(N)
+    X = rng.standard_normal(N // 2 + 1) + 1j * rng.standard_normal(N // 2 + 1)
+    Xi = np.empty((N // 2 + 1, 2), np.float32)
+    Xi[:, 0], Xi[:, 1] = X.real, X.imag
+    Z = np.empty((N // 2, 2), np.float32)
+    assert lib.host_c2r_pairs(N, Xi.ctypes.data_as(F), Z.ctypes.data_as(F)) == 0
+    z = np.fft.ifft(Z[:, 0] + 1j * Z[:, 1]) * (N // 2)
+    x = np.empty(N)
+    x[0::2], x[1::2] = z.real, z.imag
+    want = np.fft.irfft(X, n=N) * N
+    assert np.linalg.norm(x - want) / np.linalg.norm(want) <= 1e-6
