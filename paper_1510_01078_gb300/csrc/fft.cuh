@@ -161,6 +161,18 @@ __device__ __forceinline__ void c2r_pair(float2 xk, float2 xm, int k, int N, con
     zm = cadd(cconj(E), mul_i(cconj(O), +1));
 }
 
+// Real-to-complex transform of length N through the half-length complex
+// transform (H = N/2): with z[p] = x[2p] + i x[2p+1] and Z = FFT_H(z),
+// X[k] = E + exp(-2 pi i k / N) O, E = (Z[k] + conj Z[H-k]) / 2,
+// O = (Z[k] - conj Z[H-k]) / (2i), indices of Z mod H, for k = 0..H.
+// zk = Z[k mod H], zh = Z[(H-k) mod H].
+__device__ __forceinline__ float2 r2c_unpack(float2 zk, float2 zh, int k, int N, const float2* __restrict__ tw) {
+    const float2 zm = cconj(zh);
+    const float2 E = cscale(cadd(zk, zm), 0.5f);
+    const float2 O = cscale(mul_i(csub(zk, zm), -1), 0.5f);     // (zk - zm) / (2i)
+    return cadd(E, cmul(twiddle(tw, k & (N - 1), N, -1), O));
+}
+
 // ---------------------------------------------------------------------------
 // In place: every thread keeps its share of a pass in registers, so one
 // buffer holds the data throughout; the caller guarantees

@@ -51,11 +51,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_img_xr2c_adj(Geo G, int C, con
     for (int it = threadIdx.x; it < (H + 1) * C; it += NT) {
         const int k = it >> lc;
         const int c = it & (C - 1);
-        const float2 zk = A[padx(((k & (H - 1)) << lc) + c)];
-        const float2 zm = cconj(A[padx((((H - k) & (H - 1)) << lc) + c)]);
-        const float2 E = cscale(cadd(zk, zm), 0.5f);
-        const float2 O = cscale(mul_i(csub(zk, zm), -1), 0.5f);     // (zk - zm) / (2i)
-        float2 X = cadd(E, cmul(twiddle(tw, k & (G.nx - 1), G.nx, -1), O));
+        float2 X = r2c_unpack(A[padx(((k & (H - 1)) << lc) + c)], A[padx((((H - k) & (H - 1)) << lc) + c)], k,
+                              G.nx, tw);
         if (k != 0 && k != H) X = cscale(X, 2.f);
         dst[k * kstride + c] = X;
     }

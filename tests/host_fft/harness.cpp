@@ -93,3 +93,19 @@ extern "C" int host_c2r_pairs(int N, const float* X, float* out) {
     }
     return 0;
 }
+
+// The real-to-complex unpack (r2c_unpack): Z is FFT_{N/2} of the packed real
+// samples (interleaved complex); out is X[0..N/2] (interleaved).
+extern "C" int host_r2c_unpack(int N, const float* Z, float* out) {
+    if (N < 4 || N > TW_N || (N & (N - 1))) return -1;
+    static const std::vector<float2> tw = twiddles();
+    const int H = N / 2;
+    for (int k = 0; k <= H; ++k) {
+        const int a = k & (H - 1), b = (H - k) & (H - 1);
+        const float2 X = r2c_unpack(make_float2(Z[2 * a], Z[2 * a + 1]), make_float2(Z[2 * b], Z[2 * b + 1]), k, N,
+                                    tw.data());
+        out[2 * k] = X.x;
+        out[2 * k + 1] = X.y;
+    }
+    return 0;
+}

@@ -136,3 +136,21 @@ def test_complex_to_real_pairs(lib, N):
     x[0::2], x[1::2] = z.real, z.imag
     want = np.fft.irfft(X, n=N) * N
     assert np.linalg.norm(x - want) / np.linalg.norm(want) <= 1e-6
+
+
+@pytest.mark.parametrize("N", [4, 8, 16, 256, 512, 4096])
+def test_real_to_complex_unpack(lib, N):
+    """r2c_unpack (the transposed x stage): from Z = FFT_{N/2} of the packed real
+    samples z[p] = x[2p] + i x[2p+1], X[0..N/2] equals numpy's rfft(x)."""
+    F = ctypes.POINTER(ctypes.c_float)
+    lib.host_r2c_unpack.argtypes = [ctypes.c_int, F, F]
+    rng = np.random.default_rng(N + 1)
+    x = rng.standard_normal(N)
+    Z = np.fft.fft(x[0::2] + 1j * x[1::2])
+    Zi = np.empty((N // 2, 2), np.float32)
+    Zi[:, 0], Zi[:, 1] = Z.real, Z.imag
+    out = np.empty((N // 2 + 1, 2), np.float32)
+    assert lib.host_r2c_unpack(N, Zi.ctypes.data_as(F), out.ctypes.data_as(F)) == 0
+    want = np.fft.rfft(x)
+    got = out[:, 0] + 1j * out[:, 1]
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-6
