@@ -111,17 +111,27 @@ def algorithmic_bytes(cfg):
             "img_xc2r": V + p0}
 
 
+def sources_sha(sources) -> str:
+    """SHA-256 (16 hex digits) of the kernel's source files, in order."""
+    if isinstance(sources, str):
+        sources = [sources]
+    h = hashlib.sha256()
+    for name in sources:
+        with open(os.path.join(ROOT, "paper_1510_01078_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(kernel: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source."""
+    was taken on the current kernel sources (every file the kernel is built
+    from: its .cu file and the headers holding its device code)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         ent = d.get(kernel)
-        src = os.path.join(ROOT, "paper_1510_01078_gb300", "csrc", ent["source"])
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return float(ent["bytes_per_launch"]) if sha == ent["source_sha"] else None
+        return float(ent["bytes_per_launch"]) if sources_sha(ent["source"]) == ent["source_sha"] else None
     except Exception:
         return None
 
