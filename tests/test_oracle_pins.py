@@ -283,3 +283,55 @@ def test_line_spectrum_matches_spectrum():
     S = oracle.line_spectrum(pr, case["g"], jx, jy, ls)
     for i in range(3):
         np.testing.assert_allclose(S[i], F[jx[i] + 3, jy[i] + 4], atol=1e-12)
+
+
+# band mask and sparse time samples -------------------------------------------
+def test_band_mask_keeps_the_half_open_band():
+    """The band mask keeps nu in the half-open band [-Nt/2, Nt/2) of G_Ky
+    (Sec. 2).  On the j = 0 line with Z = c Nt dt, nu = l exactly; with
+    nz = 4 Nt some l lie outside the band.  The masked coefficient must be
+    zero exactly for l >= Nt/2 and l < -Nt/2, keep the tie l = -Nt/2, and
+    equal the unmasked coefficient everywhere else."""
+    Nt, nz = 16, 64
+    pr = _grid_problem(4, 4, nz, Nt)
+    pm = _grid_problem(4, 4, nz, Nt)
+    pm.band_mask = True
+    l = oracle.index_set(nz)
+    np.testing.assert_allclose(oracle.nu(pr, 0, 0, l), l, rtol=0, atol=1e-12)
+    c0 = oracle.coef(pr, np.zeros_like(l), np.zeros_like(l), l)
+    cm = oracle.coef(pm, np.zeros_like(l), np.zeros_like(l), l)
+    outside = (l >= Nt // 2) | (l < -(Nt // 2))
+    assert outside.sum() == nz - Nt
+    assert np.all(cm[outside] == 0.0)
+    np.testing.assert_array_equal(cm[~outside], c0[~outside])
+    assert cm[l == -(Nt // 2)][0] == c0[l == -(Nt // 2)][0] and c0[l == -(Nt // 2)][0] != 0.0
+    assert cm[l == Nt // 2 - 1][0] != 0.0 and cm[l == Nt // 2][0] == 0.0
+    # off the axis the band edge moves to smaller |l|: with jx = 2 on a grid of
+    # X = 4 dx and Z = c Nt dt, nu^2 = l^2 + (2 Z / X)^2, so the kept set is
+    # l^2 < (Nt/2)^2 - (2 Z / X)^2 (no ties there); W(j != 0, 0) = 0 besides
+    lat = 2.0 * pr.Z / pr.X
+    keep = l.astype(float) ** 2 < (Nt / 2) ** 2 - lat ** 2
+    assert 0 < keep.sum() < Nt
+    c2 = oracle.coef(pm, np.full_like(l, 2), np.zeros_like(l), l)
+    np.testing.assert_array_equal(c2 != 0.0, keep & (l != 0))
+
+
+def test_sparse_time_samples_equal_dense_zero_filled():
+    """The ``ns`` path (data non-zero only at the listed time samples, passed
+    as len(ns) columns) gives the same reconstruction as the dense data with
+    zeros elsewhere.  ns is unsorted and contains both 0 and Nt - 1."""
+    case = inputs.small_case(8, 8, 16, 29, 32, seed=21, layout="disc")
+    pr = _problem(case)
+    rng = np.random.default_rng(22)
+    ns = np.array([17, 0, 31, 5, 22])
+    gs = rng.standard_normal((pr.M, len(ns)))
+    g = np.zeros((pr.M, pr.Nt))
+    g[:, ns] = gs
+    dense = oracle.forward(pr, g)
+    sparse = oracle.forward(pr, gs, ns=ns)
+    assert np.abs(dense).max() > 1e-3
+    np.testing.assert_allclose(sparse, dense, rtol=0, atol=1e-12 * np.abs(dense).max())
+    # and at the spectrum level, with the band mask on
+    pm = _problem(case, band_mask=True)
+    np.testing.assert_allclose(oracle.spectrum(pm, gs, ns=ns), oracle.spectrum(pm, g), rtol=0,
+                               atol=1e-12 * np.abs(oracle.spectrum(pm, g)).max())
