@@ -57,7 +57,7 @@ typedef enum {
     NEDNER_ERANGE = 2,  /* a sensor outside the open aperture (-X/2, X/2) x (-Y/2, Y/2) */
     NEDNER_ENOMEM = 3,  /* host or device allocation failed, or workspace above the limit */
     NEDNER_ECUDA = 4,   /* a CUDA call failed (no device, launch error, ...) */
-    NEDNER_ENAN = 5     /* reserved: non-finite input detected */
+    NEDNER_ENAN = 5     /* non-finite values reached an output (see nedner_device_status) */
 } nedner_status;
 
 typedef struct {
@@ -184,6 +184,22 @@ nedner_status nedner_forward_profiled(nedner_plan_t plan, const float* g, float*
                                       float* stage_ms);
 
 /*
+ * nedner_adjoint and nedner_grad_positions with per-stage timing, for
+ * measurement: CUDA events on `stream` between the launches; waits for the
+ * stream and writes each stage's device time in milliseconds to stage_ms
+ * (host array of NEDNER_TRANSPOSED_KERNELS floats): transposed x
+ * complex-to-real, transposed y-IFFT, transposed NER, transposed y-FFT, the
+ * transposed interpolation (gather, summed over its passes of time samples)
+ * and the per-sensor sum of its entries.  Synchronous.  Same arguments and
+ * errors as the unprofiled calls otherwise.
+ */
+#define NEDNER_TRANSPOSED_KERNELS 6
+nedner_status nedner_adjoint_profiled(nedner_plan_t plan, const float* p0, float* g, void* stream,
+                                      float* stage_ms);
+nedner_status nedner_grad_positions_profiled(nedner_plan_t plan, const float* g, const float* dL_dp0,
+                                             float* dL_dxy, void* stream, float* stage_ms);
+
+/*
  * nedner_ned_stage without touching the plan's workspace and without any
  * device allocation: the same two kernels, with their intermediate array
  * ([nx/2+1][2 ny][Nt] complex64) in a fixed buffer of
@@ -200,6 +216,11 @@ nedner_status nedner_forward_profiled(nedner_plan_t plan, const float* g, float*
  * beforehand and passed in; inputs and outputs are the caller's, as in
  * nedner_ned_stage.
  *
+ *   Arguments: as nedner_ned_stage; g and Ghat 16-byte aligned, else
+ *          NEDNER_EINVAL before anything is launched.  Plans built with the
+ *          tensor-core precision modes are refused with NEDNER_EINVAL (their
+ *          stage (a) needs the plan's own operand buffers; their geometry,
+ *          128 x 128 sensors on a 256 x 256 grid, would not fit the limit).
  *   Limit: (nx/2+1) * 2 ny * Nt * 8 bytes must not exceed
  *          NEDNER_STATIC_SCRATCH_BYTES (16 MiB), else NEDNER_ENOMEM and
  *          nothing is launched.
@@ -207,7 +228,10 @@ nedner_status nedner_forward_profiled(nedner_plan_t plan, const float* g, float*
  *          16 MiB buffer until the process exits.
  *   Set-up: the first call on a device looks up the buffer's device address
  *          (cudaGetSymbolAddress, with that device current) and caches it;
- *          make that first call before any stream capture.
+ *          make that first call before any stream capture.  Calls on a stream
+ *          that is not being captured look the address up again, so after a
+ *          cudaDeviceReset the next such call refreshes it; a call on a
+ *          capturing stream with no cached address returns NEDNER_ECUDA.
  *   Sharing: all calls share the one buffer, which keeps the previous call's
  *          contents (the first kernel overwrites all of it before use, so no
  *          clearing is needed).  Calls that overlap on the GPU -- on several
@@ -218,15 +242,23 @@ nedner_status nedner_forward_profiled(nedner_plan_t plan, const float* g, float*
 nedner_status nedner_ned_stage_static(nedner_plan_t plan, const float* g, void* Ghat, void* stream);
 
 /*
- * Device-side status of the plan's tensor-core kernels (NEDNER_NED_TENSOR_BF16).
- * Those kernels bound every wait on an mbarrier (bulk copies, MMA
- * completion); when one runs out the kernel sets a flag and returns early,
- * leaving its output incomplete, instead of hanging.  Waits for the device,
- * stores 1 in *flags if such a wait ran out since the last call (0 otherwise,
- * and always 0 for plans without the tensor-core stage) and clears the flag.
- * Synchronous.  Returns NEDNER_EINVAL for a null argument, NEDNER_ECUDA if
- * the device reports an error.
+ * Device-side status of the plan's kernels since the previous call, read
+ * back and cleared.  Waits for the device (synchronous).  *flags gets:
+ *   NEDNER_STATUS_WAIT_TIMEOUT  a bounded wait of the tensor-core kernels
+ *       (precision modes with GEMMs) ran out: those kernels bound every wait
+ *       on an mbarrier (bulk copies, MMA completion), and when one runs out
+ *       the kernel sets this flag and returns early, leaving its output
+ *       incomplete, instead of hanging;
+ *   NEDNER_STATUS_NONFINITE  an output kernel (the last stage of
+ *       nedner_forward / nedner_forward_host, nedner_adjoint or
+ *       nedner_grad_positions) wrote a NaN or an infinity.  Every input value
+ *       reaches every output value through the transforms, so a non-finite
+ *       value in g (or p0, dL_dp0) marks the whole result; so does overflow.
+ * Returns NEDNER_ENAN when NEDNER_STATUS_NONFINITE is set, otherwise
+ * NEDNER_OK; NEDNER_EINVAL for a null argument, NEDNER_ECUDA if the device
+ * reports an error.  (Sec. 2 assumes finite data; the paper has no such check.)
  */
+enum { NEDNER_STATUS_WAIT_TIMEOUT = 1, NEDNER_STATUS_NONFINITE = 2 };
 nedner_status nedner_device_status(nedner_plan_t plan, int* flags);
 
 /* Bytes of device workspace held by the plan. */

@@ -11,6 +11,9 @@
 
 namespace nedner {
 
+// bits of the device status word (DevTables::status)
+constexpr int NEDNER_FLAG_NONFINITE = 2;
+
 // Geometry and constants passed by value to every kernel.
 struct Geo {
     int M, Nt, nx, ny, nz;
@@ -86,7 +89,14 @@ struct DevTables {
     int* xent_rc = nullptr;       // [E'] the entry's index in the row CSR
     int* sens_ent = nullptr;      // [M][w] row-CSR index of each of the sensor's y taps
     int4* seg = nullptr;          // [Ly][groups1] column range [x, y) and entry range [z, w)
+    int* status = nullptr;        // device flags: NEDNER_FLAG_NONFINITE when an output kernel wrote a non-finite value
 };
+
+// Stage timer of the profiled entry points (defined in nedner_api.cu): marks
+// the stream after a launch, attributing the time since the previous mark to
+// the named stage.
+struct StageTimer;
+void stage_mark(StageTimer* tm, int stage);
 
 // Tensor-product NED state (tcgen05 GEMM path).
 struct TPState {
@@ -147,9 +157,12 @@ cudaError_t launch_img_xr2c_adj(const nedner_plan_s& p, const float* p0, float2*
 cudaError_t launch_img_yfft_adj(const nedner_plan_s& p, const float2* Y, float2* V, cudaStream_t s);
 cudaError_t launch_ner_lines_adj(const nedner_plan_s& p, const float2* V, float2* Ghat, cudaStream_t s);
 cudaError_t launch_ned_yfft_adj(const nedner_plan_s& p, const float2* Ghat, float2* R, cudaStream_t s);
-cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E, float* g, cudaStream_t s);
+// the gather and its sum run once per pass of time samples; a timer, if
+// given, is marked after each (stages 4 and 5 of the transposed path)
+cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E, float* g, cudaStream_t s,
+                              StageTimer* tm = nullptr);
 cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const float* g, float2* Qe, float* dxy,
-                               cudaStream_t s);
+                               cudaStream_t s, StageTimer* tm = nullptr);
 cudaError_t configure_adj_kernels(const nedner_plan_s& p);
 
 // tensor-product NED (kernels_tp.cu)

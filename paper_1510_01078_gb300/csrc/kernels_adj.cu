@@ -511,26 +511,30 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_gather_rows2(Geo 
     }
 }
 
-// g[m][nb + t] = sum_k E[sens_ent[m][k]][t], t < Tp: the sensor's w entries (one per y tap)
+// g[m][nb + t] = sum_k E[sens_ent[m][k]][t], t < Tp: the sensor's w entries (one per y tap);
+// a non-finite result sets NEDNER_FLAG_NONFINITE in *status
 __global__ void k_adj_sum(Geo G, int nb, int Tp, const float* __restrict__ E, const int* __restrict__ sens_ent,
-                          float* __restrict__ g) {
+                          float* __restrict__ g, int* __restrict__ status) {
     const size_t total = (size_t)G.M * Tp;
     const int ltp = ilog2(Tp);
+    bool bad = false;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int m = (int)(i >> ltp), t = (int)(i & (Tp - 1));
         float v = 0.f;
         for (int k = 0; k < G.w; ++k) v += E[(size_t)__ldg(&sens_ent[(size_t)m * G.w + k]) * Tp + t];
+        bad |= !isfinite(v);
         g[(size_t)m * G.Nt + nb + t] = v;
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, NEDNER_FLAG_NONFINITE);
 }
 
 // dL/d(x_m, y_m) = sum over the sensor's w entries and the time chunks of Qe
 // (one warp per sensor, lanes over (entry, chunk) pairs, fixed order)
 __global__ void k_grad_sum(Geo G, int nch, const float2* __restrict__ Qe, const int* __restrict__ sens_ent,
-                           float* __restrict__ dxy) {
+                           float* __restrict__ dxy, int* __restrict__ status) {
     const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (m >= G.M) return;
+    if (m >= G.M) return;                       // whole warps: blockDim.x is a multiple of 32
     float sx = 0.f, sy = 0.f;
     for (int i = lane; i < G.w * nch; i += 32) {
         const int k = i / nch, ch = i - k * nch;
@@ -545,6 +549,7 @@ __global__ void k_grad_sum(Geo G, int nch, const float2* __restrict__ Qe, const 
     if (lane == 0) {
         dxy[2 * m] = sx;
         dxy[2 * m + 1] = sy;
+        if (!(isfinite(sx) && isfinite(sy))) atomicOr(status, NEDNER_FLAG_NONFINITE);
     }
 }
 
@@ -632,7 +637,8 @@ cudaError_t launch_ned_yfft_adj(const nedner_plan_s& p, const float2* Ghat, floa
         default: CALL(20); break;       \
     }
 
-cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E, float* g, cudaStream_t s) {
+cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E, float* g, cudaStream_t s,
+                              StageTimer* tm) {
     const Geo& G = p.geo;
     const int C = p.ch.ca, Tp = p.ch.tp_adj;
     const size_t total = (size_t)G.M * Tp;
@@ -659,13 +665,15 @@ cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E,
                                                                       p.t.deconv_x, p.t.tw, E, nullptr)
         NEDNER_GATHER_SWITCH(NEDNER_ADJ)
 #undef NEDNER_ADJ
-        k_adj_sum<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g);
+        stage_mark(tm, 4);
+        k_adj_sum<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g, p.t.status);
+        stage_mark(tm, 5);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const float* g, float2* Qe, float* dxy,
-                               cudaStream_t s) {
+                               cudaStream_t s, StageTimer* tm) {
     const Geo& G = p.geo;
     const int C = p.ch.ca;
     const dim3 grid(G.Ly, G.Nt / C);
@@ -689,7 +697,9 @@ cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const fl
                                                                       p.t.deconv_x, p.t.tw, nullptr, Qe)
     NEDNER_GATHER_SWITCH(NEDNER_GRAD)
 #undef NEDNER_GRAD
-    k_grad_sum<<<(G.M + 7) / 8, 256, 0, s>>>(G, G.Nt / C, Qe, p.t.sens_ent, dxy);
+    stage_mark(tm, 4);
+    k_grad_sum<<<(G.M + 7) / 8, 256, 0, s>>>(G, G.Nt / C, Qe, p.t.sens_ent, dxy, p.t.status);
+    stage_mark(tm, 5);
     return cudaGetLastError();
 }
 

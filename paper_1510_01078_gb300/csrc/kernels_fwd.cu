@@ -450,10 +450,13 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_img_yifft(Geo G, int C, const 
 // z = IFFT_H(Z), p0[2p] = Re z[p], p0[2p+1] = Im z[p].
 // The pair (k, H-k) is formed by one thread from one load of each:
 // Z[H-k] = conj E[k] + i conj O[k].  In-place padded FFT, H * C <= 16 NT.
+// A non-finite output value (from non-finite data, which reaches every voxel
+// through the transforms) sets NEDNER_FLAG_NONFINITE in *status.
 // ---------------------------------------------------------------------------
 template <int NT>
 __global__ void __launch_bounds__(NT, 768 / NT) k_img_xc2r(Geo G, int C, int zb, const float2* __restrict__ Y,
-                                                         const float2* __restrict__ tw, float* __restrict__ p0) {
+                                                         const float2* __restrict__ tw, float* __restrict__ p0,
+                                                         int* __restrict__ status) {
     extern __shared__ float4 smem4[];
     const int H = G.nx / 2;
     float2* A = reinterpret_cast<float2*>(smem4);   // [H][C], padded
@@ -473,12 +476,16 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_img_xc2r(Geo G, int C, int zb,
     }
     block_fft_ip<16>(A, H, C, +1, tw);
     float2* dst = reinterpret_cast<float2*>(p0 + ((size_t)qz * G.ny + y0) * G.nx);
+    bool bad = false;
 #pragma unroll 4
     for (int it = threadIdx.x; it < H * C; it += NT) {
         const int c = it >> lh;
         const int pp = it & (H - 1);
-        dst[it] = A[padx(pp * C + c)];
+        const float2 v = A[padx(pp * C + c)];
+        bad |= !(isfinite(v.x) && isfinite(v.y));
+        dst[it] = v;
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, NEDNER_FLAG_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------
@@ -587,7 +594,7 @@ cudaError_t launch_img_xc2r(const nedner_plan_s& p, const float2* Y, float* p0, 
     const Geo& G = p.geo;
     if (nzc < 0) nzc = G.nz - z0;
     dim3 grid(nzc, G.ny / p.ch.c5);
-    k_img_xc2r<128><<<grid, 128, p.ch.smem5, s>>>(G, p.ch.c5, z0, Y, p.t.tw, p0);
+    k_img_xc2r<128><<<grid, 128, p.ch.smem5, s>>>(G, p.ch.c5, z0, Y, p.t.tw, p0, p.t.status);
     return cudaGetLastError();
 }
 

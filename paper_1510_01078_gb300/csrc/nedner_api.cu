@@ -13,10 +13,48 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "fft.cuh"
 #include "internal.h"
+
+// Stage timer for the profiled entry points: records a CUDA event on the
+// stream after each launch and adds the time since the previous mark to the
+// stage it names (a stage launched several times, e.g. once per pass, sums).
+namespace nedner {
+
+struct StageTimer {
+    cudaStream_t s;
+    std::vector<std::pair<int, cudaEvent_t>> marks;
+    cudaError_t err = cudaSuccess;
+    explicit StageTimer(cudaStream_t st) : s(st) {}
+    void mark(int stage) {
+        cudaEvent_t ev = nullptr;
+        if (err == cudaSuccess) err = cudaEventCreate(&ev);
+        if (err == cudaSuccess) err = cudaEventRecord(ev, s);
+        if (ev) marks.emplace_back(stage, ev);
+    }
+    // waits for the last mark; ms[stage] += elapsed since the previous mark
+    cudaError_t finish(float* ms, int nstages) {
+        for (int k = 0; k < nstages; ++k) ms[k] = 0.f;
+        if (err == cudaSuccess && !marks.empty()) err = cudaEventSynchronize(marks.back().second);
+        for (size_t i = 1; i < marks.size() && err == cudaSuccess; ++i) {
+            float t = 0.f;
+            err = cudaEventElapsedTime(&t, marks[i - 1].second, marks[i].second);
+            if (marks[i].first >= 0 && marks[i].first < nstages) ms[marks[i].first] += t;
+        }
+        for (auto& m : marks) cudaEventDestroy(m.second);
+        marks.clear();
+        return err;
+    }
+};
+
+void stage_mark(StageTimer* tm, int stage) {
+    if (tm) tm->mark(stage);
+}
+
+}  // namespace nedner
 
 using namespace nedner;
 
@@ -164,8 +202,9 @@ nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
 
 void free_tables(DevTables& t) {
     cudaFree(t.tw); cudaFree(t.deconv_x); cudaFree(t.deconv_y); cudaFree(t.deconv_t);
-    cudaFree(t.tapcoef); cudaFree(t.axy);
+    cudaFree(t.tapcoef); cudaFree(t.axy); cudaFree(t.status);
     t.tw = nullptr; t.deconv_x = t.deconv_y = t.deconv_t = t.tapcoef = nullptr; t.axy = nullptr;
+    t.status = nullptr;
     free_sensor_tables(t);
 }
 
@@ -368,6 +407,8 @@ nedner_status build_static_tables(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = upload(&p.t.deconv_t, dt, s);
     if (!e) e = upload(&p.t.tapcoef, cf, s);
     if (!e) e = upload(&p.t.axy, axy, s);
+    if (!e) e = cudaMalloc((void**)&p.t.status, sizeof(int));
+    if (!e) e = cudaMemsetAsync(p.t.status, 0, sizeof(int), s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e == cudaErrorMemoryAllocation) return NEDNER_ENOMEM;
     return e ? NEDNER_ECUDA : NEDNER_OK;
@@ -680,6 +721,56 @@ nedner_status nedner_adjoint(nedner_plan_t p, const float* p0, float* g, void* s
     return run(launch_adj_gather(*p, A, Eb, g, s));
 }
 
+// the transposed path with a stage timer: stages 0-3 are the inverse image
+// transposes, the transposed NER and the transposed y-FFT, 4 the gather and 5
+// its per-sensor sum (both summed over the passes of time samples)
+static cudaError_t transposed_to_R_timed(nedner_plan_t p, const float* p0, cudaStream_t s, StageTimer& tm) {
+    float2* A = (float2*)p->ws;
+    float2* B = (float2*)((char*)p->ws + p->region_a);
+    cudaError_t e;
+    tm.mark(-1);
+    if ((e = launch_img_xr2c_adj(*p, p0, B, s))) return e;
+    tm.mark(0);
+    if ((e = launch_img_yfft_adj(*p, B, A, s))) return e;
+    tm.mark(1);
+    if ((e = launch_ner_lines_adj(*p, A, B, s))) return e;
+    tm.mark(2);
+    if ((e = launch_ned_yfft_adj(*p, B, A, s))) return e;
+    tm.mark(3);
+    return tm.err;
+}
+
+nedner_status nedner_adjoint_profiled(nedner_plan_t p, const float* p0, float* g, void* stream, float* stage_ms) {
+    if (!p || !p0 || !stage_ms || (p->M > 0 && !g)) return NEDNER_EINVAL;
+    if (((uintptr_t)p0 & 7) != 0) return NEDNER_EINVAL;
+    for (int k = 0; k < NEDNER_TRANSPOSED_KERNELS; ++k) stage_ms[k] = 0.f;
+    if (p->M == 0) return NEDNER_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    StageTimer tm(s);
+    cudaError_t e = transposed_to_R_timed(p, p0, s, tm);
+    float2* A = (float2*)p->ws;
+    float* Eb = (float*)((char*)p->ws + p->region_a);
+    if (!e) e = launch_adj_gather(*p, A, Eb, g, s, &tm);
+    cudaError_t f = tm.finish(stage_ms, NEDNER_TRANSPOSED_KERNELS);
+    return run(e ? e : f);
+}
+
+nedner_status nedner_grad_positions_profiled(nedner_plan_t p, const float* g, const float* dL_dp0, float* dL_dxy,
+                                             void* stream, float* stage_ms) {
+    if (!p || !dL_dp0 || !stage_ms || (p->M > 0 && (!g || !dL_dxy))) return NEDNER_EINVAL;
+    if (((uintptr_t)dL_dp0 & 7) != 0) return NEDNER_EINVAL;
+    for (int k = 0; k < NEDNER_TRANSPOSED_KERNELS; ++k) stage_ms[k] = 0.f;
+    if (p->M == 0) return NEDNER_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    StageTimer tm(s);
+    cudaError_t e = transposed_to_R_timed(p, dL_dp0, s, tm);
+    float2* A = (float2*)p->ws;
+    float2* Q = (float2*)((char*)p->ws + p->region_a);
+    if (!e) e = launch_grad_gather(*p, A, g, Q, dL_dxy, s, &tm);
+    cudaError_t f = tm.finish(stage_ms, NEDNER_TRANSPOSED_KERNELS);
+    return run(e ? e : f);
+}
+
 nedner_status nedner_grad_positions(nedner_plan_t p, const float* g, const float* dL_dp0, float* dL_dxy,
                                     void* stream) {
     if (!p || !dL_dp0 || (p->M > 0 && (!g || !dL_dxy))) return NEDNER_EINVAL;
@@ -696,14 +787,19 @@ nedner_status nedner_grad_positions(nedner_plan_t p, const float* g, const float
 nedner_status nedner_device_status(nedner_plan_t p, int* flags) {
     if (!p || !flags) return NEDNER_EINVAL;
     *flags = 0;
-    if (!p->tp.err) return NEDNER_OK;
     if (cudaSetDevice(p->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return NEDNER_ECUDA;
-    int f = 0;
     const int zero = 0;
-    if (cudaMemcpy(&f, p->tp.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NEDNER_ECUDA;
-    if (cudaMemcpy(p->tp.err, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return NEDNER_ECUDA;
-    *flags = f ? 1 : 0;
-    return NEDNER_OK;
+    int f = 0, st = 0;
+    if (p->tp.err) {
+        if (cudaMemcpy(&f, p->tp.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NEDNER_ECUDA;
+        if (cudaMemcpy(p->tp.err, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return NEDNER_ECUDA;
+    }
+    if (p->t.status) {
+        if (cudaMemcpy(&st, p->t.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NEDNER_ECUDA;
+        if (cudaMemcpy(p->t.status, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return NEDNER_ECUDA;
+    }
+    *flags = (f ? NEDNER_STATUS_WAIT_TIMEOUT : 0) | ((st & NEDNER_FLAG_NONFINITE) ? NEDNER_STATUS_NONFINITE : 0);
+    return (*flags & NEDNER_STATUS_NONFINITE) ? NEDNER_ENAN : NEDNER_OK;
 }
 
 size_t nedner_workspace_bytes(nedner_plan_t p) { return p ? p->ws_bytes : 0; }

@@ -59,6 +59,8 @@ SIGNATURES = {
     "nedner_grad_positions": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nedner_ned_stage": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_forward_profiled": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
+    "nedner_adjoint_profiled": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
+    "nedner_grad_positions_profiled": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
     "nedner_ned_stage_static": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_workspace_bytes": (ctypes.c_size_t, [_P]),
     "nedner_work_split": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -163,10 +165,17 @@ class Plan:
         except Exception:
             pass
 
+    STATUS_WAIT_TIMEOUT, STATUS_NONFINITE = 1, 2
+
     def device_status(self) -> int:
-        """Flags of kernels whose bounded waits ran out since the last call (0 = none); synchronous."""
+        """Device flags since the last call, read back and cleared (synchronous):
+        STATUS_WAIT_TIMEOUT (a bounded wait of the tensor-core kernels ran out),
+        STATUS_NONFINITE (an output kernel wrote a NaN or an infinity; the C call
+        then returns NEDNER_ENAN, which is reported here as the flag)."""
         f = ctypes.c_int(0)
-        _check(_load().nedner_device_status(self._handle, ctypes.byref(f)), "nedner_device_status")
+        st = _load().nedner_device_status(self._handle, ctypes.byref(f))
+        if st != ENAN:
+            _check(st, "nedner_device_status")
         return int(f.value)
 
     @property
@@ -216,6 +225,30 @@ class Plan:
                                              _stream_ptr(stream), ms)
         _check(st, "nedner_forward_profiled")
         return dict(zip(self.FORWARD_KERNELS, [float(v) for v in ms]))
+
+    TRANSPOSED_KERNELS = ("img_xr2c_adj", "img_yfft_adj", "ner_lines_adj", "ned_yfft_adj", "gather", "entry_sum")
+
+    def adjoint_profiled(self, p0, out, stream=None):
+        """adjoint() that also returns each stage's device time (ms), synchronously."""
+        import torch
+        ms = (ctypes.c_float * len(self.TRANSPOSED_KERNELS))()
+        st = _load().nedner_adjoint_profiled(self._handle,
+                                             _dev_ptr(p0, torch.float32, (self.nz, self.ny, self.nx), "p0"),
+                                             _dev_ptr(out, torch.float32, (self.M, self.Nt), "g"),
+                                             _stream_ptr(stream), ms)
+        _check(st, "nedner_adjoint_profiled")
+        return dict(zip(self.TRANSPOSED_KERNELS, [float(v) for v in ms]))
+
+    def grad_positions_profiled(self, g, dL_dp0, out, stream=None):
+        """grad_positions() that also returns each stage's device time (ms), synchronously."""
+        import torch
+        ms = (ctypes.c_float * len(self.TRANSPOSED_KERNELS))()
+        st = _load().nedner_grad_positions_profiled(
+            self._handle, _dev_ptr(g, torch.float32, (self.M, self.Nt), "g"),
+            _dev_ptr(dL_dp0, torch.float32, (self.nz, self.ny, self.nx), "dL_dp0"),
+            _dev_ptr(out, torch.float32, (self.M, 2), "dL_dxy"), _stream_ptr(stream), ms)
+        _check(st, "nedner_grad_positions_profiled")
+        return dict(zip(self.TRANSPOSED_KERNELS, [float(v) for v in ms]))
 
     def adjoint(self, p0, out=None, stream=None):
         """g = R^T p0.  p0: (nz, ny, nx) -> (M, Nt)."""

@@ -59,3 +59,35 @@ def test_static_scratch_rejects_oversized_geometry(nd):
         nd.ned_stage_static(plan, g)
     assert ei.value.status == 3
     plan.close()
+
+
+def test_static_scratch_rejects_bad_output_pointers_before_launch(nd):
+    """A Ghat that is null or not 16-byte aligned is refused on the host with
+    NEDNER_EINVAL; nothing is launched, so the GPU never sees the pointer."""
+    import ctypes
+    case = inputs.small_case(16, 16, 16, 40, 32, seed=33)
+    plan = nd.plan_from_config(case)
+    g = torch.zeros((plan.M, plan.Nt), dtype=torch.float32, device="cuda")
+    out = torch.empty((plan.nx // 2 + 1, plan.ny + 1, plan.Nt + 2), dtype=torch.complex64, device="cuda")
+    lib = nd.library()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    gp = ctypes.c_void_p(g.data_ptr())
+    assert lib.nedner_ned_stage_static(plan._handle, gp, ctypes.c_void_p(out.data_ptr() + 4), s) == nd.EINVAL
+    assert lib.nedner_ned_stage_static(plan._handle, gp, ctypes.c_void_p(out.data_ptr() + 8), s) == nd.EINVAL
+    assert lib.nedner_ned_stage_static(plan._handle, gp, None, s) == nd.EINVAL
+    assert lib.nedner_ned_stage_static(plan._handle, ctypes.c_void_p(g.data_ptr() + 4),
+                                       ctypes.c_void_p(out.data_ptr()), s) == nd.EINVAL
+    torch.cuda.synchronize()
+    plan.close()
+
+
+def test_static_scratch_refuses_tensor_core_plans(nd):
+    """Plans built for the tensor-core stage (a) are refused with NEDNER_EINVAL."""
+    cfg = inputs.make_config(4, with_data=False)
+    cfg = dict(cfg, Nt=128, dt=cfg["dt"] * 16)
+    plan = nd.plan_from_config(cfg, ned_mode="tensor_bf16")
+    g = torch.zeros((plan.M, plan.Nt), dtype=torch.float32, device="cuda")
+    with pytest.raises(nd.NednerError) as ei:
+        nd.ned_stage_static(plan, g)
+    assert ei.value.status == nd.EINVAL
+    plan.close()
