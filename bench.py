@@ -1,14 +1,27 @@
 #!/usr/bin/env python3
-"""Benchmark: reconstructed voxels/s of the NEDNER forward path on GB300.
+"""Benchmark: reconstructed voxels/s of the NEDNER path on GB300.
 
 One step = one full reconstruction p0 = R g (stages a-d: NED-NUFFT, NER-NUFFT,
-Jacobian, inverse 3-D FFT) of one synthetic workload, inputs resident in HBM.
-Default workload: 64 x 64 centre-dense tensor-grid sensors over 20 mm,
-Nt = 512 at 16.7 ns, 128 x 128 x 256 voxels, Kaiser-Bessel w = 12, sigma = 2,
-20 balls + 20 dB noise (seeded).  L2 is flushed (256 MB write) between timed
-steps.  Prints one JSON line.
+Jacobian, inverse 3-D FFT) of one synthetic workload, inputs resident in HBM;
+`value` is voxels/s of that reconstruction.  The same run also times the
+transposed path (nedner_adjoint, R^T) and the sensor-position gradient
+(nedner_grad_positions) per step, so the spread ("NED spread") and the
+interpolation ("transposed gather") kernels both get a roofline figure.
+L2 is flushed (a 256 MB write, outside the timed events) before every timed
+call.  Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2|c3|c1|c4|c5]
+Default workload (paper scale): 16384 scattered centre-dense sensors in a 30 mm
+disc, Nt = 2048 at 8.3 ns, 256 x 256 x 512 voxels, Kaiser-Bessel w = 12,
+sigma = 2, 200 balls + 20 dB noise (seeded).
+
+Accuracy is checked against the FP64 oracle on a seeded sample of the
+spectrum: 1 % of the lateral lines (a product set of jx and jy values, no
+Nyquist index) at every depth frequency.  The GPU's spectrum there is the DFT
+of its p0 (exact: p0 is the real part of an inverse DFT of a Hermitian
+spectrum).  The oracle's time for that sample, scaled to all lines, is the
+cpu_baseline (its work is proportional to the number of lines).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c3|c2|c1|c4|c5]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
 
 With N > 1 (torchrun) every rank reconstructs its own workload (independent
@@ -24,7 +37,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -32,6 +44,7 @@ sys.path.insert(0, ROOT)
 
 CONFIGS = {"c1": 0, "c2": 1, "c3": 2, "c4": 3, "c5": 4}
 METRIC = "recon voxels/s + % HBM roofline (spread/interp) at stated rel-L2 vs FP64 oracle"
+NED_MODES = ("nufft", "tensor_bf16", "tensor_fp16")
 
 
 def describe(cfg) -> str:
@@ -54,7 +67,7 @@ class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, device_index: int):
         self.idx = device_index
@@ -84,7 +97,7 @@ class ClockSampler:
         with open(self.tmp.name) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.tmp.name)
         if not rows:
@@ -93,10 +106,15 @@ class ClockSampler:
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        # samples taken while a kernel was running (utilization above half)
+        busy = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit() and r[9].isdigit() and int(r[9]) >= 50]
+        return {"sm_mhz": statistics.median(busy or sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(busy)}
 
 
+# --------------------------------------------------------------------------
+# algorithmic bytes per launch
+# --------------------------------------------------------------------------
 def algorithmic_bytes(cfg):
     """Minimum HBM bytes per launch of each forward kernel (inputs read once,
     outputs written once; complex64 intermediates on the half lattice)."""
@@ -111,6 +129,34 @@ def algorithmic_bytes(cfg):
             "img_xc2r": V + p0}
 
 
+def algorithmic_bytes_transposed(cfg, grad: bool):
+    """The same for the transposed stages (each forward stage's bytes with
+    input and output swapped).  The gather reads the rebuilt rows R and writes
+    g (adjoint), or reads R and g and writes 2 floats per sensor (gradient);
+    its per-entry intermediate and the per-sensor sum are counted as the
+    sum's bytes (entries read, result written)."""
+    f = algorithmic_bytes(cfg)
+    M, Nt, w = cfg["sensor_xy"].shape[0], cfg["Nt"], 12
+    g = M * Nt * 4
+    R = f["ned_spread_xfft"] - g
+    if grad:
+        nch = Nt // 64
+        gather, esum = R + g + M * w * nch * 8, M * w * nch * 8 + M * 8
+    else:
+        gather, esum = R + M * w * Nt * 4, M * w * Nt * 4 + g
+    return {"img_xr2c_adj": f["img_xc2r"], "img_yfft_adj": f["img_yifft"], "ner_lines_adj": f["ner_lines"],
+            "ned_yfft_adj": f["ned_yfft"], "gather": gather, "entry_sum": esum}
+
+
+def gather_alg_bytes(cfg):
+    """Algorithmic bytes of the transposed interpolation as a whole (read the
+    grid rows R once, write g once): the forward spread's bytes reversed."""
+    return algorithmic_bytes(cfg)["ned_spread_xfft"]
+
+
+# --------------------------------------------------------------------------
+# ncu DRAM traffic recorded under profiles/ (per kernel and workload)
+# --------------------------------------------------------------------------
 def sources_sha(sources) -> str:
     """SHA-256 (16 hex digits) of the kernel's source files, in order."""
     if isinstance(sources, str):
@@ -122,36 +168,91 @@ def sources_sha(sources) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources (every file the kernel is built
-    from: its .cu file and the headers holding its device code)."""
+def traffic_for(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` on `workload` (a config name) from the
+    committed ncu summary, if it was taken on the current kernel sources (its
+    .cu file and the headers holding its device code); else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        ent = d.get(kernel)
-        return float(ent["bytes_per_launch"]) if sources_sha(ent["source"]) == ent["source_sha"] else None
+        for ent in d.get("entries", []):
+            if ent["kernel"] == kernel and ent["workload"] == workload:
+                if sources_sha(ent["source"]) == ent["source_sha"]:
+                    return float(ent["bytes_per_launch"])
+        return None
     except Exception:
         return None
 
 
-def oracle_forward_seconds(cfg, steps: int = 1, want_output: bool = False):
+# --------------------------------------------------------------------------
+# sampled oracle check
+# --------------------------------------------------------------------------
+def sample_lines(cfg, fraction: float, seed: int):
+    """A seeded product set of lateral frequencies (jx, jy), about `fraction`
+    of all nx ny lines, without the Nyquist indices -nx/2, -ny/2."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    nx, ny = cfg["nx"], cfg["ny"]
+    kx = max(1, int(round((fraction * nx * ny) ** 0.5 * (nx / ny) ** 0.5)))
+    ky = max(1, int(round(fraction * nx * ny / kx)))
+    jx = np.sort(rng.choice(np.arange(-(nx // 2) + 1, nx // 2), size=min(kx, nx - 1), replace=False))
+    jy = np.sort(rng.choice(np.arange(-(ny // 2) + 1, ny // 2), size=min(ky, ny - 1), replace=False))
+    return jx, jy
+
+
+def spectrum_of_volume(p0, jx, jy):
+    """F[a, b, l] of the inverse DFT whose real part is p0 (nz, ny, nx), at the
+    lines (jx[a], jy[b]) and every depth index l = -nz/2..nz/2-1 (index l + nz/2):
+    the forward DFT of p0 on those lines (explicit sums along x and y, FFT
+    along z), times the voxel-centring sign (-1)^(jx + jy).  Exact where no
+    index is a Nyquist index and the spectrum is Hermitian."""
+    import numpy as np
+    nz, ny, nx = p0.shape
+    p = np.asarray(p0, dtype=np.float64)
+    ex = np.exp(-2j * np.pi * np.outer(np.arange(nx), jx) / nx)          # (nx, A)
+    ey = np.exp(-2j * np.pi * np.outer(np.arange(ny), jy) / ny)          # (ny, B)
+    a = p.reshape(nz * ny, nx) @ ex                                       # (nz*ny, A)
+    b = np.einsum("zya,yb->zab", a.reshape(nz, ny, len(jx)), ey)         # (nz, A, B)
+    c = np.fft.fft(b, axis=0)                                             # l mod nz
+    c = np.fft.fftshift(c, axes=0)                                        # l + nz/2
+    sign = np.where(((jx[:, None] + jy[None, :]) % 2) == 0, 1.0, -1.0)
+    return np.transpose(c, (1, 2, 0)) * sign[:, :, None]                 # (A, B, nz)
+
+
+def oracle_problem(cfg):
+    import oracle
+    return oracle.Problem(sensor_xy=cfg["sensor_xy"], h=cfg["h"], Nt=cfg["Nt"], dt=cfg["dt"], c=cfg["c"],
+                          nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], dx=cfg["dx"], dy=cfg["dy"], dz=cfg["dz"])
+
+
+def oracle_sample(cfg, fraction: float, seed: int):
+    """The oracle's spectrum on a sample of lines; returns (jx, jy, F, seconds,
+    scale) with scale = all lines / sampled lines."""
     import numpy as np
     import oracle
-    pr = oracle.Problem(sensor_xy=cfg["sensor_xy"], h=cfg["h"], Nt=cfg["Nt"], dt=cfg["dt"], c=cfg["c"],
-                        nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], dx=cfg["dx"], dy=cfg["dy"], dz=cfg["dz"])
-    times = []
-    out = None
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        out = oracle.forward(pr, np.asarray(cfg["g"], dtype=np.float64))
-        times.append(time.perf_counter() - t0)
-    return (times, out) if want_output else times
+    jx, jy = sample_lines(cfg, fraction, seed)
+    pr = oracle_problem(cfg)
+    ls = oracle.index_set(cfg["nz"])
+    t0 = time.perf_counter()
+    F = oracle.spectrum_block(pr, np.asarray(cfg["g"], dtype=np.float64), jx, jy, ls)
+    secs = time.perf_counter() - t0
+    return jx, jy, F, secs, (cfg["nx"] * cfg["ny"]) / float(len(jx) * len(jy))
 
 
+def sampled_errors(p0_gpu, jx, jy, F_orc):
+    """rel-L2 and max-abs (relative to max |F|) of the GPU spectrum on the
+    sampled lines, all depth frequencies but the Nyquist one."""
+    import numpy as np
+    got = spectrum_of_volume(p0_gpu, jx, jy)[:, :, 1:]
+    want = F_orc[:, :, 1:]
+    d = got - want
+    return (float(np.linalg.norm(d) / np.linalg.norm(want)), float(np.abs(d).max() / np.abs(want).max()))
 
 
+# --------------------------------------------------------------------------
+# multi-rank bookkeeping
+# --------------------------------------------------------------------------
 def max_over_ranks(x: float, world: int, device) -> float:
     """The largest x over all ranks: the slowest replica sets the step time."""
     if world <= 1:
@@ -169,36 +270,89 @@ def whole_job_value(voxels: int, world: int, ms_step: float) -> float:
     return voxels * world / (ms_step / 1e3)
 
 
+# --------------------------------------------------------------------------
+# the reference arm: the FP64 oracle on the host cores
+# --------------------------------------------------------------------------
 def run_reference(args, cfg, voxels, rank, world):
     if rank != 0:
         return
     import oracle
     oracle.build()
     cores = os.cpu_count()
-    for _ in range(args.warmup):
-        oracle_forward_seconds(cfg, 1)
-    times = oracle_forward_seconds(cfg, args.steps)
-    sec = sum(times) / len(times)
+    frac = args.reference_fraction
+    for w in range(args.warmup):
+        oracle_sample(cfg, frac, 9000 + w)
+    secs = []
+    lines = 0
+    for k in range(args.steps):
+        jx, jy, _, t, scale = oracle_sample(cfg, frac, 1000 + k)
+        secs.append(t * scale)                 # one full reconstruction, extrapolated from the sample
+        lines = len(jx) * len(jy)
+    sec = sum(secs) / len(secs)
     value = voxels / sec
+    sample = ("per step a seeded sample of %d of %d lateral lines (%.2f %%) at all %d depth frequencies "
+              "(FP64 direct NED and NER sums, OpenMP); time scaled by lines to one full reconstruction"
+              % (lines, cfg["nx"] * cfg["ny"], 100.0 * lines / (cfg["nx"] * cfg["ny"]), cfg["nz"]))
     line = {"metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded balls + noise)",
             "config": {"workload": describe(cfg), "l2": "n/a (host)"}, "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cores, "kind": "oracle",
-                             "sample": "one full FP64 oracle reconstruction of the workload per step"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# the GPU arm
+# --------------------------------------------------------------------------
+def transposed_passes(cfg) -> int:
+    """Passes of time samples of the transposed gather (the plan's rule, no
+    workspace limit): its entry buffer of M w floats per sample must fit in
+    max(Ghat, V, 256 MB)."""
+    M, Nt, nx, ny, nz, w = cfg["sensor_xy"].shape[0], cfg["Nt"], cfg["nx"], cfg["ny"], cfg["nz"], 12
+    nxh = nx // 2 + 1
+    cap = max(nxh * (ny + 1) * Nt * 8, nxh * ny * nz * 8, 256 << 20)
+    ca = 64 if (2 * nx <= 512 and Nt >= 64) else None
+    tp = Nt
+    while (ca is None or tp > ca) and tp > 1 and M * w * tp * 4 > cap:
+        tp //= 2
+    return Nt // tp
+
+
+def timed_loop(fn, steps, flush):
+    """Calls fn() `steps` times after an L2 flush each; fn returns a dict of
+    per-kernel device times (ms).  Returns the per-kernel lists."""
+    per = {}
+    for _ in range(steps):
+        flush.fill_(1.0)                       # evict L2 (not timed: outside fn's events)
+        ms = fn()
+        for k, v in ms.items():
+            per.setdefault(k, []).append(v)
+    return per
+
+
+def kernel_table(per, abytes):
+    avg = {k: sum(v) / len(v) for k, v in per.items()}
+    tot = sum(avg.values())
+    return avg, {k: {"ms": round(avg[k], 5), "share": round(avg[k] / tot, 4), "alg_bytes": abytes[k],
+                     "gbs": round(abytes[k] / (avg[k] * 1e-3) / 1e9, 1)} for k in avg}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="nedner", choices=["nedner", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ned-mode", default="nufft", choices=["nufft", "tensor_bf16"],
+    ap.add_argument("--no-transposed", action="store_true", help="time the forward only")
+    ap.add_argument("--oracle-fraction", type=float, default=0.01,
+                    help="fraction of lateral lines of the accuracy check / cpu_baseline sample")
+    ap.add_argument("--reference-fraction", type=float, default=0.001,
+                    help="fraction of lateral lines per step of the reference arm")
+    ap.add_argument("--ned-mode", default="nufft", choices=NED_MODES,
                     help="stage (a) as NUFFT (any layout) or tensor-core GEMMs (128x128 tensor grids)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -236,9 +390,19 @@ def main():
     g = torch.as_tensor(np.asarray(cfg["g"], dtype=np.float32), device=dev).contiguous()
     p0 = torch.empty((cfg["nz"], cfg["ny"], cfg["nx"]), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    do_t = not args.no_transposed
+    if do_t:
+        rng = np.random.default_rng(cfg["seed"] + 99)
+        lam = torch.as_tensor(rng.standard_normal((cfg["nz"], cfg["ny"], cfg["nx"])), dtype=torch.float32,
+                              device=dev)
+        g_adj = torch.empty_like(g)
+        dxy = torch.empty((plan.M, 2), dtype=torch.float32, device=dev)
 
     for _ in range(args.warmup):
         plan.forward(g, out=p0)
+        if do_t:
+            plan.adjoint(lam, out=g_adj)
+            plan.grad_positions(g, lam, out=dxy)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(torch.cuda.current_device())
@@ -246,21 +410,19 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    per_kernel = {k: [] for k in nedner.Plan.FORWARD_KERNELS}
-    step_ms = []
     t_wall = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1.0)                                     # evict L2 between steps (not timed)
-        ms = plan.forward_profiled(g, p0)                    # events around each kernel, same stream
-        for k, v in ms.items():
-            per_kernel[k].append(v)
-        step_ms.append(sum(ms.values()))
+    per_fwd = timed_loop(lambda: plan.forward_profiled(g, p0), args.steps, flush)
+    if do_t:
+        per_adj = timed_loop(lambda: plan.adjoint_profiled(lam, g_adj), args.steps, flush)
+        per_grad = timed_loop(lambda: plan.grad_positions_profiled(g, lam, dxy), args.steps, flush)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
+    status_flags = plan.device_status()
 
+    step_ms = [sum(v) for v in zip(*per_fwd.values())]
     ms_step = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
     value = whole_job_value(voxels, world, ms_step)
 
@@ -268,13 +430,11 @@ def main():
     g_host = torch.as_tensor(np.asarray(cfg["g"], dtype=np.float32)).pin_memory()
     p_host = torch.empty((cfg["nz"], cfg["ny"], cfg["nx"]), dtype=torch.float32).pin_memory()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # nedner_forward_host: the public call with host buffers, uploads and
-    # downloads overlapped with the kernels inside the timed region
     for _ in range(args.warmup):
         plan.forward_host(g_host, out=p_host, stream=stream)
     torch.cuda.synchronize()
     e2e_ms = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, 20)):
         flush.fill_(1.0)
         e0.record(stream)
         plan.forward_host(g_host, out=p_host, stream=stream)
@@ -283,45 +443,87 @@ def main():
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, dev)
 
-    # roofline of the dominant kernel
+    # per-kernel tables and rooflines
+    peak, peak_kind = peaks()
     abytes = algorithmic_bytes(cfg)
-    avg = {k: sum(v) / len(v) for k, v in per_kernel.items()}
     if args.ned_mode != "nufft":
-        # stage (a) is one group of tensor-core kernels, reported under the first name
-        avg = {("tp_ned_gemm" if k == "ned_spread_xfft" else k): v for k, v in avg.items() if k != "ned_yfft"}
+        # stage (a) is one group of tensor-core kernels, reported under one name
+        per_fwd = {("tp_ned_gemm" if k == "ned_spread_xfft" else k): v for k, v in per_fwd.items() if k != "ned_yfft"}
         M, Nt = cfg["sensor_xy"].shape[0], cfg["Nt"]
         abytes = dict(abytes, tp_ned_gemm=M * Nt * 4 + (cfg["nx"] // 2 + 1) * (cfg["ny"] + 1) * Nt * 8)
+    avg, kernels = kernel_table(per_fwd, abytes)
     dom = max(avg, key=avg.get)
-    peak, peak_kind = peaks()
-    kernels = {k: {"ms": round(avg[k], 5), "share": round(avg[k] / sum(avg.values()), 4),
-                   "alg_bytes": abytes[k], "gbs": round(abytes[k] / (avg[k] * 1e-3) / 1e9, 1)} for k in avg}
     achieved = abytes[dom] / (avg[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic_for(dom), "peak_source": peak_kind}
-    # the spread kernel's own fraction (the metric names spread/interp)
+                "frac": round(achieved / peak, 4), "traffic": traffic_for(dom, cfg["name"]),
+                "peak_source": peak_kind + " (burst copy bandwidth)"}
     spread_frac = (round(abytes["ned_spread_xfft"] / (avg["ned_spread_xfft"] * 1e-3) / 1e9 / peak, 4)
                    if "ned_spread_xfft" in avg else None)
 
-    # kernels launched per reconstruction: five for the NUFFT path; the tensor-core
-    # stage a runs prep + two GEMMs per pass of 512 time samples, then the Nyquist line
+    transposed = None
+    interp_roofline = None
+    if do_t:
+        aa, ak = kernel_table(per_adj, algorithmic_bytes_transposed(cfg, False))
+        ga, gk = kernel_table(per_grad, algorithmic_bytes_transposed(cfg, True))
+        adj_ms = max_over_ranks(sum(aa.values()), world, dev)
+        grad_ms = max_over_ranks(sum(ga.values()), world, dev)
+        transposed = {"adjoint": {"ms": round(adj_ms, 4), "voxels_per_s": whole_job_value(voxels, world, adj_ms),
+                                  "kernels": ak},
+                      "grad_positions": {"ms": round(grad_ms, 4),
+                                         "voxels_per_s": whole_job_value(voxels, world, grad_ms), "kernels": gk}}
+        gb = gather_alg_bytes(cfg)
+        gms = aa["gather"] + aa["entry_sum"]
+        interp_roofline = {"bound": "hbm", "kernel": "adjoint gather + entry sum (transposed interpolation)",
+                           "achieved": round(gb / (gms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                           "frac": round(gb / (gms * 1e-3) / 1e9 / peak, 4),
+                           "traffic": traffic_for("gather", cfg["name"]), "peak_source": peak_kind}
+
+    # kernels launched in the timed region: five per reconstruction for the NUFFT
+    # path; the tensor-core stage a runs prep + two GEMMs per pass of 512 time
+    # samples, then the Nyquist line, plus the scale reduction in FP16 mode
     if args.ned_mode == "nufft":
-        launches_per_step = len(nedner.Plan.FORWARD_KERNELS)
+        fwd_launches = len(nedner.Plan.FORWARD_KERNELS)
     else:
-        launches_per_step = 3 * (cfg["Nt"] // min(512, cfg["Nt"])) + 1 + 3
+        fwd_launches = 3 * (cfg["Nt"] // min(512, cfg["Nt"])) + 1 + 3 + (1 if args.ned_mode == "tensor_fp16" else 0)
+    passes = transposed_passes(cfg)
+    t_launches = (4 + 2 * passes) + 6 if do_t else 0
+    launches = (fwd_launches + t_launches) * args.steps
 
     cpu = None
-    accuracy = {"rel_l2_vs_oracle": None, "tolerance": 1e-5 if args.ned_mode == "nufft" else 3e-5}
+    tol = {"nufft": 1e-5, "tensor_bf16": 3e-5, "tensor_fp16": 1e-5}[args.ned_mode]
+    accuracy = {"rel_l2_vs_oracle": None, "max_abs_rel_vs_oracle": None, "tolerance_rel_l2": tol,
+                "check": None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             import oracle
             oracle.build()
-            secs, ref = oracle_forward_seconds(cfg, 1, want_output=True)
-            secs = secs[0]
-            cpu = {"value": voxels / secs, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": "one full FP64 oracle reconstruction of the workload (%.1f s)" % secs}
-            # the accuracy the throughput is quoted at: the timed run's p0 against the oracle's
-            got = p_host.double().numpy()                     # the result of the host-buffer call
-            accuracy["rel_l2_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            got = p_host.double().numpy()                      # the result of the timed host-buffer call
+            if cfg["sensor_xy"].shape[0] * cfg["nx"] * cfg["ny"] * cfg["Nt"] <= 1e11:
+                # small workloads: the whole oracle reconstruction, every voxel
+                pr = oracle_problem(cfg)
+                t0 = time.perf_counter()
+                ref = oracle.forward(pr, np.asarray(cfg["g"], dtype=np.float64))
+                secs = time.perf_counter() - t0
+                accuracy["rel_l2_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+                accuracy["max_abs_rel_vs_oracle"] = float(np.abs(got - ref).max() / np.abs(ref).max())
+                accuracy["check"] = "every voxel against one full FP64 oracle reconstruction"
+                cpu = {"value": voxels / secs, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
+                       "sample": "one full FP64 oracle reconstruction of the workload (%.1f s)" % secs}
+            else:
+                jx, jy, F, secs, scale = oracle_sample(cfg, args.oracle_fraction, cfg["seed"] + 7)
+                rl2, mx = sampled_errors(got, jx, jy, F)
+                accuracy["rel_l2_vs_oracle"] = rl2
+                accuracy["max_abs_rel_vs_oracle"] = mx
+                lines = len(jx) * len(jy)
+                accuracy["check"] = ("spectrum of the timed p0 on a seeded sample of %d of %d lateral lines "
+                                     "(%.2f %%, no Nyquist index) at every depth frequency, against the FP64 "
+                                     "oracle's direct sums there" % (lines, cfg["nx"] * cfg["ny"],
+                                                                    100.0 * lines / (cfg["nx"] * cfg["ny"])))
+                cpu = {"value": voxels / (secs * scale), "unit": "voxels/s", "cores": os.cpu_count(),
+                       "kind": "oracle",
+                       "sample": ("FP64 oracle on %d of %d lateral lines at all %d depth frequencies: %.1f s, "
+                                  "scaled by lines (x%.1f) to one full reconstruction"
+                                  % (lines, cfg["nx"] * cfg["ny"], cfg["nz"], secs, scale))}
         except Exception as ex:  # the baseline is reported, not required
             cpu = {"value": None, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "failed: %s" % ex}
@@ -330,13 +532,14 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded balls + 20 dB noise)",
-                "config": {"workload": describe(cfg), "l2": "flushed between timed steps (256 MB write)",
+                "config": {"workload": describe(cfg), "l2": "flushed before every timed call (256 MB write)",
                            "parallelism": "independent reconstruction per GPU", "ned_mode": args.ned_mode},
-                "roofline": roofline, "spread_frac_of_peak": spread_frac, "accuracy": accuracy, "kernels": kernels,
-                "cpu_baseline": cpu, "clocks": clk,
+                "roofline": roofline, "spread_frac_of_peak": spread_frac, "interp_roofline": interp_roofline,
+                "accuracy": accuracy, "kernels": kernels, "transposed": transposed,
+                "cpu_baseline": cpu, "clocks": clk, "device_status_flags": status_flags,
                 "e2e": {"value": whole_job_value(voxels, world, e2e_step), "unit": "voxels/s",
                         "h2d_bytes_per_step": int(g_host.numel() * 4), "d2h_bytes_per_step": int(p_host.numel() * 4)},
-                "gpu_launches": launches_per_step * args.steps,
+                "gpu_launches": launches,
                 "wall_s_timed_region": round(wall, 3)}
         print(json.dumps(line), flush=True)
     plan.close()

@@ -80,23 +80,28 @@ typedef struct {
                                      limit the transposed entry points work in shorter passes
                                      over the time samples where that lets the plan fit. */
     const double* sensor_w;       /* host [M] detector areas h_m (m^2), or NULL for X Y / M */
-    int ned_mode;                 /* NEDNER_NED_NUFFT (default) or NEDNER_NED_TENSOR_BF16, see below */
+    int precision;                /* NEDNER_PRECISION_* (default FP32 NUFFT), see below */
 } nedner_opts;
 
 /*
- * ned_mode selects how nedner_forward and nedner_ned_stage evaluate stage (a):
- *   NEDNER_NED_NUFFT        the NED-NUFFT of Sec. 3.2 (any sensor layout);
- *   NEDNER_NED_TENSOR_BF16  sensors on a tensor product x_m = xs[a], y_m = ys[b],
- *                           m = b * 128 + a, 128 x 128 of them, output grid
- *                           nx = ny = 256: the NED sum (Eq. NUDFT2 with a separable
- *                           exponent) evaluated exactly as two complex GEMMs per time
- *                           sample on the tensor cores, BF16 operands with a hi + lo
- *                           split of every factor and FP32 accumulation.  Other
- *                           layouts give NEDNER_EINVAL.  The transposed entry points
- *                           (nedner_adjoint, nedner_grad_positions) always use the
- *                           NUFFT formulation.
+ * precision selects the arithmetic of stage (a) in nedner_forward,
+ * nedner_forward_host and nedner_ned_stage (every other stage is FP32):
+ *   NEDNER_PRECISION_FP32_NUFFT  the NED-NUFFT of Sec. 3.2 in FP32 (any sensor layout);
+ *   NEDNER_PRECISION_BF16_GEMM   sensors on a tensor product x_m = xs[a], y_m = ys[b],
+ *                                m = b * 128 + a, 128 x 128 of them, output grid
+ *                                nx = ny = 256: the NED sum (Eq. NUDFT2 with a
+ *                                separable exponent) evaluated exactly as two complex
+ *                                GEMMs per time sample on the tensor cores, BF16
+ *                                operands with a hi + lo split of every factor
+ *                                (hi*hi + lo*hi + hi*lo) and FP32 accumulation;
+ *   NEDNER_PRECISION_FP16_GEMM   the same GEMMs with FP16 hi + lo operands (11
+ *                                significant bits per part), the data scaled by a
+ *                                power of two on the device so that they fit FP16's
+ *                                range (the scale is removed in FP32 afterwards).
+ * The GEMM modes give NEDNER_EINVAL for other layouts.  The transposed entry
+ * points (nedner_adjoint, nedner_grad_positions) always use the FP32 NUFFT.
  */
-enum { NEDNER_NED_NUFFT = 0, NEDNER_NED_TENSOR_BF16 = 1 };
+enum { NEDNER_PRECISION_FP32_NUFFT = 0, NEDNER_PRECISION_BF16_GEMM = 1, NEDNER_PRECISION_FP16_GEMM = 2 };
 
 /*
  * Build a plan (host tables, device tables, device workspace).
@@ -107,7 +112,7 @@ enum { NEDNER_NED_NUFFT = 0, NEDNER_NED_TENSOR_BF16 = 1 };
  *   out_grid   output grid (see nedner_grid).
  *   window     interpolation window of both NUFFTs (Sec. 3.1-3.2).
  *   sigma      oversampling factor (the paper's c > 1); this build supports 2.0.
- *   opts       NULL for defaults {1, 0, 0, NULL, NEDNER_NED_NUFFT}.
+ *   opts       NULL for defaults {1, 0, 0, NULL, NEDNER_PRECISION_FP32_NUFFT}.
  *   stream     stream used for the table uploads (synchronised before return).
  *   out        receives the plan; untouched on error.
  * Returns NEDNER_OK, NEDNER_EINVAL, NEDNER_ERANGE, NEDNER_ENOMEM or NEDNER_ECUDA.
@@ -260,6 +265,18 @@ nedner_status nedner_ned_stage_static(nedner_plan_t plan, const float* g, void* 
  */
 enum { NEDNER_STATUS_WAIT_TIMEOUT = 1, NEDNER_STATUS_NONFINITE = 2 };
 nedner_status nedner_device_status(nedner_plan_t plan, int* flags);
+
+/*
+ * Test hook for the bounded waits of the tensor-core kernels: the pipeline
+ * waits (operand ring, accumulator hand-over) give up after `polls` polls of
+ * their mbarrier (0: at once) instead of the default 2^26; the waits that
+ * drain a CTA's own copies and MMAs before it frees tensor memory keep the
+ * default.  With a small limit a pipeline wait runs out, the kernels set
+ * NEDNER_STATUS_WAIT_TIMEOUT and return with their output incomplete; pass
+ * 1 << 26 to restore.  No effect on plans without the tensor-core stage.
+ * Returns NEDNER_EINVAL for a null plan or negative polls.  No paper counterpart.
+ */
+nedner_status nedner_debug_set_wait_limit(nedner_plan_t plan, int polls);
 
 /* Bytes of device workspace held by the plan. */
 size_t nedner_workspace_bytes(nedner_plan_t plan);

@@ -272,6 +272,21 @@ def line_spectrum(pr: Problem, g: np.ndarray, jx, jy, ls) -> np.ndarray:
     return out
 
 
+def spectrum_block(pr: Problem, g: np.ndarray, jx, jy, ls) -> np.ndarray:
+    """F[a, b, c] at jx[a], jy[b] (every pair: the lines of a product set) and
+    depth frequencies ls[c]: the sums of ``spectrum`` on a subset of lines,
+    one NED call for all of them.  Used for sampled checks where the whole
+    spectrum is too slow; the work is proportional to len(jx) * len(jy)."""
+    jx = np.asarray(jx, dtype=np.int64)
+    jy = np.asarray(jy, dtype=np.int64)
+    ls = np.asarray(ls, dtype=np.int64)
+    G = ned(pr, g, jx, jy)                                   # (len(jx), len(jy), Nt)
+    JX, JY, L = np.meshgrid(jx, jy, ls, indexing="ij")
+    nus = nu(pr, JX, JY, L).reshape(len(jx) * len(jy), len(ls))
+    F = ner(pr, G.reshape(len(jx) * len(jy), pr.Nt), nus)
+    return F.reshape(len(jx), len(jy), len(ls)) * coef(pr, JX, JY, L)
+
+
 def _centre_sign(pr: Problem, JX, JY):
     # exp(2 pi i jx (qx - nx/2)/nx) = (-1)^jx exp(2 pi i jx qx / nx)
     return np.where(((JX + JY) % 2) == 0, 1.0, -1.0)
@@ -292,52 +307,82 @@ def forward(pr: Problem, g: np.ndarray, ns=None) -> np.ndarray:
     return image_from_spectrum(pr, spectrum(pr, g, ns))
 
 
-def _dual_spectrum(pr: Problem, p: np.ndarray, sign: int) -> np.ndarray:
-    """(1/N) sum_q p[q] exp(sign * i theta(k, q)) on G_x x G_Ky, (nx, ny, nz)."""
-    jx, jy, l, JX, JY, L = _grid_indices(pr)
+def _dual_spectrum(pr: Problem, p: np.ndarray, sign: int, JX=None, JY=None, L=None) -> np.ndarray:
+    """(1/N) sum_q p[q] exp(sign * i theta(k, q)) on G_x x G_Ky, (nx, ny, nz)
+    (or on the index arrays JX, JY, L)."""
+    if JX is None:
+        jx, jy, l, JX, JY, L = _grid_indices(pr)
     p = np.asarray(p, dtype=np.float64).reshape(pr.nz, pr.ny, pr.nx)
     N = pr.nx * pr.ny * pr.nz
     A = np.fft.fftn(p) / N if sign < 0 else np.fft.ifftn(p)
     return A[np.mod(L, pr.nz), np.mod(JY, pr.ny), np.mod(JX, pr.nx)] * _centre_sign(pr, JX, JY)
 
 
-def adjoint(pr: Problem, p0: np.ndarray) -> np.ndarray:
+def _line_subset(pr: Problem, jx, jy):
+    """Lateral index sets of the transposed sums: all of G_x, or the product
+    set jx x jy (the spectrum is then taken as zero on every other line)."""
+    if jx is None:
+        return _grid_indices(pr)
+    jx = np.asarray(jx, dtype=np.int64)
+    jy = np.asarray(jy, dtype=np.int64)
+    l = index_set(pr.nz)
+    JX, JY, L = np.meshgrid(jx, jy, l, indexing="ij")
+    return jx, jy, l, JX, JY, L
+
+
+def _sensor_subset(pr: Problem, sensors):
+    xy = np.asarray(pr.sensor_xy, dtype=np.float64)
+    w = pr.sensor_factor()
+    if sensors is not None:
+        sensors = np.asarray(sensors, dtype=np.int64)
+        xy, w = xy[sensors], w[sensors]
+    return np.ascontiguousarray(xy), np.ascontiguousarray(w, dtype=np.float64)
+
+
+def adjoint(pr: Problem, p0: np.ndarray, jx=None, jy=None, sensors=None) -> np.ndarray:
     """R^T p (real transpose of ``forward``):
     g[m, n] = w_m Re sum_{j,l} coef P[j, l] exp(+2 pi i (nu n / Nt + j.x_m)),
-    P[j, l] = (1/N) sum_q p[q] exp(-i theta(j, l; q)).  Returns (M, Nt)."""
-    jx, jy, l, JX, JY, L = _grid_indices(pr)
-    P = _dual_spectrum(pr, p0, -1) * coef(pr, JX, JY, L)
-    nus = nu(pr, JX, JY, L).reshape(pr.nx * pr.ny, pr.nz)
-    T = ner_adj(pr, P.reshape(pr.nx * pr.ny, pr.nz), nus)     # (nx*ny, Nt)
-    T = np.ascontiguousarray(T.reshape(pr.nx, pr.ny, pr.Nt))
-    xy = np.ascontiguousarray(pr.sensor_xy, dtype=np.float64)
-    w = np.ascontiguousarray(pr.sensor_factor(), dtype=np.float64)
+    P[j, l] = (1/N) sum_q p[q] exp(-i theta(j, l; q)).  Returns (M, Nt).
+    With ``jx``, ``jy`` the sum runs over the lines of the product set jx x jy
+    only (exact when the spectrum of p vanishes on the other lines); with
+    ``sensors`` only those rows of g are computed."""
+    jx, jy, l, JX, JY, L = _line_subset(pr, jx, jy)
+    P = _dual_spectrum(pr, p0, -1, JX, JY, L) * coef(pr, JX, JY, L)
+    nl = len(jx) * len(jy)
+    nus = nu(pr, JX, JY, L).reshape(nl, pr.nz)
+    T = ner_adj(pr, P.reshape(nl, pr.nz), nus)                  # (lines, Nt)
+    T = np.ascontiguousarray(T.reshape(len(jx), len(jy), pr.Nt))
+    xy, w = _sensor_subset(pr, sensors)
     jx32 = np.ascontiguousarray(jx, dtype=np.int32)
     jy32 = np.ascontiguousarray(jy, dtype=np.int32)
-    out = np.zeros((pr.M, pr.Nt), dtype=np.float64)
-    rc = _load().orc_ned_adj(pr.M, _p(xy), _p(w), pr.Nt, pr.X, pr.Y, len(jx32), _p(jx32),
+    out = np.zeros((len(w), pr.Nt), dtype=np.float64)
+    rc = _load().orc_ned_adj(len(w), _p(xy), _p(w), pr.Nt, pr.X, pr.Y, len(jx32), _p(jx32),
                              len(jy32), _p(jy32), _p(T), _p(out), _nthreads())
     if rc != 0:
         raise MemoryError("orc_ned_adj: allocation failed")
     return out
 
 
-def grad_positions(pr: Problem, g: np.ndarray, dL_dp0: np.ndarray) -> np.ndarray:
+def grad_positions(pr: Problem, g: np.ndarray, dL_dp0: np.ndarray, jx=None, jy=None, sensors=None) -> np.ndarray:
     """dL/d(x_m, y_m) for p0 = R g with dL/dp0 given; the areas h_m are held
-    fixed.  Differentiates the NED exponent of Eq. disc_rec.  Returns (M, 2)."""
-    jx, jy, l, JX, JY, L = _grid_indices(pr)
-    Lam = _dual_spectrum(pr, dL_dp0, +1) * coef(pr, JX, JY, L)
-    nus = nu(pr, JX, JY, L).reshape(pr.nx * pr.ny, pr.nz)
+    fixed.  Differentiates the NED exponent of Eq. disc_rec.  Returns (M, 2).
+    ``jx``, ``jy`` and ``sensors`` restrict the sums as in ``adjoint``."""
+    jx, jy, l, JX, JY, L = _line_subset(pr, jx, jy)
+    Lam = _dual_spectrum(pr, dL_dp0, +1, JX, JY, L) * coef(pr, JX, JY, L)
+    nl = len(jx) * len(jy)
+    nus = nu(pr, JX, JY, L).reshape(nl, pr.nz)
     # S[j, n] = sum_l coef Lam exp(-2 pi i nu n / Nt)
-    S = np.conj(ner_adj(pr, np.conj(Lam).reshape(pr.nx * pr.ny, pr.nz), nus))
-    S = np.ascontiguousarray(S.reshape(pr.nx, pr.ny, pr.Nt))
-    xy = np.ascontiguousarray(pr.sensor_xy, dtype=np.float64)
-    w = np.ascontiguousarray(pr.sensor_factor(), dtype=np.float64)
-    gg = np.ascontiguousarray(g, dtype=np.float64).reshape(pr.M, pr.Nt)
+    S = np.conj(ner_adj(pr, np.conj(Lam).reshape(nl, pr.nz), nus))
+    S = np.ascontiguousarray(S.reshape(len(jx), len(jy), pr.Nt))
+    xy, w = _sensor_subset(pr, sensors)
+    gg = np.asarray(g, dtype=np.float64).reshape(pr.M, pr.Nt)
+    if sensors is not None:
+        gg = gg[np.asarray(sensors, dtype=np.int64)]
+    gg = np.ascontiguousarray(gg)
     jx32 = np.ascontiguousarray(jx, dtype=np.int32)
     jy32 = np.ascontiguousarray(jy, dtype=np.int32)
-    out = np.zeros((pr.M, 2), dtype=np.float64)
-    rc = _load().orc_ned_grad(pr.M, _p(xy), _p(w), pr.Nt, _p(gg), pr.X, pr.Y, len(jx32),
+    out = np.zeros((len(w), 2), dtype=np.float64)
+    rc = _load().orc_ned_grad(len(w), _p(xy), _p(w), pr.Nt, _p(gg), pr.X, pr.Y, len(jx32),
                               _p(jx32), len(jy32), _p(jy32), _p(S), _p(out), _nthreads())
     if rc != 0:
         raise MemoryError("orc_ned_grad: allocation failed")
@@ -345,5 +390,5 @@ def grad_positions(pr: Problem, g: np.ndarray, dL_dp0: np.ndarray) -> np.ndarray
 
 
 __all__ = ["Problem", "build", "index_set", "nu", "jacobian", "coef", "ned", "ner",
-           "ner_adj", "spectrum", "line_spectrum", "image_from_spectrum", "forward",
+           "ner_adj", "spectrum", "line_spectrum", "spectrum_block", "image_from_spectrum", "forward",
            "adjoint", "grad_positions"]

@@ -109,6 +109,9 @@ struct TPState {
     float2* exn = nullptr;        // device FP32: Ex row jx = nx/2
     float2* eyf = nullptr;        // device FP32: Ey [ny+1][nys]
     int* err = nullptr;           // device flag: a bounded wait ran out
+    int fp16 = 0;                 // operands FP16 (else BF16)
+    int wait_limit = 1 << 26;     // polls of the pipeline waits (nedner_debug_set_wait_limit); drains keep 1 << 26
+    unsigned int* absmax = nullptr;   // device word: bits of max |w_m g| (FP16 mode's data scale)
 };
 
 }  // namespace nedner
@@ -170,5 +173,6 @@ cudaError_t configure_tp_kernels();
 cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, cudaStream_t s);
 size_t tp_work_bytes(int Nt);
 constexpr int TP_SENSORS = 128;   // sensors per axis the tensor-core path is built for
+constexpr int TP_WAIT_LIMIT = 1 << 26;   // polls of a bounded mbarrier wait
 
 }  // namespace nedner

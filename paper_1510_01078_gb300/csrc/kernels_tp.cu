@@ -11,10 +11,14 @@
 //   GEMM 1 (per n):       D[jx, b] = sum_a Ex[jx, a] A[b, a, n]     M = jx, N = b, K = a
 //   GEMM 2 (per jx):      G[jy, n] = sum_b D[jx, b, n] Ey[jy, b]    M = n, N = jy, K = b
 // GEMM 2 takes n as its M dimension so that every output column jy is a run
-// of contiguous time samples of Ghat.  Operands are BF16 with a hi + lo split of
-// every real factor (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)); each real
-// product is formed as hi*hi + lo*hi + hi*lo with FP32 accumulation in tensor
-// memory.  Shapes handled: nxs = nys = 128 sensors per axis, nx = ny = 256
+// of contiguous time samples of Ghat.  Operands are BF16 or FP16 (the two
+// precision modes) with a hi + lo split of every real factor (x = hi + lo,
+// hi = round(x), lo = round(x - hi)); each real product is formed as
+// hi*hi + lo*hi + hi*lo with FP32 accumulation in tensor memory.  FP16 keeps
+// 11 significant bits per part against BF16's 8 but has a narrow exponent
+// range, so in FP16 mode the data are first scaled by a power of two s (from
+// the largest |w_m g[m, n]|, k_tp_absmax) that puts them in [2^7, 2^8) at most,
+// which keeps D = sum_a Ex A below 2^15; the epilogues multiply by 1/s.  Shapes handled: nxs = nys = 128 sensors per axis, nx = ny = 256
 // output grid: jx = 0..127 as GEMM tiles of 128 rows, jy in two M tiles
 // (-128..-1 and 0..127); the row jy = +128 is summed in FP32 in GEMM 1's
 // epilogue and the line jx = 128 on the CUDA cores (k_tp_prep, k_tp_nyq_g).
@@ -28,6 +32,7 @@
 // bytes; 128 bytes between core matrices along K, 1024 bytes between 8-row
 // groups).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -47,7 +52,7 @@ constexpr int KA = 32;                              // K chunk of the GEMM 2 D t
 constexpr uint32_t DT_BLK = TM * KA * 2;            // 8 KB: one matrix of a D tile, one K chunk
 constexpr uint32_t DT_STAGE = 4 * DT_BLK;           // Re hi, Re lo, Im hi, Im lo of one K chunk
 constexpr int STAGES = 3;                           // operand ring of both GEMMs
-constexpr int WAIT_LIMIT = 1 << 26;    // iterations of a bounded mbarrier wait
+constexpr int WAIT_LIMIT = TP_WAIT_LIMIT;   // polls of a bounded mbarrier wait (drains; pipeline default)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -66,9 +71,40 @@ __device__ __forceinline__ uint64_t sdesc_sbo(uint32_t saddr, uint32_t sbo) {
 // the same for K chunks of 64 (8-row groups 1024 B apart)
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) { return sdesc_sbo(saddr, 1024); }
 
-// instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = n
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// instruction descriptor: kind::f16, D = F32, A = B = BF16 (ab = 1) or FP16
+// (ab = 0), both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_f16kind(int n, uint32_t ab) {
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// the two operand types: the A/B type field of the instruction descriptor and
+// the hi + lo split of an FP32 value
+template <typename T> struct Op;
+template <> struct Op<__nv_bfloat16> {
+    static constexpr uint32_t ab = 1;
+    static __device__ __forceinline__ void split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+        hi = __float2bfloat16_rn(x);
+        lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+};
+template <> struct Op<__half> {
+    static constexpr uint32_t ab = 0;
+    static __device__ __forceinline__ void split(float x, __half& hi, __half& lo) {
+        hi = __float2half_rn(x);
+        lo = __float2half_rn(x - __half2float(hi));
+    }
+};
+
+// data scale of the FP16 mode from the largest |w_m g[m, n]| (its bits in
+// *absmax): s = 2^(8 - e) with max in [2^(e-1), 2^e), so that s max < 2^8; 1
+// when absmax is null (BF16 mode), zero or not finite
+__device__ __forceinline__ float data_scale(const unsigned int* absmax) {
+    if (!absmax) return 1.f;
+    const float mx = __uint_as_float(*absmax);
+    if (!(mx > 0.f) || !isfinite(mx)) return 1.f;
+    int e = 0;
+    frexpf(mx, &e);
+    return ldexpf(1.f, min(120, max(-120, 8 - e)));
 }
 
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -102,16 +138,26 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
-// bounded wait for the phase of parity `parity`; false if it did not complete
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait for the phase of parity `parity` (at most `limit` polls);
+// false if it did not complete
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, int limit = WAIT_LIMIT) {
     uint32_t done = 0;
-    for (int it = 0; it < WAIT_LIMIT && !done; ++it) {
+    for (int it = 0; it < limit && !done; ++it) {
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done)
                      : "r"(smem_u32(bar)), "r"(parity)
                      : "memory");
     }
     return done != 0;
+}
+
+// the producer's drain before tensor memory and shared memory are released:
+// waits (long limit) for the copies of the last min(STAGES, last + 1) ring
+// slots it filled, u = last - STAGES + 1 .. last.  Each of those slots has
+// not been refilled since (the producer refills a slot only after the
+// consumer frees it), so its barrier completes exactly that phase.
+__device__ __forceinline__ void drain_ring(uint64_t* full, int last) {
+    for (int u = last; u >= 0 && u > last - STAGES; --u) bar_wait(&full[u % STAGES], (u / STAGES) & 1);
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
@@ -126,20 +172,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+// ---------------------------------------------------------------------------
+// FP16 mode: *absmax = bits of max |w_m g[m][n]| (non-negative floats order
+// as their bit patterns); *absmax is zeroed before the launch
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_tp_absmax(const Geo G, const float* __restrict__ g,
+                                                   const float* __restrict__ fac, unsigned int* __restrict__ absmax) {
+    const size_t n4 = (size_t)G.M * G.Nt / 4;
+    const int lnt4 = __ffs(G.Nt / 4) - 1;                 // Nt / 4 is a power of two
+    float mx = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(g) + i);
+        const float f = fabsf(__ldg(&fac[i >> lnt4]));
+        mx = fmaxf(mx, f * fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(absmax, __float_as_uint(mx));
 }
 
 // ---------------------------------------------------------------------------
-// prep: A[b][a][n] = w_m g[m][n] -> per n, matrices (hi, lo) with rows b, K = a
+// prep: A[b][a][n] = s w_m g[m][n] -> per n, matrices (hi, lo) with rows b, K = a
 // (256 threads; CTA = 16 time samples x 4 rows b)
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __restrict__ g,
                                                  const float* __restrict__ fac, const float2* __restrict__ exn,
-                                                 __nv_bfloat16* __restrict__ At, float2* __restrict__ t, int nb,
-                                                 int ne) {
+                                                 T* __restrict__ At, float2* __restrict__ t, int nb, int ne,
+                                                 const unsigned int* __restrict__ absmax) {
     __shared__ float tile[4 * K][17];
+    const float sc = data_scale(absmax);
     const int n0 = nb + blockIdx.x * 16;
     const int b0 = blockIdx.y * 4;
     for (int i = threadIdx.x; i < 4 * K * 16; i += blockDim.x) {
@@ -153,11 +214,11 @@ __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __res
         const int c = it >> 6, rb = (it >> 4) & 3, ag = it & 15;
         const int n = n0 + c;
         if (n >= ne) continue;
-        __align__(16) __nv_bfloat16 hi[8], lo[8];
+        __align__(16) T hi[8], lo[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) split_bf16(tile[rb * K + ag * 8 + j][c], hi[j], lo[j]);
+        for (int j = 0; j < 8; ++j) Op<T>::split(sc * tile[rb * K + ag * 8 + j][c], hi[j], lo[j]);
         const int off = tile_off(b0 + rb, ag * 8, ROWS);
-        __nv_bfloat16* base = At + (size_t)(n - nb) * 2 * (ROWS * K);
+        T* base = At + (size_t)(n - nb) * 2 * (ROWS * K);
         *reinterpret_cast<uint4*>(base + off) = *reinterpret_cast<uint4*>(hi);
         *reinterpret_cast<uint4*>(base + ROWS * K + off) = *reinterpret_cast<uint4*>(lo);
     }
@@ -190,11 +251,13 @@ __global__ void __launch_bounds__(256) k_tp_prep(const Geo G, const float* __res
 //   G[jx, +ny/2, n] = sum_b Ey[+ny/2, b] D[jx, b].
 // Waits are bounded as in GEMM 2.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfloat16* __restrict__ Ex,
-                                                     const __nv_bfloat16* __restrict__ At,
+template <typename T>
+__global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const T* __restrict__ Ex,
+                                                     const T* __restrict__ At,
                                                      const float2* __restrict__ eyf,
-                                                     __nv_bfloat16* __restrict__ Dt, float2* __restrict__ Ghat,
-                                                     int* __restrict__ err, int nb, int ne) {
+                                                     T* __restrict__ Dt, float2* __restrict__ Ghat,
+                                                     int* __restrict__ err, int nb, int ne,
+                                                     const unsigned int* __restrict__ absmax, int wl) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sEx = smem;                                  // 4 x 32 KB
     unsigned char* sA = smem + 4 * MAT;                         // STAGES x (hi, lo) chunks of 16 KB
@@ -231,10 +294,10 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
             int u = 0, last = -1;
             bool ok = true;
             for (int n = nb + blockIdx.x; n < ne && ok; n += gridDim.x) {
-                const __nv_bfloat16* an = At + (size_t)(n - nb) * 2 * (ROWS * K);
+                const T* an = At + (size_t)(n - nb) * 2 * (ROWS * K);
                 for (int c = 0; c < 2; ++c, ++u) {
                     const int s = u % STAGES;
-                    if (!bar_wait(&empty[s], ((u / STAGES) & 1) ^ 1)) {
+                    if (!bar_wait(&empty[s], ((u / STAGES) & 1) ^ 1, wl)) {
                         atomicExch(err, 1);
                         ok = false;
                         break;
@@ -245,27 +308,27 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
                     last = u;
                 }
             }
-            if (last >= 0) bar_wait(&full[last % STAGES], (last / STAGES) & 1);
+            drain_ring(full, last);
             bar_wait(&ex_bar, 0);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            bool ok = bar_wait(&ex_bar, 0);
-            const uint32_t id = idesc_bf16(128);
+            bool ok = bar_wait(&ex_bar, 0, wl);
+            const uint32_t id = idesc_f16kind(128, Op<T>::ab);
             const uint64_t x0 = sdesc(smem_u32(sEx)), x1 = x0 + (MAT >> 4), x2 = x0 + 2 * (MAT >> 4),
                            x3 = x0 + 3 * (MAT >> 4);
             const uint64_t abase = sdesc(smem_u32(sA));
             int q = 0, u = 0;
             for (int n = nb + blockIdx.x; n < ne && ok; n += gridDim.x, ++q) {
                 const int a = q & 1;
-                if (!bar_wait(&tempty[a], ((q >> 1) & 1) ^ 1)) {
+                if (!bar_wait(&tempty[a], ((q >> 1) & 1) ^ 1, wl)) {
                     ok = false;
                     break;
                 }
                 const uint32_t tre = tacc + 256 * a, tim = tre + 128;
                 for (int c = 0; c < 2; ++c, ++u) {
                     const int s = u % STAGES;
-                    if (!bar_wait(&full[s], (u / STAGES) & 1)) {
+                    if (!bar_wait(&full[s], (u / STAGES) & 1, wl)) {
                         ok = false;
                         break;
                     }
@@ -296,17 +359,18 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
         const int jx = quarter * 32 + lane;
         const int ntn = (ne - nb) / TM;
         const float2* eyp = eyf + (size_t)G.ny * K;             // Ey row jy = +ny/2
+        const float inv = 1.f / data_scale(absmax);             // a power of two: exact
         int q = 0;
         for (int n = nb + blockIdx.x; n < ne; n += gridDim.x, ++q) {
             const int a = q & 1;
-            if (!__all_sync(0xffffffffu, bar_wait(&tfull[a], (q >> 1) & 1))) {
+            if (!__all_sync(0xffffffffu, bar_wait(&tfull[a], (q >> 1) & 1, wl))) {
                 if (lane == 0) atomicExch(err, 1);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t trow = tacc + ((uint32_t)(quarter * 32) << 16) + 256 * a;
             const int nr = (n - nb) % TM;
-            __nv_bfloat16* out = Dt + ((size_t)jx * ntn + (n - nb) / TM) * (4 * DT_STAGE / 2);
+            T* out = Dt + ((size_t)jx * ntn + (n - nb) / TM) * (4 * DT_STAGE / 2);
             float gr = 0.f, gi = 0.f;
             for (int c0 = 0; c0 < 128; c0 += 32) {
                 const bool mine = (c0 >> 6) == half;
@@ -326,11 +390,11 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
                 if (!mine) continue;
 #pragma unroll
                 for (int g8 = 0; g8 < 4; ++g8) {
-                    __align__(16) __nv_bfloat16 rh[8], rl[8], ih[8], il[8];
+                    __align__(16) T rh[8], rl[8], ih[8], il[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        split_bf16(__uint_as_float(vr[g8 * 8 + j]), rh[j], rl[j]);
-                        split_bf16(__uint_as_float(vi[g8 * 8 + j]), ih[j], il[j]);
+                        Op<T>::split(__uint_as_float(vr[g8 * 8 + j]), rh[j], rl[j]);
+                        Op<T>::split(__uint_as_float(vi[g8 * 8 + j]), ih[j], il[j]);
                     }
                     {
                         // (row n, b) in K chunk b / 32: ((n / 8) * 4 + (b % 32) / 8) * 64 + (n % 8) * 8 + b % 8
@@ -347,7 +411,7 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(&tempty[a]);
-            if (half == 0) Ghat[((size_t)jx * G.nyp + G.ny) * G.Nt + n] = make_float2(gr, gi);
+            if (half == 0) Ghat[((size_t)jx * G.nyp + G.ny) * G.Nt + n] = make_float2(gr * inv, gi * inv);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -378,10 +442,11 @@ __global__ void __launch_bounds__(320, 1) k_tp_gemm1(const Geo G, const __nv_bfl
 // and the CTA waits for its own copies and MMAs in flight before it frees
 // tensor memory.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfloat16* __restrict__ Dt,
-                                                     const __nv_bfloat16* __restrict__ Ey,
+template <typename T>
+__global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const T* __restrict__ Dt,
+                                                     const T* __restrict__ Ey,
                                                      float2* __restrict__ Ghat, int* __restrict__ err, int nb,
-                                                     int ne) {
+                                                     int ne, const unsigned int* __restrict__ absmax, int wl) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sEy = smem;                                  // 4 x 32 KB
     unsigned char* sD = smem + 4 * MAT;                         // STAGES x 32 KB
@@ -423,10 +488,10 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
             int u = 0, last = -1;
             bool ok = true;
             for (int it = slot; it < items && ok; it += nslots) {
-                const __nv_bfloat16* src = Dt + (size_t)it * (4 * DT_STAGE / 2);   // item = jx * ntn + nt
+                const T* src = Dt + (size_t)it * (4 * DT_STAGE / 2);   // item = jx * ntn + nt
                 for (int c = 0; c < 4; ++c, ++u) {
                     const int s = u % STAGES;
-                    if (!bar_wait(&empty[s], ((u / STAGES) & 1) ^ 1)) {
+                    if (!bar_wait(&empty[s], ((u / STAGES) & 1) ^ 1, wl)) {
                         atomicExch(err, 1);
                         ok = false;
                         break;
@@ -436,13 +501,13 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
                     last = u;
                 }
             }
-            if (last >= 0) bar_wait(&full[last % STAGES], (last / STAGES) & 1);
+            drain_ring(full, last);
             bar_wait(&ey_bar, 0);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            bool ok = bar_wait(&ey_bar, 0);
-            const uint32_t id = idesc_bf16(128), idn = id | (1u << 13);    // M = N = 128; negate A
+            bool ok = bar_wait(&ey_bar, 0, wl);
+            const uint32_t id = idesc_f16kind(128, Op<T>::ab), idn = id | (1u << 13);    // M = N = 128; negate A
             // descriptors of the operand bases; a K step adds its byte offset / 16
             // to the start-address field (no carry: shared addresses < 2^18)
             const uint64_t e0 = sdesc(smem_u32(sEy)), e1 = e0 + (MAT >> 4), e2 = e0 + 2 * (MAT >> 4),
@@ -451,14 +516,14 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
             int q = 0, u = 0;
             for (int it = slot; it < items && ok; it += nslots, ++q) {
                 const int a = q & 1;
-                if (!bar_wait(&tempty[a], ((q >> 1) & 1) ^ 1)) {
+                if (!bar_wait(&tempty[a], ((q >> 1) & 1) ^ 1, wl)) {
                     ok = false;
                     break;
                 }
                 const uint32_t tre = tacc + 256 * a, tim = tre + 128;
                 for (int c = 0; c < 4; ++c, ++u) {
                     const int s = u % STAGES;
-                    if (!bar_wait(&full[s], (u / STAGES) & 1)) {
+                    if (!bar_wait(&full[s], (u / STAGES) & 1, wl)) {
                         ok = false;
                         break;
                     }
@@ -499,10 +564,11 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
     } else {
         const int quarter = warp & 3;                           // TMEM lanes 32 quarter .. + 31
         const int row = quarter * 32 + lane;                    // time sample within the tile
+        const float inv = 1.f / data_scale(absmax);             // a power of two: exact
         int q = 0;
         for (int it = slot; it < items; it += nslots, ++q) {
             const int a = q & 1;
-            if (!__all_sync(0xffffffffu, bar_wait(&tfull[a], (q >> 1) & 1))) {
+            if (!__all_sync(0xffffffffu, bar_wait(&tfull[a], (q >> 1) & 1, wl))) {
                 if (lane == 0) atomicExch(err, 1);
                 break;
             }
@@ -516,7 +582,7 @@ __global__ void __launch_bounds__(192, 1) k_tp_gemm2(const Geo G, const __nv_bfl
                 tmem_ld32(ta + 128 + j0, vi);
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
-                    o[(size_t)(j0 + j) * G.Nt] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+                    o[(size_t)(j0 + j) * G.Nt] = make_float2(__uint_as_float(vr[j]) * inv, __uint_as_float(vi[j]) * inv);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -576,27 +642,43 @@ size_t tp_gemm2_smem() { return 4 * tp::MAT + tp::STAGES * tp::DT_STAGE; }
 cudaError_t configure_tp_kernels() {
     cudaError_t e;
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if ((e = cudaFuncSetAttribute(tp::k_tp_gemm1, a, (int)tp_gemm1_smem()))) return e;
-    if ((e = cudaFuncSetAttribute(tp::k_tp_gemm2, a, (int)tp_gemm2_smem()))) return e;
+    if ((e = cudaFuncSetAttribute(tp::k_tp_gemm1<__nv_bfloat16>, a, (int)tp_gemm1_smem()))) return e;
+    if ((e = cudaFuncSetAttribute(tp::k_tp_gemm2<__nv_bfloat16>, a, (int)tp_gemm2_smem()))) return e;
+    if ((e = cudaFuncSetAttribute(tp::k_tp_gemm1<__half>, a, (int)tp_gemm1_smem()))) return e;
+    if ((e = cudaFuncSetAttribute(tp::k_tp_gemm2<__half>, a, (int)tp_gemm2_smem()))) return e;
     return cudaSuccess;
 }
 
-cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, cudaStream_t s) {
+template <typename T>
+static cudaError_t launch_tp_ned_t(const nedner_plan_s& p, const float* g, float2* Ghat, cudaStream_t s,
+                                   const unsigned int* absmax) {
     const Geo& G = p.geo;
-    __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(p.tp.work);
+    T* At = reinterpret_cast<T*>(p.tp.work);
     const int ch = tp_chunk(G.Nt);
-    __nv_bfloat16* Dt = At + (size_t)ch * 2 * (tp::ROWS * tp::K);
+    T* Dt = At + (size_t)ch * 2 * (tp::ROWS * tp::K);
     float2* tl = reinterpret_cast<float2*>(Dt + (size_t)ch * 4 * (tp::ROWS * tp::K));
     for (int nb = 0; nb < G.Nt; nb += ch) {
         const int ne = nb + ch;
-        tp::k_tp_prep<<<dim3(ch / 16, tp::K / 4), 256, 0, s>>>(G, g, p.t.sens_fac, p.tp.exn, At, tl, nb, ne);
-        tp::k_tp_gemm1<<<std::min(ch, p.tp.sms), 320, tp_gemm1_smem(), s>>>(
-            G, reinterpret_cast<const __nv_bfloat16*>(p.tp.ex), At, p.tp.eyf, Dt, Ghat, p.tp.err, nb, ne);
-        tp::k_tp_gemm2<<<2 * std::max(1, p.tp.sms / 2), 192, tp_gemm2_smem(), s>>>(
-            G, Dt, reinterpret_cast<const __nv_bfloat16*>(p.tp.ey), Ghat, p.tp.err, nb, ne);
+        tp::k_tp_prep<T><<<dim3(ch / 16, tp::K / 4), 256, 0, s>>>(G, g, p.t.sens_fac, p.tp.exn, At, tl, nb, ne,
+                                                                  absmax);
+        tp::k_tp_gemm1<T><<<std::min(ch, p.tp.sms), 320, tp_gemm1_smem(), s>>>(
+            G, reinterpret_cast<const T*>(p.tp.ex), At, p.tp.eyf, Dt, Ghat, p.tp.err, nb, ne, absmax,
+            p.tp.wait_limit);
+        tp::k_tp_gemm2<T><<<2 * std::max(1, p.tp.sms / 2), 192, tp_gemm2_smem(), s>>>(
+            G, Dt, reinterpret_cast<const T*>(p.tp.ey), Ghat, p.tp.err, nb, ne, absmax, p.tp.wait_limit);
     }
     tp::k_tp_nyq_g<<<dim3((G.Nt + 31) / 32, (G.nyp + 7) / 8), 256, 0, s>>>(G, tl, p.tp.eyf, Ghat);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, cudaStream_t s) {
+    if (!p.tp.fp16) return launch_tp_ned_t<__nv_bfloat16>(p, g, Ghat, s, nullptr);
+    cudaError_t e = cudaMemsetAsync(p.tp.absmax, 0, sizeof(unsigned int), s);
+    if (e) return e;
+    const size_t n4 = (size_t)p.geo.M * p.geo.Nt / 4;
+    const int blocks = (int)std::min<size_t>((n4 + 255) / 256, (size_t)p.tp.sms * 8);
+    tp::k_tp_absmax<<<blocks, 256, 0, s>>>(p.geo, g, p.t.sens_fac, p.tp.absmax);
+    return launch_tp_ned_t<__half>(p, g, Ghat, s, p.tp.absmax);
 }
 
 }  // namespace nedner

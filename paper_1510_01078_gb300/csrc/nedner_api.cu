@@ -7,6 +7,7 @@
 // grid row, the deconvolution tables 1/phihat of both NUFFTs (Eq. PSI), the
 // tap polynomials of the NER interpolation, and the lateral part of nu^2 for
 // every line.  It then allocates the device workspace.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -95,6 +96,7 @@ void free_sensor_tables(DevTables& t) {
 
 void free_tp(TPState& tp) {
     cudaFree(tp.work); cudaFree(tp.ex); cudaFree(tp.ey); cudaFree(tp.exn); cudaFree(tp.eyf); cudaFree(tp.err);
+    cudaFree(tp.absmax);
     tp = TPState();
 }
 
@@ -112,6 +114,30 @@ float bf2f(uint16_t h) {
     return f;
 }
 
+// host FP16 (round to nearest even, subnormals kept) through the CUDA header's conversion
+uint16_t f2h(float f) {
+    const __half h = __float2half_rn(f);
+    uint16_t u;
+    std::memcpy(&u, &h, 2);
+    return u;
+}
+float h2f(uint16_t u) {
+    __half h;
+    std::memcpy(&h, &u, 2);
+    return __half2float(h);
+}
+
+// the hi + lo split of an exponent factor in the plan's operand type
+void split16(float x, bool fp16, uint16_t& hi, uint16_t& lo) {
+    if (fp16) {
+        hi = f2h(x);
+        lo = f2h(x - h2f(hi));
+    } else {
+        hi = f2bf(x);
+        lo = f2bf(x - bf2f(hi));
+    }
+}
+
 // element offset of (r, k) in a chunked K-major operand matrix (K chunks of 64)
 size_t tp_off(int r, int k, int rows) {
     const int c = k >> 6, kk = k & 63;
@@ -119,7 +145,7 @@ size_t tp_off(int r, int k, int rows) {
 }
 
 // Tensor-product path: check the layout and build the exponent operands.
-nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
+nedner_status build_tp(nedner_plan_s& p, cudaStream_t s, bool fp16) {
     const int NS = TP_SENSORS;
     const Geo& G = p.geo;
     if (p.M != (int64_t)NS * NS || G.nx != 2 * NS || G.ny != 2 * NS) return NEDNER_EINVAL;
@@ -141,11 +167,8 @@ nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
             const double ph = -2.0 * kPi * (double)jx * xs[a] / X;
             const float re = (float)std::cos(ph), im = (float)std::sin(ph);
             const size_t o = tp_off(jx, a, NS);
-            const uint16_t rh = f2bf(re), ih = f2bf(im);
-            ex[0 * MATE + o] = rh;
-            ex[1 * MATE + o] = f2bf(re - bf2f(rh));
-            ex[2 * MATE + o] = ih;
-            ex[3 * MATE + o] = f2bf(im - bf2f(ih));
+            split16(re, fp16, ex[0 * MATE + o], ex[1 * MATE + o]);
+            split16(im, fp16, ex[2 * MATE + o], ex[3 * MATE + o]);
         }
     // Ey as GEMM 2's A operand: two M tiles (jy = -128..-1, 0..127), 4 matrices each
     for (int t = 0; t < 2; ++t)
@@ -155,11 +178,8 @@ nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
                 const double ph = -2.0 * kPi * (double)jy * ys[b] / Y;
                 const float re = (float)std::cos(ph), im = (float)std::sin(ph);
                 const size_t o = (size_t)t * 4 * MATE + tp_off(r, b, NS);
-                const uint16_t rh = f2bf(re), ih = f2bf(im);
-                ey[o + 0 * MATE] = rh;
-                ey[o + 1 * MATE] = f2bf(re - bf2f(rh));
-                ey[o + 2 * MATE] = ih;
-                ey[o + 3 * MATE] = f2bf(im - bf2f(ih));
+                split16(re, fp16, ey[o + 0 * MATE], ey[o + 1 * MATE]);
+                split16(im, fp16, ey[o + 2 * MATE], ey[o + 3 * MATE]);
             }
         }
     std::vector<float2> exn(NS), eyf((size_t)G.nyp * NS);
@@ -189,6 +209,7 @@ nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = cudaMalloc(&tp.work, tp.work_bytes);
     if (!e) e = cudaMalloc((void**)&tp.err, sizeof(int));
     if (!e) e = cudaMemsetAsync(tp.err, 0, sizeof(int), s);
+    if (!e && fp16) e = cudaMalloc((void**)&tp.absmax, sizeof(unsigned int));
     if (!e) e = configure_tp_kernels();
     if (!e) e = cudaStreamSynchronize(s);
     if (e) {
@@ -197,6 +218,7 @@ nedner_status build_tp(nedner_plan_s& p, cudaStream_t s) {
         return e == cudaErrorMemoryAllocation ? NEDNER_ENOMEM : NEDNER_ECUDA;
     }
     tp.enabled = 1;
+    tp.fp16 = fp16 ? 1 : 0;
     return NEDNER_OK;
 }
 
@@ -533,9 +555,11 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     if (sigma != 2.0) return NEDNER_EINVAL;
     if (window.kind != NEDNER_WINDOW_KB && window.kind != NEDNER_WINDOW_GAUSS) return NEDNER_EINVAL;
     if (window.width < 4 || window.width > 16 || (window.width & 1)) return NEDNER_EINVAL;
-    nedner_opts o = {1, 0, 0, nullptr, NEDNER_NED_NUFFT};
+    nedner_opts o = {1, 0, 0, nullptr, NEDNER_PRECISION_FP32_NUFFT};
     if (opts) o = *opts;
-    if (o.ned_mode != NEDNER_NED_NUFFT && o.ned_mode != NEDNER_NED_TENSOR_BF16) return NEDNER_EINVAL;
+    if (o.precision != NEDNER_PRECISION_FP32_NUFFT && o.precision != NEDNER_PRECISION_BF16_GEMM &&
+        o.precision != NEDNER_PRECISION_FP16_GEMM)
+        return NEDNER_EINVAL;
 
     nedner_plan_s* p = new (std::nothrow) nedner_plan_s();
     if (!p) return NEDNER_ENOMEM;
@@ -611,7 +635,8 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     if (st == NEDNER_OK) st = build_sensor_tables(*p, s);
     if (st == NEDNER_OK && configure_fwd_kernels(*p) != cudaSuccess) st = NEDNER_ECUDA;
     if (st == NEDNER_OK && configure_adj_kernels(*p) != cudaSuccess) st = NEDNER_ECUDA;
-    if (st == NEDNER_OK && o.ned_mode == NEDNER_NED_TENSOR_BF16) st = build_tp(*p, s);
+    if (st == NEDNER_OK && o.precision != NEDNER_PRECISION_FP32_NUFFT)
+        st = build_tp(*p, s, o.precision == NEDNER_PRECISION_FP16_GEMM);
     if (st != NEDNER_OK) {
         cudaGetLastError();
         free_tables(p->t);
@@ -800,6 +825,12 @@ nedner_status nedner_device_status(nedner_plan_t p, int* flags) {
     }
     *flags = (f ? NEDNER_STATUS_WAIT_TIMEOUT : 0) | ((st & NEDNER_FLAG_NONFINITE) ? NEDNER_STATUS_NONFINITE : 0);
     return (*flags & NEDNER_STATUS_NONFINITE) ? NEDNER_ENAN : NEDNER_OK;
+}
+
+nedner_status nedner_debug_set_wait_limit(nedner_plan_t p, int polls) {
+    if (!p || polls < 0) return NEDNER_EINVAL;
+    p->tp.wait_limit = std::min(polls, TP_WAIT_LIMIT);
+    return NEDNER_OK;
 }
 
 size_t nedner_workspace_bytes(nedner_plan_t p) { return p ? p->ws_bytes : 0; }

@@ -102,19 +102,30 @@ def random_balls(n: int, rng: np.random.Generator, r_range, xy_half: float, z_ra
 
 def nwave_data(sensor_xy: np.ndarray, balls: Balls, Nt: int, dt: float, c: float = C_SOUND,
                chunk: int = 1024) -> np.ndarray:
-    """g[m, n] = sum over balls of A (r - c t_n) / (2 r) for |r - c t_n| < R."""
+    """g[m, n] = sum over balls of A (r - c t_n) / (2 r) for |r - c t_n| < R.
+
+    Each ball's signal is non-zero only for |r - c t_n| < R, so only the
+    samples of that window (plus one on each side) are evaluated; the values
+    and the order in which the balls are added are those of the plain sum."""
     xy = np.asarray(sensor_xy, dtype=np.float64)
     M = xy.shape[0]
     g = np.zeros((M, Nt), dtype=np.float64)
     ct = c * dt * np.arange(Nt, dtype=np.float64)
+    cdt = c * dt
     for b in range(len(balls.radii)):
         cx, cy, cz = balls.centres[b]
         R, A = balls.radii[b], balls.amps[b]
+        K = int(np.ceil(2.0 * R / cdt)) + 4                 # samples of a window, with margin
         for s in range(0, M, chunk):
             r = np.sqrt((xy[s:s + chunk, 0] - cx) ** 2 + (xy[s:s + chunk, 1] - cy) ** 2 + cz * cz)
-            d = r[:, None] - ct[None, :]
-            inside = np.abs(d) < R
-            g[s:s + chunk] += np.where(inside, A * d / (2.0 * r[:, None]), 0.0)
+            n0 = np.floor((r - R) / cdt).astype(np.int64) - 1
+            idx = n0[:, None] + np.arange(K)[None, :]
+            ok = (idx >= 0) & (idx < Nt)
+            idc = np.clip(idx, 0, Nt - 1)
+            d = r[:, None] - ct[idc]
+            inside = ok & (np.abs(d) < R)
+            rows = np.broadcast_to(np.arange(s, s + len(r))[:, None], idc.shape)
+            g[rows[inside], idc[inside]] += (A * d / (2.0 * r[:, None]))[inside]
     return g
 
 

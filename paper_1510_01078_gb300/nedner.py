@@ -41,10 +41,12 @@ class _Window(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("apply_weights", ctypes.c_int), ("band_mask", ctypes.c_int),
                 ("max_workspace_bytes", ctypes.c_size_t), ("sensor_w", ctypes.c_void_p),
-                ("ned_mode", ctypes.c_int)]
+                ("precision", ctypes.c_int)]
 
 
-NED_NUFFT, NED_TENSOR_BF16 = 0, 1
+PRECISION_FP32_NUFFT, PRECISION_BF16_GEMM, PRECISION_FP16_GEMM = 0, 1, 2
+# ned_mode names of the binding -> precision values of nedner_opts
+NED_MODES = {"nufft": PRECISION_FP32_NUFFT, "tensor_bf16": PRECISION_BF16_GEMM, "tensor_fp16": PRECISION_FP16_GEMM}
 
 
 # symbol -> (restype, argtypes); mirrors include/nedner.h
@@ -67,6 +69,7 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "nedner_forward_host": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_device_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "nedner_debug_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int]),
     "nedner_destroy": (ctypes.c_int, [_P]),
     "nedner_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -143,7 +146,7 @@ class Plan:
         kind = {"kb": WINDOW_KB, "gauss": WINDOW_GAUSS}[window[0]] if isinstance(window[0], str) else int(window[0])
         w = _Window(kind, int(window[1]))
         self._h = None if sensor_w is None else np.ascontiguousarray(np.asarray(sensor_w, dtype=np.float64))
-        mode = {"nufft": NED_NUFFT, "tensor_bf16": NED_TENSOR_BF16}[ned_mode]
+        mode = NED_MODES[ned_mode]
         opts = _Opts(int(bool(apply_weights)), int(bool(band_mask)), int(max_workspace_bytes),
                      None if self._h is None else self._h.ctypes.data, mode)
         handle = ctypes.c_void_p()
@@ -177,6 +180,11 @@ class Plan:
         if st != ENAN:
             _check(st, "nedner_device_status")
         return int(f.value)
+
+    def debug_set_wait_limit(self, polls: int):
+        """Test hook: the tensor-core kernels' pipeline waits give up after
+        ``polls`` polls (0: at once); 1 << 26 restores the default."""
+        _check(_load().nedner_debug_set_wait_limit(self._handle, int(polls)), "nedner_debug_set_wait_limit")
 
     @property
     def workspace_bytes(self) -> int:

@@ -14,6 +14,7 @@ import pytest
 import oracle
 from oracle import Problem
 from paper_1510_01078_gb300 import inputs
+from parity import check
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -59,7 +60,7 @@ def test_adjoint_matches_oracle(nd, spec):
     plan = nd.plan_from_config(case)
     got = plan.adjoint(torch.as_tensor(p, dtype=torch.float32, device="cuda")).cpu().numpy()
     plan.close()
-    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    check(got, want, TOL)
 
 
 @pytest.mark.parametrize("spec", CASES[:3], ids=IDS[:3])
@@ -87,7 +88,7 @@ def test_grad_positions_matches_oracle(nd, spec):
     got = plan.grad_positions(torch.as_tensor(case["g"], dtype=torch.float32, device="cuda"),
                               torch.as_tensor(lam, dtype=torch.float32, device="cuda")).cpu().numpy()
     plan.close()
-    assert rel_l2(got, want) <= TOL_GRAD, rel_l2(got, want)
+    check(got, want, TOL_GRAD)
 
 
 def test_adjoint_c2_full_size(nd):
@@ -99,7 +100,7 @@ def test_adjoint_c2_full_size(nd):
     plan = nd.plan_from_config(case)
     got = plan.adjoint(torch.as_tensor(p, dtype=torch.float32, device="cuda")).cpu().numpy()
     plan.close()
-    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    check(got, want, TOL)
 
 
 def test_adjoint_options(nd):
@@ -111,7 +112,7 @@ def test_adjoint_options(nd):
         plan = nd.plan_from_config(case, **kw)
         got = plan.adjoint(torch.as_tensor(p, dtype=torch.float32, device="cuda")).cpu().numpy()
         plan.close()
-        assert rel_l2(got, want) <= TOL, (kw, rel_l2(got, want))
+        check(got, want, TOL)
 
 
 def test_autograd_function(nd):
@@ -127,8 +128,8 @@ def test_autograd_function(nd):
     (p0 * lam_t).sum().backward()
     want_g = oracle.adjoint(problem(case), lam)
     want_xy = oracle.grad_positions(problem(case), case["g"], lam)
-    assert rel_l2(g.grad.cpu().numpy(), want_g) <= TOL
-    assert rel_l2(xy.grad.numpy(), want_xy) <= TOL_GRAD
+    check(g.grad.cpu().numpy(), want_g, TOL)
+    check(xy.grad.numpy(), want_xy, TOL_GRAD)
     plan.close()
 
 
@@ -143,11 +144,11 @@ def test_adjoint_and_grad_wide_rows(nd):
     plan = nd.plan_from_config(case)
     pt = torch.as_tensor(p, dtype=torch.float32, device="cuda")
     got = plan.adjoint(pt).cpu().numpy()
-    assert rel_l2(got, oracle.adjoint(pr, p)) <= TOL, rel_l2(got, oracle.adjoint(pr, p))
+    check(got, oracle.adjoint(pr, p), TOL)
     gg = plan.grad_positions(torch.as_tensor(g, dtype=torch.float32, device="cuda"), pt).cpu().numpy()
     want = oracle.grad_positions(pr, g, p)
     plan.close()
-    assert rel_l2(gg, want) <= TOL_GRAD, rel_l2(gg, want)
+    check(gg, want, TOL_GRAD)
 
 
 def test_adjoint_in_passes_under_workspace_limit(nd):
@@ -167,7 +168,7 @@ def test_adjoint_in_passes_under_workspace_limit(nd):
     b = tight.adjoint(pt).cpu().numpy()
     tight.close()
     assert rel_l2(b, a) <= 1e-6, rel_l2(b, a)
-    assert rel_l2(b, oracle.adjoint(problem(case), p)) <= TOL
+    check(b, oracle.adjoint(problem(case), p), TOL)
 
 
 LIMITS = [
@@ -190,8 +191,8 @@ def test_adjoint_and_grad_at_size_limits(nd, spec):
     pt = torch.as_tensor(p, dtype=torch.float32, device="cuda")
     got = plan.adjoint(pt).cpu().numpy()
     want = oracle.adjoint(pr, p)
-    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    check(got, want, TOL)
     gg = plan.grad_positions(torch.as_tensor(case["g"], dtype=torch.float32, device="cuda"), pt).cpu().numpy()
     want_g = oracle.grad_positions(pr, case["g"], p)
     plan.close()
-    assert rel_l2(gg, want_g) <= TOL_GRAD, rel_l2(gg, want_g)
+    check(gg, want_g, TOL_GRAD)

@@ -13,6 +13,7 @@ import pytest
 import oracle
 from oracle import Problem
 from paper_1510_01078_gb300 import inputs
+from parity import check
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -63,7 +64,7 @@ def test_forward_matches_oracle_small(nd, spec):
     case = inputs.small_case(**spec)
     want = oracle.forward(problem(case), case["g"])
     got = gpu_forward(nd, case)
-    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    check(got, want, TOL)
 
 
 @pytest.mark.parametrize("spec", SMALL[:3], ids=lambda s: "{nx}x{ny}_M{M}_Nt{Nt}".format(**s))
@@ -76,7 +77,7 @@ def test_ned_stage_matches_oracle(nd, spec):
     plan = nd.plan_from_config(case)
     got = plan.ned_stage(torch.as_tensor(case["g"], dtype=torch.float32, device="cuda")).cpu().numpy()
     plan.close()
-    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    check(got, want, TOL)
 
 
 def test_forward_c1_tiny(nd):
@@ -84,7 +85,7 @@ def test_forward_c1_tiny(nd):
     case = inputs.make_config(0)
     want = oracle.forward(problem(case), case["g"])
     got = gpu_forward(nd, case)
-    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    check(got, want, TOL)
 
 
 def test_forward_c2_full_size(nd):
@@ -92,7 +93,7 @@ def test_forward_c2_full_size(nd):
     case = inputs.make_config(1)
     want = oracle.forward(problem(case), case["g"])
     got = gpu_forward(nd, case)
-    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    check(got, want, TOL)
 
 
 def test_forward_c3_full_size_sparse_time(nd):
@@ -107,7 +108,7 @@ def test_forward_c3_full_size_sparse_time(nd):
     g[:, ns] = gs
     want = oracle.forward(problem(case), gs, ns=ns)
     got = gpu_forward(nd, case, g=g)
-    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    check(got, want, TOL)
 
 
 # nx, ny or nz at the plan's maximum of 2048, and Nt at its maximum of 4096: a
@@ -127,7 +128,7 @@ def test_forward_at_size_limits(nd, spec):
     case = inputs.small_case(**spec)
     want = oracle.forward(problem(case), case["g"])
     got = gpu_forward(nd, case)
-    assert rel_l2(got, want) <= TOL, rel_l2(got, want)
+    check(got, want, TOL)
 
 
 @pytest.mark.parametrize("opt", ["unweighted", "band_mask", "gauss16", "kb8"])
@@ -146,7 +147,7 @@ def test_forward_options(nd, opt):
         tol = 1e-4                      # KB w = 8 interpolation error ~ 2e-7
     want = oracle.forward(problem(case, **okw), case["g"])
     got = gpu_forward(nd, case, **kw)
-    assert rel_l2(got, want) <= tol, rel_l2(got, want)
+    check(got, want, tol)
 
 
 def test_forward_no_sensors(nd):
@@ -180,7 +181,7 @@ def test_set_positions_matches_fresh_plan(nd):
     a = plan.forward(g).cpu().numpy()
     case2 = dict(case, sensor_xy=xy2)
     want = oracle.forward(problem(case2), case["g"])
-    assert rel_l2(a, want) <= TOL
+    check(a, want, TOL)
     plan.close()
 
 
@@ -214,4 +215,4 @@ def test_forward_host_small_and_ragged(nd):
     out = plan.forward_host(torch.as_tensor(g).pin_memory())
     torch.cuda.synchronize()
     plan.close()
-    assert rel_l2(out.numpy(), oracle.forward(problem(case), g)) <= TOL
+    check(out.numpy(), oracle.forward(problem(case), g), TOL)

@@ -335,3 +335,40 @@ def test_sparse_time_samples_equal_dense_zero_filled():
     pm = _problem(case, band_mask=True)
     np.testing.assert_allclose(oracle.spectrum(pm, gs, ns=ns), oracle.spectrum(pm, g), rtol=0,
                                atol=1e-12 * np.abs(oracle.spectrum(pm, g)).max())
+
+
+def test_spectrum_block_matches_spectrum():
+    """The product-set subset evaluation equals the full spectrum on its lines."""
+    case = inputs.small_case(6, 8, 8, 11, 10, seed=13)
+    pr = _problem(case)
+    F = oracle.spectrum(pr, case["g"])
+    jx = np.array([-3, 0, 2]); jy = np.array([1, -4]); ls = np.array([-4, 0, 3])
+    S = oracle.spectrum_block(pr, case["g"], jx, jy, ls)
+    np.testing.assert_allclose(S, F[np.ix_(jx + 3, jy + 4, ls + 4)], atol=1e-12)
+
+
+def test_line_restricted_transposes_equal_the_full_ones():
+    """adjoint and grad_positions restricted to a product set of lines (and a
+    subset of sensors) equal the full sums when the volume's spectrum vanishes
+    outside that set: the volume is the real part of an inverse DFT of a
+    spectrum supported on jx x jy, whose mirror -jx x -jy the set contains."""
+    case = inputs.small_case(16, 8, 16, 40, 32, seed=61, layout="disc")
+    pr = _problem(case)
+    rng = np.random.default_rng(62)
+    jx = np.array([-3, 2]); jy = np.array([1, 3])
+    lx = np.concatenate([jx, -jx]); ly = np.concatenate([jy, -jy])
+    B = np.zeros((pr.nz, pr.ny, pr.nx), dtype=np.complex128)
+    for a in jx:
+        for b in jy:
+            B[:, b % pr.ny, a % pr.nx] = rng.standard_normal(pr.nz) + 1j * rng.standard_normal(pr.nz)
+    p = np.real(np.fft.ifftn(B)) * pr.nx * pr.ny * pr.nz
+    sens = np.array([0, 7, 19, 39])
+    full = oracle.adjoint(pr, p)
+    part = oracle.adjoint(pr, p, lx, ly, sens)
+    np.testing.assert_allclose(part, full[sens], rtol=0, atol=1e-10 * np.abs(full).max())
+    gf = oracle.grad_positions(pr, case["g"], p)
+    gp = oracle.grad_positions(pr, case["g"], p, lx, ly, sens)
+    np.testing.assert_allclose(gp, gf[sens], rtol=0, atol=1e-10 * np.abs(gf).max())
+    # a set that misses the mirror lines gives a different (wrong) answer
+    wrong = oracle.adjoint(pr, p, jx, jy, sens)
+    assert np.abs(wrong - full[sens]).max() > 1e-3 * np.abs(full).max()
