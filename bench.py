@@ -462,6 +462,7 @@ def main():
 
     transposed = None
     interp_roofline = None
+    passes = transposed_passes(cfg)
     if do_t:
         aa, ak = kernel_table(per_adj, algorithmic_bytes_transposed(cfg, False))
         ga, gk = kernel_table(per_grad, algorithmic_bytes_transposed(cfg, True))
@@ -473,10 +474,14 @@ def main():
                                          "voxels_per_s": whole_job_value(voxels, world, grad_ms), "kernels": gk}}
         gb = gather_alg_bytes(cfg)
         gms = aa["gather"] + aa["entry_sum"]
+        tg = traffic_for("gather", cfg["name"])
         interp_roofline = {"bound": "hbm", "kernel": "adjoint gather + entry sum (transposed interpolation)",
                            "achieved": round(gb / (gms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                            "frac": round(gb / (gms * 1e-3) / 1e9 / peak, 4),
-                           "traffic": traffic_for("gather", cfg["name"]), "peak_source": peak_kind}
+                           "traffic": None if tg is None else tg * passes,
+                           "traffic_note": "DRAM bytes of the %d gather launches of one adjoint (entry sum not captured)"
+                                           % passes,
+                           "peak_source": peak_kind}
 
     # kernels launched in the timed region: five per reconstruction for the NUFFT
     # path; the tensor-core stage a runs prep + two GEMMs per pass of 512 time
@@ -485,7 +490,6 @@ def main():
         fwd_launches = len(nedner.Plan.FORWARD_KERNELS)
     else:
         fwd_launches = 3 * (cfg["Nt"] // min(512, cfg["Nt"])) + 1 + 3 + (1 if args.ned_mode == "tensor_fp16" else 0)
-    passes = transposed_passes(cfg)
     t_launches = (4 + 2 * passes) + 6 if do_t else 0
     launches = (fwd_launches + t_launches) * args.steps
 
