@@ -115,18 +115,26 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # algorithmic bytes per launch
 # --------------------------------------------------------------------------
-def algorithmic_bytes(cfg):
-    """Minimum HBM bytes per launch of each forward kernel (inputs read once,
-    outputs written once; complex64 intermediates on the half lattice)."""
+def algorithmic_bytes(cfg, split=True):
+    """Minimum HBM bytes per reconstruction of each forward kernel (inputs read
+    once, outputs written once; complex64 intermediates on the half lattice).
+    Stage (a) split: the spread writes the oversampled real grid Q (2nx x 2ny
+    per time sample), the x-FFT reads it and writes R; fused: one kernel reads
+    g and writes R."""
     M, Nt, nx, ny, nz = cfg["sensor_xy"].shape[0], cfg["Nt"], cfg["nx"], cfg["ny"], cfg["nz"]
-    nxh, Ly = nx // 2 + 1, 2 * ny
+    nxh, Ly, Lx = nx // 2 + 1, 2 * ny, 2 * nx
     g = M * Nt * 4
+    Q = Ly * Lx * Nt * 4
     R = nxh * Ly * Nt * 8
     Gh = nxh * (ny + 1) * Nt * 8
     V = nxh * ny * nz * 8
     p0 = nx * ny * nz * 4
-    return {"ned_spread_xfft": g + R, "ned_yfft": R + Gh, "ner_lines": Gh + V, "img_yifft": 2 * V,
-            "img_xc2r": V + p0}
+    d = {"ned_yfft": R + Gh, "ner_lines": Gh + V, "img_yifft": 2 * V, "img_xc2r": V + p0}
+    if split:
+        d.update(ned_spread=g + Q, ned_xfft=Q + R)
+    else:
+        d.update(ned_spread=g + R, ned_xfft=0)
+    return d
 
 
 def algorithmic_bytes_transposed(cfg, grad: bool):
@@ -135,10 +143,10 @@ def algorithmic_bytes_transposed(cfg, grad: bool):
     g (adjoint), or reads R and g and writes 2 floats per sensor (gradient);
     its per-entry intermediate and the per-sensor sum are counted as the
     sum's bytes (entries read, result written)."""
-    f = algorithmic_bytes(cfg)
+    f = algorithmic_bytes(cfg, split=False)
     M, Nt, w = cfg["sensor_xy"].shape[0], cfg["Nt"], 12
     g = M * Nt * 4
-    R = f["ned_spread_xfft"] - g
+    R = f["ned_spread"] - g
     if grad:
         nch = Nt // 64
         gather, esum = R + g + M * w * nch * 8, M * w * nch * 8 + M * 8
@@ -150,8 +158,8 @@ def algorithmic_bytes_transposed(cfg, grad: bool):
 
 def gather_alg_bytes(cfg):
     """Algorithmic bytes of the transposed interpolation as a whole (read the
-    grid rows R once, write g once): the forward spread's bytes reversed."""
-    return algorithmic_bytes(cfg)["ned_spread_xfft"]
+    grid rows R once, write g once): the fused forward spread's bytes reversed."""
+    return algorithmic_bytes(cfg, split=False)["ned_spread"]
 
 
 # --------------------------------------------------------------------------
@@ -334,6 +342,7 @@ def timed_loop(fn, steps, flush):
 
 def kernel_table(per, abytes):
     avg = {k: sum(v) / len(v) for k, v in per.items()}
+    avg = {k: v for k, v in avg.items() if v > 0.0}              # stages this path does not launch
     tot = sum(avg.values())
     return avg, {k: {"ms": round(avg[k], 5), "share": round(avg[k] / tot, 4), "alg_bytes": abytes[k],
                      "gbs": round(abytes[k] / (avg[k] * 1e-3) / 1e9, 1)} for k in avg}
@@ -445,10 +454,12 @@ def main():
 
     # per-kernel tables and rooflines
     peak, peak_kind = peaks()
-    abytes = algorithmic_bytes(cfg)
+    split = bool(nedner.work_split(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Nt"], 12)["split1"])
+    abytes = algorithmic_bytes(cfg, split)
     if args.ned_mode != "nufft":
         # stage (a) is one group of tensor-core kernels, reported under one name
-        per_fwd = {("tp_ned_gemm" if k == "ned_spread_xfft" else k): v for k, v in per_fwd.items() if k != "ned_yfft"}
+        per_fwd = {("tp_ned_gemm" if k == "ned_spread" else k): v for k, v in per_fwd.items()
+                   if k not in ("ned_xfft", "ned_yfft")}
         M, Nt = cfg["sensor_xy"].shape[0], cfg["Nt"]
         abytes = dict(abytes, tp_ned_gemm=M * Nt * 4 + (cfg["nx"] // 2 + 1) * (cfg["ny"] + 1) * Nt * 8)
     avg, kernels = kernel_table(per_fwd, abytes)
@@ -457,8 +468,8 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic_for(dom, cfg["name"]),
                 "peak_source": peak_kind + " (burst copy bandwidth)"}
-    spread_frac = (round(abytes["ned_spread_xfft"] / (avg["ned_spread_xfft"] * 1e-3) / 1e9 / peak, 4)
-                   if "ned_spread_xfft" in avg else None)
+    spread_frac = (round(abytes["ned_spread"] / (avg["ned_spread"] * 1e-3) / 1e9 / peak, 4)
+                   if "ned_spread" in avg else None)
 
     transposed = None
     interp_roofline = None
@@ -487,7 +498,8 @@ def main():
     # path; the tensor-core stage a runs prep + two GEMMs per pass of 512 time
     # samples, then the Nyquist line, plus the scale reduction in FP16 mode
     if args.ned_mode == "nufft":
-        fwd_launches = len(nedner.Plan.FORWARD_KERNELS)
+        ws = nedner.work_split(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Nt"], 12)
+        fwd_launches = 3 * (cfg["Nt"] // ws["tq"]) + 3 if ws["split1"] else 5
     else:
         fwd_launches = 3 * (cfg["Nt"] // min(512, cfg["Nt"])) + 1 + 3 + (1 if args.ned_mode == "tensor_fp16" else 0)
     t_launches = (4 + 2 * passes) + 6 if do_t else 0

@@ -181,10 +181,13 @@ nedner_status nedner_ned_stage(nedner_plan_t plan, const float* g, void* Ghat, v
  * nedner_forward with per-kernel timing, for measurement: records a CUDA event
  * around each of the forward kernels on `stream`, waits for the stream, and
  * writes each kernel's device time in milliseconds to stage_ms (host array of
- * NEDNER_FORWARD_KERNELS floats, in launch order: spread + x-FFT, y-FFT, NER
- * lines, y-IFFT, x-c2r).  Synchronous.  Same arguments and errors otherwise.
+ * NEDNER_FORWARD_KERNELS floats: NED spread, x-FFT, y-FFT, NER lines, y-IFFT,
+ * x complex-to-real; where stage (a) runs per chunk of time samples its
+ * three kernels' times are summed over the chunks; where the spread and
+ * x-FFT are one kernel, or stage (a) is the tensor-core GEMMs, its time is the
+ * first and the x-FFT's is 0).  Synchronous.  Same arguments and errors otherwise.
  */
-#define NEDNER_FORWARD_KERNELS 5
+#define NEDNER_FORWARD_KERNELS 6
 nedner_status nedner_forward_profiled(nedner_plan_t plan, const float* g, float* p0, void* stream,
                                       float* stage_ms);
 
@@ -290,7 +293,10 @@ size_t nedner_workspace_bytes(nedner_plan_t plan);
  * rows or lines per CTA, threads per CTA, values per thread and time samples
  * per lane of the stages), then the dynamic shared memory in bytes of the
  * spread, y-FFT, NER, y-IFFT, x complex-to-real and transposed gather
- * (adjoint, gradient) kernels.  Returns the number of values (21), or -1 for
+ * (adjoint, gradient) kernels; then split1 (1: stage (a) runs as block spread,
+ * x-FFT and y-FFT per chunk of tq time samples), tq, the block spread's warps
+ * per CTA, the x-FFT kernel's complex columns, threads and values per thread
+ * per CTA, and the shared memory of both.  Returns the number of values (29), or -1 for
  * a geometry nedner_plan rejects or a null out.  No paper counterpart.
  */
 int nedner_work_split(int nx, int ny, int nz, int Nt, int w, int64_t* out, int nout);

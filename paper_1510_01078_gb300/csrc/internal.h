@@ -37,6 +37,13 @@ struct Chunks {
     int threads1;  // threads per CTA in the spread stage
     int per1;      // values per thread in the spread stage's in-place x-FFT (16 or 32)
     int tpl1;      // time samples per lane in the spread stage (1 or 2)
+    int split1;    // 1: stage (a) runs as block spread + x-FFT + y-FFT over chunks of tq samples
+    int tq;        // time samples per chunk of the split stage (a multiple of 64 dividing Nt)
+    int wpc_s;     // warps (16-column blocks) per CTA of the block spread
+    int nbx;       // complex columns (time-sample pairs) per CTA of the x-FFT kernel
+    int thx;       // threads per CTA of the x-FFT kernel
+    int perx;      // values per thread of its in-place FFT (16 or 32)
+    size_t smem_s, smem_x;
     int ca;        // time samples per CTA in the transposed interpolation stage
     int per_adj;   // values per thread in its in-place row FFT (16 or 32)
     int tpl_adj;   // time samples per lane in the transposed gather (1 or 2; 2 means ca = 64)
@@ -89,6 +96,12 @@ struct DevTables {
     int* xent_rc = nullptr;       // [E'] the entry's index in the row CSR
     int* sens_ent = nullptr;      // [M][w] row-CSR index of each of the sensor's y taps
     int4* seg = nullptr;          // [Ly][groups1] column range [x, y) and entry range [z, w)
+    // the block spread (split1): per (row, 16-column block) the range of
+    // entries whose exact taps reach into the block, and per entry its exact
+    // first column and its w taps
+    int2* bseg = nullptr;         // [Ly][Lx/16]
+    int* pent_bx = nullptr;       // [E'] first x column (negative for the second copy of a wrapped entry)
+    float* pent_w = nullptr;      // [E'][4 ceil(w/4)] x tap times y tap times sensor factor, from pent_bx on
     int* status = nullptr;        // device flags: NEDNER_FLAG_NONFINITE when an output kernel wrote a non-finite value
 };
 
@@ -148,7 +161,11 @@ namespace nedner {
 cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float2* R, cudaStream_t s, int t0 = 0,
                                    int nt = -1);
 cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s, int t0 = 0,
-                            int nt = -1);
+                            int nt = -1, int rstride = -1, int roff = 0);
+// stage (a) in chunks of tq time samples: block spread into Q, x-FFT into R
+// (both one chunk), y-FFT into Ghat; Q and R hold tq samples
+cudaError_t launch_ned_stage_split(const nedner_plan_s& p, const float* g, float* Q, float2* R, float2* Ghat,
+                                   cudaStream_t s, StageTimer* tm = nullptr);
 cudaError_t launch_ner_lines(const nedner_plan_s& p, const float2* Ghat, float2* V, cudaStream_t s);
 cudaError_t launch_img_yifft(const nedner_plan_s& p, const float2* V, float2* Y, cudaStream_t s);
 cudaError_t launch_img_xc2r(const nedner_plan_s& p, const float2* Y, float* p0, cudaStream_t s, int z0 = 0,

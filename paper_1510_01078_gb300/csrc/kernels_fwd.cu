@@ -2,8 +2,10 @@
 //
 // Data flow (all intermediates complex64, n / qz / qy fastest as noted):
 //   g [M][Nt]
-//     -- ned_spread_xfft -->  R    [nx/2+1][Ly][Nt]   spread along y and x, x-FFT
-//     -- ned_yfft         -->  Ghat [nx/2+1][ny+1][Nt] y-FFT, crop, deconvolve
+//     -- ned_spread_blocks -> Q   [tq/32][Ly][Lx][32] spread along y and x, one chunk of tq time samples
+//     -- ned_xfft         -->  R    [nx/2+1][Ly][tq]   x-FFT, crop, deconvolve (the chunk)
+//     -- ned_yfft         -->  Ghat [nx/2+1][ny+1][Nt] y-FFT, crop, deconvolve (the chunk)
+//   (or, fused, ned_spread_xfft --> R [nx/2+1][Ly][Nt] for every time sample at once)
 //     -- ner_lines        -->  V    [nx/2+1][ny][nz]   NER, Jacobian, z-IFFT
 //     -- img_yifft        -->  Y    [nx/2+1][nz][ny]   y-IFFT
 //     -- img_xc2r         -->  p0   [nz][ny][nx]       x complex-to-real IFFT
@@ -243,6 +245,142 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
 }
 
 // ---------------------------------------------------------------------------
+// Stage (a), part 1 as two kernels over a chunk of tq time samples [t0, t0 + tq).
+//
+// k_ned_spread_blocks: NED spreading (Eq. NED_NUFFT) into the oversampled
+// grid Q [tq/32][Ly][Lx][32] (real; groups of 32 time samples, time fastest).
+// One warp owns one block of 16 columns of one grid row for 64 time samples
+// (two per lane, packed FMAs) and adds every entry (sensor, y tap) of the row
+// whose W x taps reach into the block, from the entry's exact first column on
+// (block_entry); the row's entries are sorted by first column, so a block's
+// entries are one range bseg[row][block].  Entries are staged eight at a time
+// per warp (sensor indices one batch ahead, then first column, taps and
+// samples of g by asynchronous copies while the current batch is added).  The
+// warp then stores its 16 columns (128 contiguous bytes per column and 32
+// samples) and is done: no shared row buffer and no barrier, so warps of dense
+// and sparse blocks do not wait for one another, and many small CTAs keep
+// every SM busy.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int tq, const float* __restrict__ g,
+                                                              const int2* __restrict__ bseg,
+                                                              const int* __restrict__ xent_m,
+                                                              const float* __restrict__ pent_w,
+                                                              const int* __restrict__ pent_bx, float* __restrict__ Q) {
+    constexpr int B = 8, C = 64, NB = 32;
+    constexpr int WQ = (W + 3) / 4;                                 // float4 of taps per entry
+    constexpr int DB = B + B * 4 * WQ;                              // ints + floats before the g block
+    constexpr int dsz = DB + B * C;                                 // one data buffer (4-byte words)
+    extern __shared__ float4 smem4[];
+    const int wpc = blockDim.x >> 5;
+    const int q = threadIdx.x >> 5;
+    const int ln = threadIdx.x & 31;
+    const int nblk = G.Lx >> 4;
+    const int gb = blockIdx.x * wpc + q;                            // (row, block) index
+    const int gy = gb / nblk;
+    const int c0 = (gb - gy * nblk) << 4;
+    const int nc = blockIdx.y * C;                                  // first sample of the warp in the chunk
+    const int2 rg = bseg[gb];
+
+    float2 acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
+
+    int* st_m = reinterpret_cast<int*>(smem4) + (size_t)q * (2 * B + 2 * dsz);   // [2][B]
+    int* st_d = st_m + 2 * B;                                                     // [2][dsz]
+    const int nent = rg.y - rg.x;
+    const int nbt = (nent + B - 1) / B;
+    auto issue_m = [&](int b) {
+        const int e0 = rg.x + b * B, nb_ = min(B, rg.y - e0);
+        if (ln < nb_) cp_async(st_m + (b & 1) * B + ln, xent_m + e0 + ln, 4);
+    };
+    auto issue_data = [&](int b) {
+        const int e0 = rg.x + b * B, nb_ = min(B, rg.y - e0);
+        int* d = st_d + (b & 1) * dsz;
+        const int* mm = st_m + (b & 1) * B;
+        if (ln < nb_) cp_async(d + ln, pent_bx + e0 + ln, 4);
+        const float* wsrc = pent_w + (size_t)e0 * 4 * WQ;
+        for (int i = ln; i < nb_ * WQ; i += 32) cp_async(d + B + 4 * i, wsrc + 4 * i, 16);
+#pragma unroll
+        for (int r = 0; r < B * (C / 4) / 32; ++r) {
+            const int i = ln + 32 * r;
+            const int j = i >> 4, c = i & 15;
+            if (j < nb_) cp_async(d + DB + j * C + 4 * c, g + (size_t)mm[j] * G.Nt + t0 + nc + 4 * c, 16);
+        }
+    };
+    if (nbt > 0) {
+        issue_m(0);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+        issue_data(0);
+        if (nbt > 1) issue_m(1);
+        cp_async_commit();
+    }
+    for (int b = 0; b < nbt; ++b) {
+        cp_async_wait_all();
+        __syncwarp();
+        if (b + 1 < nbt) issue_data(b + 1);
+        if (b + 2 < nbt) issue_m(b + 2);
+        cp_async_commit();
+        const int nbat = min(B, nent - b * B);
+        const int* st_bx = st_d + (b & 1) * dsz;
+        const float4* wst = reinterpret_cast<const float4*>(st_bx + B);
+        const float2* st_g = reinterpret_cast<const float2*>(st_bx + DB);
+#pragma unroll 1
+        for (int j = 0; j < nbat; ++j) {
+            float4 wa[WQ];
+#pragma unroll
+            for (int k4 = 0; k4 < WQ; ++k4) wa[k4] = wst[j * WQ + k4];
+            block_entry<W>(acc, st_bx[j], c0, wa, st_g[j * NB + ln]);
+        }
+        __syncwarp();
+    }
+    // Q is [tq/32][Ly][Lx][32]: lanes 0-15 hold the first 32 samples of the
+    // warp's 64, lanes 16-31 the next 32; a column's 32 samples are 128
+    // contiguous bytes, and the 16 columns of the block 2 KB
+    float2* out = reinterpret_cast<float2*>(Q + ((((size_t)(nc >> 5) + (ln >> 4)) * G.Ly + gy) * G.Lx + c0) * 32) +
+                  (ln & 15);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) out[16 * k] = acc[k];
+}
+
+// ---------------------------------------------------------------------------
+// k_ned_xfft: the x-FFT of the chunk.  One CTA per (grid row gy, 2 NBX time
+// samples of the chunk): the row of Q is loaded as NBX complex columns (time
+// samples 2b, 2b+1 packed as real and imaginary part) into a padded buffer by
+// asynchronous copies (all in flight at once), transformed in place along x
+// (PER values per thread), and jx = 0..nx/2 is written to R (the chunk's
+// [nx/2+1][Ly][tq]), divided by phihat(jx/Lx).  With NBX = 16 the CTA's part
+// of Q is one contiguous block of Lx x 32 samples.
+// ---------------------------------------------------------------------------
+template <int PER>
+__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_xfft(Geo G, int tq, int nbx, const float* __restrict__ Q,
+                                                                    const float* __restrict__ deconv_x,
+                                                                    const float2* __restrict__ tw,
+                                                                    float2* __restrict__ R) {
+    extern __shared__ float4 smem4[];
+    float2* Z = reinterpret_cast<float2*>(smem4);                   // [Lx][nbx], padded
+    const int gy = blockIdx.x;
+    const int nc = blockIdx.y * 2 * nbx;                             // first sample in the chunk
+    const int lnb = ilog2(nbx);
+    // samples nc .. nc + 2 nbx of the row: group nc / 32, offset nc % 32
+    const float2* src = reinterpret_cast<const float2*>(Q + ((size_t)(nc >> 5) * G.Ly + gy) * G.Lx * 32 + (nc & 31));
+    for (int it = threadIdx.x; it < (G.Lx << lnb); it += blockDim.x) {
+        const int gx = it >> lnb, b = it & (nbx - 1);
+        cp_async(&Z[padx(it)], src + (size_t)gx * 16 + b, 8);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    const bool fold = (ilog2(G.Lx) & 3) == 1;
+    block_fft_ip<PER>(Z, G.Lx, nbx, -1, tw, fold);
+    Geo Gc = G;
+    Gc.Nt = tq;                                                     // R holds the chunk's tq samples
+    for (int it = threadIdx.x; it < (G.nxh << lnb); it += blockDim.x)
+        spread_output(Gc, Z, lnb, it & (nbx - 1), it >> lnb, fold, deconv_x, tw, gy, nc, R);
+}
+
+// ---------------------------------------------------------------------------
 // Stage (a), part 2: y-FFT of length Ly for one jx and C time samples; keeps
 // jy = -ny/2..ny/2 (both Nyquist rows) divided by phihat(jy/Ly).  The FFT
 // runs in place in a padded buffer, Ly * C <= 256 PER (PER values per thread);
@@ -250,8 +388,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
 // blockIdx.x runs over the time chunks, so consecutive CTAs read neighbouring
 // pieces of the same rows.
 // ---------------------------------------------------------------------------
+// R holds time samples [roff, roff + rstride) (the whole record, or one chunk).
 template <int PER>
 __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int C, int yb, const float2* __restrict__ R,
+                                                     int rstride, int roff,
                                                      const float* __restrict__ deconv_y,
                                                      const float2* __restrict__ tw, float2* __restrict__ Ghat) {
     extern __shared__ float4 smem4[];
@@ -259,12 +399,13 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int 
     const int jx = blockIdx.y;
     const int n0 = (yb + blockIdx.x) * C;
     const int lc = ilog2(C);
-#pragma unroll 8
     for (int it = threadIdx.x; it < G.Ly * C; it += 256) {
         const int gy = it >> lc;
         const int c = it & (C - 1);
-        A[padx(it)] = R[((size_t)jx * G.Ly + gy) * G.Nt + n0 + c];
+        cp_async(&A[padx(it)], &R[((size_t)jx * G.Ly + gy) * rstride + n0 - roff + c], 8);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     const bool fold = (ilog2(G.Ly) & 3) == 1;
     block_fft_ip<PER>(A, G.Ly, C, -1, tw, fold);
     const int items = G.nyp * C;
@@ -504,6 +645,13 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     NEDNER_ATTR_SPREAD2(8) NEDNER_ATTR_SPREAD2(12) NEDNER_ATTR_SPREAD2(16) NEDNER_ATTR_SPREAD2(20)
 #undef NEDNER_ATTR_SPREAD2
 #undef NEDNER_ATTR_SPREAD
+#define NEDNER_ATTR_BLOCKS(W) \
+    if ((e = cudaFuncSetAttribute(k_ned_spread_blocks<W>, (cudaFuncAttribute)a, (int)p.ch.smem_s))) return e;
+    NEDNER_ATTR_BLOCKS(4) NEDNER_ATTR_BLOCKS(6) NEDNER_ATTR_BLOCKS(8) NEDNER_ATTR_BLOCKS(10) NEDNER_ATTR_BLOCKS(12)
+    NEDNER_ATTR_BLOCKS(14) NEDNER_ATTR_BLOCKS(16)
+#undef NEDNER_ATTR_BLOCKS
+    if ((e = cudaFuncSetAttribute(k_ned_xfft<16>, (cudaFuncAttribute)a, (int)p.ch.smem_x))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_xfft<32>, (cudaFuncAttribute)a, (int)p.ch.smem_x))) return e;
     if ((e = cudaFuncSetAttribute(k_ned_yfft<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2f))) return e;
     if ((e = cudaFuncSetAttribute(k_ned_yfft<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2f))) return e;
 #define NEDNER_ATTR_NER(W, D)                                                                                   \
@@ -548,16 +696,66 @@ cudaError_t launch_ned_spread_xfft(const nedner_plan_s& p, const float* g, float
     return cudaGetLastError();
 }
 
-cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s, int t0, int nt) {
+cudaError_t launch_ned_yfft(const nedner_plan_s& p, const float2* R, float2* Ghat, cudaStream_t s, int t0, int nt,
+                            int rstride, int roff) {
     const Geo& G = p.geo;
     if (nt < 0) nt = G.Nt - t0;
+    if (rstride < 0) rstride = G.Nt;
     const int yb = t0 / p.ch.c2f;
     dim3 grid(nt / p.ch.c2f, G.nxh);
     if ((long)G.Ly * p.ch.c2f <= 16L * 256)
-        k_ned_yfft<16><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, yb, R, p.t.deconv_y, p.t.tw, Ghat);
+        k_ned_yfft<16><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, yb, R, rstride, roff, p.t.deconv_y, p.t.tw, Ghat);
     else
-        k_ned_yfft<32><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, yb, R, p.t.deconv_y, p.t.tw, Ghat);
+        k_ned_yfft<32><<<grid, 256, p.ch.smem2f, s>>>(G, p.ch.c2f, yb, R, rstride, roff, p.t.deconv_y, p.t.tw, Ghat);
     return cudaGetLastError();
+}
+
+cudaError_t launch_ned_spread_blocks(const nedner_plan_s& p, const float* g, float* Q, int t0, cudaStream_t s) {
+    const Geo& G = p.geo;
+    const int tq = p.ch.tq, wpc = p.ch.wpc_s;
+    const dim3 grid(G.Ly * (G.Lx / 16) / wpc, tq / 64);
+#define NEDNER_BLOCKS(W)                                                                                 \
+    k_ned_spread_blocks<W><<<grid, 32 * wpc, p.ch.smem_s, s>>>(G, t0, tq, g, p.t.bseg, p.t.xent_m, p.t.pent_w, \
+                                                               p.t.pent_bx, Q)
+    switch (G.w) {
+        case 4: NEDNER_BLOCKS(4); break;
+        case 6: NEDNER_BLOCKS(6); break;
+        case 8: NEDNER_BLOCKS(8); break;
+        case 10: NEDNER_BLOCKS(10); break;
+        case 12: NEDNER_BLOCKS(12); break;
+        case 14: NEDNER_BLOCKS(14); break;
+        default: NEDNER_BLOCKS(16); break;
+    }
+#undef NEDNER_BLOCKS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ned_xfft(const nedner_plan_s& p, const float* Q, float2* R, cudaStream_t s) {
+    const Geo& G = p.geo;
+    const dim3 grid(G.Ly, p.ch.tq / (2 * p.ch.nbx));
+    if (p.ch.perx <= 16)
+        k_ned_xfft<16><<<grid, p.ch.thx, p.ch.smem_x, s>>>(G, p.ch.tq, p.ch.nbx, Q, p.t.deconv_x, p.t.tw, R);
+    else
+        k_ned_xfft<32><<<grid, p.ch.thx, p.ch.smem_x, s>>>(G, p.ch.tq, p.ch.nbx, Q, p.t.deconv_x, p.t.tw, R);
+    return cudaGetLastError();
+}
+
+// Stage (a) as spread, x-FFT and y-FFT per chunk of tq time samples, Q and R
+// holding one chunk; a timer, if given, is marked after each launch (stages 0,
+// 1 and 2: spread, x-FFT, y-FFT, summed over the chunks).
+cudaError_t launch_ned_stage_split(const nedner_plan_s& p, const float* g, float* Q, float2* R, float2* Ghat,
+                                   cudaStream_t s, StageTimer* tm) {
+    const Geo& G = p.geo;
+    cudaError_t e = cudaSuccess;
+    for (int t0 = 0; t0 < G.Nt && !e; t0 += p.ch.tq) {
+        if ((e = launch_ned_spread_blocks(p, g, Q, t0, s))) break;
+        stage_mark(tm, 0);
+        if ((e = launch_ned_xfft(p, Q, R, s))) break;
+        stage_mark(tm, 1);
+        if ((e = launch_ned_yfft(p, R, Ghat, s, t0, p.ch.tq, p.ch.tq, t0))) break;
+        stage_mark(tm, 2);
+    }
+    return e;
 }
 
 cudaError_t launch_ner_lines(const nedner_plan_s& p, const float2* Ghat, float2* V, cudaStream_t s) {

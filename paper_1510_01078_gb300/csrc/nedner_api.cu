@@ -83,6 +83,8 @@ void free_sensor_tables(DevTables& t) {
     cudaFree(t.xrow_ptr); cudaFree(t.xent_m); cudaFree(t.xent_wx); cudaFree(t.xent_bx); cudaFree(t.seg);
     cudaFree(t.xent_gx); cudaFree(t.xent_gy); cudaFree(t.xrow_first);
     cudaFree(t.xent_rc); cudaFree(t.sens_ent);
+    cudaFree(t.bseg); cudaFree(t.pent_bx); cudaFree(t.pent_w);
+    t.bseg = nullptr; t.pent_bx = nullptr; t.pent_w = nullptr;
     t.sens_bx = t.sens_by = nullptr;
     t.sens_wx = t.sens_wy = t.sens_dwx = t.sens_dwy = t.sens_fac = nullptr;
     t.row_ptr = t.row_m = nullptr;
@@ -299,6 +301,13 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     std::vector<int> xent_m, xent_bx, xent_e;
     std::vector<float> xent_wx, xent_gx, xent_gy;
     std::vector<int4> seg((size_t)G.Ly * C.groups1);
+    // block spread (split1): exact first column and w taps per entry, and per
+    // (row, 16-column block) the range of entries reaching into the block
+    const int PW = (w + 3) / 4 * 4;
+    const int nblk = G.Lx / 16;
+    std::vector<int> pent_bx;
+    std::vector<float> pent_w;
+    std::vector<int2> bseg(C.split1 ? (size_t)G.Ly * nblk : 0);
     std::vector<XE> tmp;
     for (int r = 0; r < G.Ly; ++r) {
         tmp.clear();
@@ -316,6 +325,10 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
             xent_m.push_back(x.m);
             xent_bx.push_back(bx4);
             xent_e.push_back(x.e);
+            if (C.split1) {
+                pent_bx.push_back(x.bx);
+                for (int k = 0; k < PW; ++k) pent_w.push_back(k < w ? x.w * wx[(size_t)x.m * w + k] : 0.f);
+            }
             for (int k = 0; k < WT; ++k) {
                 const int t = k - off;
                 const bool in = t >= 0 && t < w;
@@ -327,6 +340,16 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
         }
         xrow_ptr[r + 1] = (int)xent_m.size();
         const int Er = (int)tmp.size();
+        if (C.split1) {
+            // entries of block b: first column in [16 b - w + 1, 16 b + 16)
+            int lo = 0, hi = 0;
+            for (int b = 0; b < nblk; ++b) {
+                while (lo < Er && tmp[lo].bx < 16 * b - w + 1) ++lo;
+                if (hi < lo) hi = lo;
+                while (hi < Er && tmp[hi].bx < 16 * b + 16) ++hi;
+                bseg[(size_t)r * nblk + b] = make_int2(base + lo, base + hi);
+            }
+        }
         // cut the columns so that each lane group's sweep costs about the same:
         // an entry costs about as much as 1.5 columns of window sliding
         std::vector<int> cut(C.groups1 + 1);
@@ -389,6 +412,9 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = upload(&p.t.xent_rc, xent_e, s);
     if (!e) e = upload(&p.t.sens_ent, sens_ent, s);
     if (!e) e = upload(&p.t.seg, seg, s);
+    if (!e) e = upload(&p.t.bseg, bseg, s);
+    if (!e) e = upload(&p.t.pent_bx, pent_bx, s);
+    if (!e) e = upload(&p.t.pent_w, pent_w, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e == cudaErrorMemoryAllocation) return NEDNER_ENOMEM;
     return e ? NEDNER_ECUDA : NEDNER_OK;
@@ -445,9 +471,35 @@ int pow2_floor(long v) {
     return r;
 }
 
+// preferred time samples per chunk of the split stage (a): the whole record
+// where the workspace allows (fewer, fuller launches); a limit on the
+// workspace makes the chunks shorter
+constexpr int kChunkPref = 4096;
+
+// bytes of the split stage's per-chunk buffers (Q, then R) for tq samples
+size_t split_chunk_bytes(const Geo& G, int tq) {
+    const size_t q = ((size_t)G.Ly * G.Lx * tq * 4 + 255) / 256 * 256;
+    return q + (size_t)G.nxh * G.Ly * tq * 8;
+}
+
 void choose_chunks(nedner_plan_s& p) {
     Geo& G = p.geo;
     Chunks& c = p.ch;
+    // split stage (a): block spread (4 warps of 16 columns per CTA), x-FFT of
+    // nbx complex columns per CTA (32 values per thread when Lx nbx = 8192)
+    c.split1 = (G.Nt >= 64 && G.Lx >= 64) ? 1 : 0;
+    c.wpc_s = 4;
+    {
+        // per warp, double-buffered batches of 8 entries: sensor indices, and
+        // first columns, taps and 64 samples of g
+        const long pw = (G.w + 3) / 4 * 4;
+        c.smem_s = (size_t)c.wpc_s * (2 * 8 + 2 * (8 + 8 * pw + 8 * 64)) * 4;
+    }
+    c.nbx = (int)std::min<long>(16, 8192 / G.Lx);
+    c.perx = ((long)G.Lx * c.nbx >= 8192) ? 32 : 16;
+    c.thx = (int)((long)G.Lx * c.nbx / c.perx);
+    c.smem_x = (size_t)((padded((long)G.Lx * c.nbx) + 1) & ~1L) * 8;
+    c.tq = std::min(G.Nt, kChunkPref);
     // spread + x-FFT: lane groups of a full warp (32 time samples) while the
     // row fits in 128 KB of shared memory, smaller groups beyond
     c.c1 = std::min<long>(32, std::max<long>(2, pow2_floor((128L * 1024) / (8L * G.Lx))));
@@ -523,6 +575,33 @@ void choose_chunks(nedner_plan_s& p) {
 
 static nedner_status run(cudaError_t e) {
     return e == cudaSuccess ? NEDNER_OK : NEDNER_ECUDA;
+}
+
+// Stage (a) of the forward path into Ghat (region B), with the plan's
+// workspace region A as scratch: the tensor-core stage, the split stage (block
+// spread, x-FFT and y-FFT per chunk of time samples, the chunk's Q and R in
+// region A) or the fused spread + x-FFT followed by the y-FFT.  A timer, if
+// given, gets stages 0 (spread), 1 (x-FFT) and 2 (y-FFT); the tensor-core
+// stage and the fused spread count as stage 0.
+static cudaError_t launch_stage_a(const nedner_plan_s& p, const float* g, float2* Ghat, cudaStream_t s,
+                                  StageTimer* tm = nullptr) {
+    cudaError_t e;
+    if (p.tp.enabled) {
+        e = launch_tp_ned(p, g, Ghat, s);
+        stage_mark(tm, 0);
+        return e;
+    }
+    if (p.ch.split1) {
+        float* Q = (float*)p.ws;
+        float2* R = (float2*)((char*)p.ws + ((size_t)p.geo.Ly * p.geo.Lx * p.ch.tq * 4 + 255) / 256 * 256);
+        return launch_ned_stage_split(p, g, Q, R, Ghat, s, tm);
+    }
+    float2* A = (float2*)p.ws;
+    if ((e = launch_ned_spread_xfft(p, g, A, s))) return e;
+    stage_mark(tm, 0);
+    e = launch_ned_yfft(p, A, Ghat, s);
+    stage_mark(tm, 2);
+    return e;
 }
 
 extern "C" {
@@ -612,7 +691,18 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     // time sample of a pass) and the gradient's per-entry sums.  Passes are as
     // long as fit in max(Ghat / Y, 256 MB), or, under a workspace limit, in what
     // the limit leaves beside region A.
-    p->region_a = (std::max(r_bytes, v_bytes) + 255) / 256 * 256;
+    // The split stage (a) keeps one chunk of tq time samples of the oversampled
+    // grid Q and of R in region A: the whole record by default; under a
+    // workspace limit the chunks shrink (to 64 samples at least) until the
+    // plan fits, so the forward streams over time instead of failing.
+    const size_t base_a = (std::max(r_bytes, v_bytes) + 255) / 256 * 256;
+    auto region_a_for = [&](int tq) {
+        return p->ch.split1 ? std::max(base_a, (split_chunk_bytes(G, tq) + 255) / 256 * 256) : base_a;
+    };
+    const size_t base_b = std::max(gh_bytes, v_bytes);
+    if (p->ch.split1 && o.max_workspace_bytes)
+        while (p->ch.tq > 64 && region_a_for(p->ch.tq) + base_b > o.max_workspace_bytes) p->ch.tq /= 2;
+    p->region_a = region_a_for(p->ch.tq);
     const size_t ents = (size_t)M * G.w;
     size_t cap = std::max(gh_bytes, v_bytes);
     size_t extra = (size_t)256 << 20;
@@ -666,12 +756,7 @@ nedner_status nedner_forward(nedner_plan_t p, const float* g, float* p0, void* s
     float2* A = (float2*)p->ws;
     float2* B = (float2*)((char*)p->ws + p->region_a);
     cudaError_t e;
-    if (p->tp.enabled) {
-        if ((e = launch_tp_ned(*p, g, B, s))) return run(e);
-    } else {
-        if ((e = launch_ned_spread_xfft(*p, g, A, s))) return run(e);
-        if ((e = launch_ned_yfft(*p, A, B, s))) return run(e);
-    }
+    if ((e = launch_stage_a(*p, g, B, s))) return run(e);
     if ((e = launch_ner_lines(*p, B, A, s))) return run(e);
     if ((e = launch_img_yifft(*p, A, B, s))) return run(e);
     return run(launch_img_xc2r(*p, B, p0, s));
@@ -684,42 +769,24 @@ nedner_status nedner_forward_profiled(nedner_plan_t p, const float* g, float* p0
     cudaStream_t s = (cudaStream_t)stream;
     float2* A = (float2*)p->ws;
     float2* B = (float2*)((char*)p->ws + p->region_a);
-    cudaEvent_t ev[NEDNER_FORWARD_KERNELS + 1];
-    int made = 0;
-    cudaError_t e = cudaSuccess;
-    for (; made <= NEDNER_FORWARD_KERNELS && !e; ++made) e = cudaEventCreate(&ev[made]);
-    if (!e) e = cudaEventRecord(ev[0], s);
-    if (p->tp.enabled) {
-        // tensor-product NED: all of stage (a) is reported as the first kernel group
-        if (!e) e = launch_tp_ned(*p, g, B, s);
-        if (!e) e = cudaEventRecord(ev[1], s);
-    } else {
-        if (!e) e = launch_ned_spread_xfft(*p, g, A, s);
-        if (!e) e = cudaEventRecord(ev[1], s);
-        if (!e) e = launch_ned_yfft(*p, A, B, s);
-    }
-    if (!e) e = cudaEventRecord(ev[2], s);
+    StageTimer tm(s);
+    tm.mark(-1);
+    cudaError_t e = launch_stage_a(*p, g, B, s, &tm);
     if (!e) e = launch_ner_lines(*p, B, A, s);
-    if (!e) e = cudaEventRecord(ev[3], s);
+    tm.mark(3);
     if (!e) e = launch_img_yifft(*p, A, B, s);
-    if (!e) e = cudaEventRecord(ev[4], s);
+    tm.mark(4);
     if (!e) e = launch_img_xc2r(*p, B, p0, s);
-    if (!e) e = cudaEventRecord(ev[5], s);
-    if (!e) e = cudaEventSynchronize(ev[5]);
-    for (int k = 0; k < NEDNER_FORWARD_KERNELS && !e; ++k) e = cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]);
-    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
-    return run(e);
+    tm.mark(5);
+    cudaError_t f = tm.finish(stage_ms, NEDNER_FORWARD_KERNELS);
+    return run(e ? e : f);
 }
 
 nedner_status nedner_ned_stage(nedner_plan_t p, const float* g, void* Ghat, void* stream) {
     if (!p || !Ghat || (p->M > 0 && !g)) return NEDNER_EINVAL;
     if (((uintptr_t)g & 15) != 0 || ((uintptr_t)Ghat & 15) != 0) return NEDNER_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    float2* A = (float2*)p->ws;
-    cudaError_t e;
-    if (p->tp.enabled) return run(launch_tp_ned(*p, g, (float2*)Ghat, s));
-    if ((e = launch_ned_spread_xfft(*p, g, A, s))) return run(e);
-    return run(launch_ned_yfft(*p, A, (float2*)Ghat, s));
+    return run(launch_stage_a(*p, g, (float2*)Ghat, s));
 }
 
 // Transposed stages shared by the adjoint and the position gradient:
@@ -853,7 +920,8 @@ int nedner_work_split(int nx, int ny, int nz, int Nt, int w, int64_t* out, int n
     const int64_t v[] = {c.c1, c.c2f, c.c4, c.c5, c.groups1, c.threads1, c.per1, c.tpl1, c.ca, c.per_adj,
                          c.tpl_adj, c.threads_adj, c.lpc, c.threads3, (int64_t)c.smem1, (int64_t)c.smem2f,
                          (int64_t)c.smem3, (int64_t)c.smem4, (int64_t)c.smem5, (int64_t)c.smem_adj,
-                         (int64_t)c.smem_grad};
+                         (int64_t)c.smem_grad, c.split1, c.tq, c.wpc_s, c.nbx, c.thx, c.perx, (int64_t)c.smem_s,
+                         (int64_t)c.smem_x};
     const int n = (int)(sizeof(v) / sizeof(v[0]));
     for (int i = 0; i < n && i < nout; ++i) out[i] = v[i];
     return n;
@@ -894,12 +962,7 @@ nedner_status nedner_forward_host(nedner_plan_t p, const float* g_host, float* p
             return run(e);
         if ((e = cudaEventRecord(ev[1 + i], cs[i])) || (e = cudaStreamWaitEvent(s, ev[1 + i], 0))) return run(e);
     }
-    if (p->tp.enabled) {
-        if ((e = launch_tp_ned(*p, p->host_g, B, s))) return run(e);
-    } else {
-        if ((e = launch_ned_spread_xfft(*p, p->host_g, A, s))) return run(e);
-        if ((e = launch_ned_yfft(*p, A, B, s))) return run(e);
-    }
+    if ((e = launch_stage_a(*p, p->host_g, B, s))) return run(e);
     if ((e = launch_ner_lines(*p, B, A, s))) return run(e);
     if ((e = launch_img_yifft(*p, A, B, s))) return run(e);
     // p0 in NCS blocks of depth planes, each downloaded as soon as it is written

@@ -102,6 +102,45 @@ __device__ __forceinline__ void sweep_entry2(float2 (&acc)[2 * WT], float2* Z, i
     else if (WT >= 20 && d == 5) add_taps2<WT, (WT >= 20 ? 20 : 0)>(acc, wv, g2);
 }
 
+// Block spread (k_ned_spread_blocks): one warp accumulates one block of 16
+// columns [c0, c0 + 16) of a grid row for 64 time samples (two per lane, as
+// above) over every entry whose W taps reach into the block.  The taps start at
+// the entry's exact first column bx (no alignment padding); with d = bx - c0 in
+// [1 - W, 15] only taps k with 0 <= d + k < 16 land in the block, so every FMA
+// adds to a column of the block and every entry's W taps are applied exactly
+// once over the blocks it touches.
+template <int W, int D>
+__device__ __forceinline__ void add_taps_block(float2 (&acc)[16], const float4 (&wv)[(W + 3) / 4], float2 g2) {
+    constexpr int k0 = D < 0 ? -D : 0;
+    constexpr int k1 = (16 - D) < W ? (16 - D) : W;
+#pragma unroll
+    for (int k = k0; k < k1; ++k) {
+        const float4 q = wv[k >> 2];
+        const float t = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
+        acc[D + k] = __ffma2_rn(make_float2(t, t), g2, acc[D + k]);
+    }
+}
+
+// adds one entry (first column bx) to the block starting at column c0
+template <int W>
+__device__ __forceinline__ void block_entry(float2 (&acc)[16], int bx, int c0, const float4 (&wv)[(W + 3) / 4],
+                                            float2 g2) {
+#define NEDNER_BLOCK_CASE(I) \
+    case I: add_taps_block<W, (I) - (W - 1)>(acc, wv, g2); break;
+    switch (bx - c0 + (W - 1)) {
+        NEDNER_BLOCK_CASE(0) NEDNER_BLOCK_CASE(1) NEDNER_BLOCK_CASE(2) NEDNER_BLOCK_CASE(3)
+        NEDNER_BLOCK_CASE(4) NEDNER_BLOCK_CASE(5) NEDNER_BLOCK_CASE(6) NEDNER_BLOCK_CASE(7)
+        NEDNER_BLOCK_CASE(8) NEDNER_BLOCK_CASE(9) NEDNER_BLOCK_CASE(10) NEDNER_BLOCK_CASE(11)
+        NEDNER_BLOCK_CASE(12) NEDNER_BLOCK_CASE(13) NEDNER_BLOCK_CASE(14) NEDNER_BLOCK_CASE(15)
+        NEDNER_BLOCK_CASE(16) NEDNER_BLOCK_CASE(17) NEDNER_BLOCK_CASE(18) NEDNER_BLOCK_CASE(19)
+        NEDNER_BLOCK_CASE(20) NEDNER_BLOCK_CASE(21) NEDNER_BLOCK_CASE(22) NEDNER_BLOCK_CASE(23)
+        NEDNER_BLOCK_CASE(24) NEDNER_BLOCK_CASE(25) NEDNER_BLOCK_CASE(26) NEDNER_BLOCK_CASE(27)
+        NEDNER_BLOCK_CASE(28) NEDNER_BLOCK_CASE(29) NEDNER_BLOCK_CASE(30)
+        default: break;
+    }
+#undef NEDNER_BLOCK_CASE
+}
+
 // Output step of the spread stage: jx = 0..nx/2 of the row, divided by
 // phihat(jx/Lx), for complex column b (real time samples 2b, 2b+1 packed as
 // real and imaginary part), written as the two time samples n0 + 2b, n0 + 2b + 1

@@ -222,7 +222,7 @@ class Plan:
         _check(st, "nedner_forward_host")
         return out
 
-    FORWARD_KERNELS = ("ned_spread_xfft", "ned_yfft", "ner_lines", "img_yifft", "img_xc2r")
+    FORWARD_KERNELS = ("ned_spread", "ned_xfft", "ned_yfft", "ner_lines", "img_yifft", "img_xc2r")
 
     def forward_profiled(self, g, out, stream=None):
         """forward() that also returns each kernel's device time (ms), synchronously."""
@@ -390,7 +390,7 @@ def reconstruct(plan: Plan, g, sensor_xy=None):
 
 WORK_SPLIT_FIELDS = ("c1", "c2f", "c4", "c5", "groups1", "threads1", "per1", "tpl1", "ca", "per_adj", "tpl_adj",
                      "threads_adj", "lpc", "threads3", "smem1", "smem2f", "smem3", "smem4", "smem5", "smem_adj",
-                     "smem_grad")
+                     "smem_grad", "split1", "tq", "wpc_s", "nbx", "thx", "perx", "smem_s", "smem_x")
 
 
 def work_split(nx: int, ny: int, nz: int, Nt: int, w: int = 12) -> dict:

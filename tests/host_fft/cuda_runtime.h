@@ -11,6 +11,9 @@ struct float2 {
 struct float4 {
     float x, y, z, w;
 };
+struct int2 {
+    int x, y;
+};
 struct int4 {
     int x, y, z, w;
 };

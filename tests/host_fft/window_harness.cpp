@@ -199,3 +199,41 @@ extern "C" int host_spread_output(int Lx, int nb, int fold, const float* Zin, co
     }
     return 0;
 }
+
+// The block spread (block_entry): the 32 lanes of a warp accumulate the
+// 16-column block [c0, c0 + 16) over the entries whose W taps (from their
+// exact first column bx, taps [nent][4 ceil(W/4)]) reach into it; g is
+// [nent][64].  out: [16][64] (column, time sample).
+template <int W>
+static void block_sweep(int c0, int nent, const int* bx, const float* taps, const float* g, float* out) {
+    constexpr int WQ = (W + 3) / 4;
+    for (int ln = 0; ln < 32; ++ln) {
+        float2 acc[16];
+        for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
+        for (int e = 0; e < nent; ++e) {
+            float4 wv[WQ];
+            for (int k4 = 0; k4 < WQ; ++k4)
+                wv[k4] = float4{taps[e * 4 * WQ + 4 * k4], taps[e * 4 * WQ + 4 * k4 + 1],
+                                taps[e * 4 * WQ + 4 * k4 + 2], taps[e * 4 * WQ + 4 * k4 + 3]};
+            block_entry<W>(acc, bx[e], c0, wv, make_float2(g[e * 64 + 2 * ln], g[e * 64 + 2 * ln + 1]));
+        }
+        for (int k = 0; k < 16; ++k) {
+            out[k * 64 + 2 * ln] = acc[k].x;
+            out[k * 64 + 2 * ln + 1] = acc[k].y;
+        }
+    }
+}
+
+extern "C" int host_block_sweep(int W, int c0, int nent, const int* bx, const float* taps, const float* g,
+                                float* out) {
+    switch (W) {
+        case 4: block_sweep<4>(c0, nent, bx, taps, g, out); return 0;
+        case 6: block_sweep<6>(c0, nent, bx, taps, g, out); return 0;
+        case 8: block_sweep<8>(c0, nent, bx, taps, g, out); return 0;
+        case 10: block_sweep<10>(c0, nent, bx, taps, g, out); return 0;
+        case 12: block_sweep<12>(c0, nent, bx, taps, g, out); return 0;
+        case 14: block_sweep<14>(c0, nent, bx, taps, g, out); return 0;
+        case 16: block_sweep<16>(c0, nent, bx, taps, g, out); return 0;
+    }
+    return -1;
+}

@@ -216,3 +216,26 @@ def test_forward_host_small_and_ragged(nd):
     torch.cuda.synchronize()
     plan.close()
     check(out.numpy(), oracle.forward(problem(case), g), TOL)
+
+
+def test_forward_streams_in_time_chunks_under_a_workspace_limit(nd):
+    """Under a workspace limit the split stage (a) runs in chunks of time
+    samples (the oversampled grid is held for one chunk at a time) instead of
+    failing.  Each time sample's arithmetic is the same in any chunking, so the
+    result equals the unlimited plan's bit for bit, and the oracle's."""
+    case = inputs.make_config(1, with_data=False)           # 64x64 sensors, Nt 512, 128x128x256
+    rng = np.random.default_rng(78)
+    g = rng.standard_normal((case["sensor_xy"].shape[0], case["Nt"])).astype(np.float32)
+    full = nd.plan_from_config(case)
+    lim = nd.plan_from_config(case, max_workspace_bytes=150 << 20)
+    assert lim.workspace_bytes <= 150 << 20 < full.workspace_bytes
+    x = torch.as_tensor(g, device="cuda")
+    a = full.forward(x).cpu().numpy()
+    b = lim.forward(x).cpu().numpy()
+    full.close(); lim.close()
+    assert np.array_equal(a, b)
+    small = inputs.small_case(32, 32, 32, 300, 256, seed=79, layout="disc")
+    plan = nd.plan_from_config(small, max_workspace_bytes=6 << 20)          # two chunks of 128 samples
+    got = plan.forward(torch.as_tensor(small["g"], dtype=torch.float32, device="cuda")).cpu().numpy()
+    plan.close()
+    check(got, oracle.forward(problem(small), small["g"]), TOL)

@@ -185,3 +185,34 @@ def test_spread_output_step(lib, Lx, nb, fold):
     got = out[..., 0] + 1j * out[..., 1]
     want = np.fft.fft(x, axis=0)[:nxh] * dec[:, None]
     assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-6
+
+
+@pytest.mark.parametrize("w", [4, 6, 8, 10, 12, 14, 16])
+def test_block_spread_accumulates_exact_taps(lib, w):
+    """The block spread's accumulation (block_entry in csrc/spread_window.cuh):
+    a warp's 16-column block [c0, c0 + 16) gets, from every entry whose w taps
+    start anywhere in [c0 - w + 1, c0 + 15], exactly the taps that land in the
+    block (all w of them for entries inside, the overlapping part at both
+    edges), against a direct FP64 sum; also for a block at a negative first
+    column (the second copy of a wrapped entry) and an empty entry list."""
+    I, F = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)
+    lib.host_block_sweep.argtypes = [ctypes.c_int] * 3 + [I, F, F, F]
+    PW = (w + 3) // 4 * 4
+    rng = np.random.default_rng(100 + w)
+    for c0, n in [(0, 60), (496, 40), (-16, 9), (64, 0), (240, 200)]:
+        bx = np.sort(rng.integers(c0 - w + 1, c0 + 16, n)).astype(np.int32)
+        bx[:min(n, 2)] = c0 - w + 1                        # entries touching the block with one tap
+        bx[-min(n, 2):] = c0 + 15 if n else bx[-min(n, 2):]
+        taps = np.zeros((n, PW), np.float32)
+        taps[:, :w] = rng.uniform(0.1, 1.0, (n, w))
+        g = rng.standard_normal((n, 64)).astype(np.float32)
+        out = np.empty((16, 64), np.float32)
+        assert lib.host_block_sweep(w, c0, n, bx.ctypes.data_as(I), taps.ctypes.data_as(F), g.ctypes.data_as(F),
+                                    out.ctypes.data_as(F)) == 0
+        want = np.zeros((16, 64))
+        for e in range(n):
+            for k in range(w):
+                col = int(bx[e]) + k - c0
+                if 0 <= col < 16:
+                    want[col] += float(taps[e, k]) * g[e].astype(np.float64)
+        np.testing.assert_allclose(out, want, rtol=0, atol=2e-5 * max(1.0, np.abs(want).max()))

@@ -41,6 +41,14 @@ def check(nx, ny, nz, Nt, s):
         need(s["groups1"] * s["c1"] == 256, "spread: lane groups fill the CTA")
         need(s["per1"] in (16, 32) and Lx * s["c1"] // 2 <= s["per1"] * 256, "spread: row FFT fits")
     need(s["smem1"] <= SMEM_MAX, "spread: shared memory")
+    # split stage (a): block spread over 16-column blocks, x-FFT of nbx complex
+    # columns per CTA, chunks of tq samples dividing Nt and the y-FFT's chunk
+    if s["split1"]:
+        need(Nt >= 64 and Lx >= 64 and (Lx // 16) % s["wpc_s"] == 0, "block spread: whole CTAs of 16-column blocks")
+        need(s["tq"] % 64 == 0 and Nt % s["tq"] == 0 and s["tq"] % s["c2f"] == 0, "split: chunk of time samples")
+        need(s["tq"] % (2 * s["nbx"]) == 0, "x-FFT: whole CTAs per chunk")
+        need(Lx * s["nbx"] == s["perx"] * s["thx"] and s["perx"] in (16, 32) and s["thx"] <= 256, "x-FFT: fits")
+        need(s["smem_s"] <= SMEM_MAX and s["smem_x"] <= SMEM_MAX, "split: shared memory")
     # y-FFT (values per thread 16 or 32) and its transpose (16)
     need(Nt % s["c2f"] == 0 and Ly * s["c2f"] <= 16 * 256, "y-FFT: column FFT fits")
     need(s["smem2f"] <= SMEM_MAX, "y-FFT: shared memory")
@@ -87,3 +95,5 @@ def test_known_splits(nd):
     assert (c2["tpl1"], c2["c1"], c2["threads1"], c2["lpc"], c2["tpl_adj"]) == (2, 64, 256, 4, 2)
     c3 = nd.work_split(256, 256, 512, 2048, 12)
     assert (c3["tpl1"], c3["threads1"], c3["lpc"], c3["threads_adj"], c3["c4"], c3["c5"]) == (2, 512, 1, 512, 8, 16)
+    assert (c3["split1"], c3["tq"], c3["nbx"], c3["thx"], c3["perx"]) == (1, 2048, 16, 256, 32)
+    assert (c2["split1"], c2["nbx"], c2["thx"], c2["perx"]) == (1, 16, 256, 16)
