@@ -296,7 +296,8 @@ size_t nedner_workspace_bytes(nedner_plan_t plan);
  * (adjoint, gradient) kernels; then split1 (1: stage (a) runs as block spread,
  * x-FFT and y-FFT per chunk of tq time samples), tq, the block spread's warps
  * per CTA, the x-FFT kernel's complex columns, threads and values per thread
- * per CTA, and the shared memory of both.  Returns the number of values (29), or -1 for
+ * per CTA, the shared memory of both, and that of the transposed NER.
+ * Returns the number of values (30), or -1 for
  * a geometry nedner_plan rejects or a null out.  No paper counterpart.
  */
 int nedner_work_split(int nx, int ny, int nz, int Nt, int w, int64_t* out, int nout);

@@ -51,7 +51,7 @@ struct Chunks {
     int tp_adj;    // time samples per pass of the transposed gather (its entry buffer holds M w tp_adj floats)
     int lpc;       // line groups per CTA in the NER stage
     int threads3;  // threads per CTA in the NER stage
-    size_t smem1, smem2f, smem3, smem4, smem5;
+    size_t smem1, smem2f, smem3, smem3a, smem4, smem5;   // smem3a: the transposed NER
     size_t smem_adj, smem_grad;
 };
 

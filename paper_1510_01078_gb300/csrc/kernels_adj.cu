@@ -22,6 +22,16 @@
 
 namespace nedner {
 
+// asynchronous global -> shared copy of 8 bytes (cp.async), completed per
+// thread by cp.async.wait_group; both addresses 8-byte aligned
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Transpose of img_xc2r: Y[kx] = d_kx sum_qx p[qx] exp(-2 pi i kx qx / nx),
 // kx = 0..nx/2, d = 1 at kx = 0, nx/2 and 2 otherwise.  Real-to-complex FFT
@@ -150,12 +160,19 @@ __device__ __forceinline__ void ner_scatter(const TapPoly& P, float2* LA, int mu
     }
 }
 
-// coefficient(l) * exp(+i pi nu) * tb spread onto column col of the line's
-// oversampled spectrum (the transpose of ner_value)
-template <int W, int D>
-__device__ __forceinline__ void ner_spread_value(const Geo& G, const TapPoly& P, float2 axy, bool j0, int l, float2 tb,
-                                                 float2* LA, int lld, int col) {
-    if (tb.x == 0.f && tb.y == 0.f) return;
+// The transposed NER value of one depth frequency l of a line: its weight
+// (Jacobian, scale, band mask) times exp(+i pi nu) times tb, and where its w
+// taps land on the line's 2Nt grid: the first grid point mu0 and the tap
+// argument s (tap k at s, tap w-1-k at -s, as in ner_gather).  mu0 is
+// computed whether or not the value is zero, so that it is non-decreasing in
+// l (nu is increasing in l).
+struct NerAdjItem {
+    int mu0;
+    float s;
+    float2 v;
+};
+
+__device__ __forceinline__ NerAdjItem ner_adj_item(const Geo& G, float2 axy, bool j0, int l, float2 tb) {
     FF2 nu = nu_abs2(G, axy, l);
     float Wj;
     if (l == 0) {
@@ -170,23 +187,119 @@ __device__ __forceinline__ void ner_spread_value(const Geo& G, const TapPoly& P,
         const double nd = (double)nu.hi + (double)nu.lo;
         if (!(nd >= -0.5 * G.Nt - 1e-9 && nd < 0.5 * G.Nt - 1e-9)) cl = 0.f;
     }
-    if (cl == 0.f) return;
-    tb = cscale(tb, cl);
     const float vh = 2.f * nu.hi, vl = 2.f * nu.lo;
     float fl = floorf(vh);
     float t = (vh - fl) + vl;
     if (t < 0.f) { t += 1.f; fl -= 1.f; }
     if (t >= 1.f) { t -= 1.f; fl += 1.f; }
     const int ifl = (int)fl;
-    // exp(+i pi nu) = i^floor(v) exp(+i pi t / 2)
-    float sn, cs;
-    sincospif(0.5f * t, &sn, &cs);
-    float2 ph = make_float2(cs, sn);
-    const int q = ifl & 3;
-    if (q == 1) ph = make_float2(-ph.y, ph.x);
-    else if (q == 2) ph = make_float2(-ph.x, -ph.y);
-    else if (q == 3) ph = make_float2(ph.y, -ph.x);
-    ner_scatter<W, D>(P, LA, ifl - W / 2 + 1, 2.f * t - 1.f, G.Lt, lld, col, cmul(ph, tb));
+    NerAdjItem it;
+    it.mu0 = ifl - G.w / 2 + 1;
+    it.s = 2.f * t - 1.f;
+    it.v = make_float2(0.f, 0.f);
+    tb = cscale(tb, cl);
+    if (tb.x != 0.f || tb.y != 0.f) {
+        // exp(+i pi nu) = i^floor(v) exp(+i pi t / 2)
+        float sn, cs;
+        sincospif(0.5f * t, &sn, &cs);
+        float2 ph = make_float2(cs, sn);
+        const int q = ifl & 3;
+        if (q == 1) ph = make_float2(-ph.y, ph.x);
+        else if (q == 2) ph = make_float2(-ph.x, -ph.y);
+        else if (q == 3) ph = make_float2(ph.y, -ph.x);
+        it.v = cmul(ph, tb);
+    }
+    return it;
+}
+
+// the W tap weights P_k(s), k = 0..W-1 (tap W-1-k is tap k at -s)
+template <int W, int D>
+__device__ __forceinline__ void ner_taps(const TapPoly& P, float s, float* w) {
+    constexpr int DE = D & ~1;
+    constexpr int DO = (D & 1) ? D : D - 1;
+    const float u = s * s;
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+        float e = P.c[k * (D + 1) + DE];
+#pragma unroll
+        for (int d = DE - 2; d >= 0; d -= 2) e = fmaf(e, u, P.c[k * (D + 1) + d]);
+        float o = P.c[k * (D + 1) + DO];
+#pragma unroll
+        for (int d = DO - 2; d >= 1; d -= 2) o = fmaf(o, u, P.c[k * (D + 1) + d]);
+        const float so = s * o;
+        w[k] = e + so;
+        w[W - 1 - k] = e - so;
+    }
+}
+
+// items of one line held at a time by the transposed NER (a line has nz + 1)
+constexpr int NER_ADJ_ICAP = 1025;
+
+// One line of the transposed NER into column col of the padded line buffer
+// LA (2^lld columns, zero on entry): Bbar[mu] = sum_l P_{mu - mu0_l}(s_l) v_l
+// over the depth frequencies whose taps reach mu.  The nz + 1 depth
+// frequencies are taken in chunks of at most NER_ADJ_ICAP: phase 1 stores each
+// one's mu0, v and W tap weights (it_mu0, it_v, it_w); phase 2 gives each grid
+// point of the chunk's band [mu0_first, mu0_last + W) to one thread, which
+// finds the l reaching it by binary search in the non-decreasing mu0 (two
+// items of slack either side for rounding in nu) and adds their contributions
+// in order of l to the point: no atomics, and the same result on every run.
+// A band longer than the grid (nu far beyond the Nyquist band, where grid
+// points would be shared modulo 2Nt) is spread with shared-memory atomics
+// instead.  Returns true if every band lies within [-Lt/4, Lt/4), i.e. the
+// inverse FFT's input is zero on [Lt/4, 3Lt/4).
+template <int W, int D, int NT, typename TB>
+__device__ bool ner_adj_line(const Geo& G, const TapPoly& P, float2 axy, bool j0, TB tb_of, float2* LA, int lld,
+                             int col, int* it_mu0, float2* it_v, float* it_w) {
+    const int nz1 = G.nz + 1, half_nz = G.nz / 2;
+    bool zp = true;
+    for (int e0 = 0; e0 < nz1; e0 += NER_ADJ_ICAP) {
+        const int ni = min(NER_ADJ_ICAP, nz1 - e0);
+        for (int i = threadIdx.x; i < ni; i += NT) {
+            const NerAdjItem it = ner_adj_item(G, axy, j0, e0 + i - half_nz, tb_of(e0 + i));
+            it_mu0[i] = it.mu0;
+            it_v[i] = it.v;
+            ner_taps<W, D>(P, it.s, it_w + i * W);
+        }
+        __syncthreads();
+        const int lo = it_mu0[0] - 2, hi = it_mu0[ni - 1] + W + 2;
+        if (hi - lo <= G.Lt) {
+            for (int mu = lo + (int)threadIdx.x; mu < hi; mu += NT) {
+                // first item whose mu0 >= mu - W + 1, then two earlier for slack
+                int a = 0, b = ni;
+                while (a < b) {
+                    const int m = (a + b) >> 1;
+                    if (it_mu0[m] < mu - W + 1) a = m + 1;
+                    else b = m;
+                }
+                float2 acc = make_float2(0.f, 0.f);
+                for (int i = max(0, a - 2); i < ni && it_mu0[i] <= mu + 2; ++i) {
+                    const int k = mu - it_mu0[i];
+                    if (k >= 0 && k < W) {
+                        const float wk = it_w[i * W + k];
+                        const float2 v = it_v[i];
+                        acc.x = fmaf(wk, v.x, acc.x);
+                        acc.y = fmaf(wk, v.y, acc.y);
+                    }
+                }
+                float2* d = &LA[padx((((mu + G.Lt) & (G.Lt - 1)) << lld) + col)];
+                *d = e0 == 0 ? acc : cadd(*d, acc);
+            }
+        } else {
+            for (int i = threadIdx.x; i < ni; i += NT) {
+                const float2 v = it_v[i];
+                if (v.x == 0.f && v.y == 0.f) continue;
+                for (int k = 0; k < W; ++k) {
+                    float2* d = &LA[padx((((it_mu0[i] + k) & (G.Lt - 1)) << lld) + col)];
+                    atomicAdd(&d->x, it_w[i * W + k] * v.x);
+                    atomicAdd(&d->y, it_w[i * W + k] * v.y);
+                }
+            }
+        }
+        __syncthreads();
+        zp = zp && lo >= -(G.Lt / 4) && hi <= G.Lt / 4;
+    }
+    return zp;
 }
 
 // Transpose of ner_lines for the LPC line groups (kx, k0..k0+LPC-1) of the
@@ -196,20 +309,28 @@ __device__ __forceinline__ void ner_spread_value(const Geo& G, const TapPoly& P,
 //   the group ky = -ny/2 feeds line -ny/2 through ca only and line +ny/2
 //   through cb (slot(e) = l for e < nz, -nz/2 for e = nz), as the fold reads them;
 // each Tbar[e] is weighted (Jacobian, scale, band mask), multiplied by
-// exp(+i pi nu) and spread with the w taps onto the line's 2Nt grid (shared
-// atomics), the grids are inverse-transformed together, and the centred Nt
-// samples, divided by phihat, are the lines of Ghat.
+// exp(+i pi nu) and spread with the w taps onto the line's 2Nt grid
+// (ner_adj_line), the grids are inverse-transformed together (the first pass
+// skipping the zero half where every band allows), and the centred Nt
+// samples, divided by phihat in time and by phihat(jy/Ly) (the transposed
+// y-FFT's deconvolution, applied here), are the lines of Ghat.
 template <int W, int D, int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines_adj(Geo G, const __grid_constant__ TapPoly P,
                                                                        int LPC, const float2* __restrict__ V,
                                                                        const float2* __restrict__ axy_tab,
                                                                        const float* __restrict__ deconv_t,
+                                                                       const float* __restrict__ deconv_y,
                                                                        const float2* __restrict__ tw,
                                                                        float2* __restrict__ Ghat) {
     constexpr int PER = 16;
     extern __shared__ float4 smem4[];
+    const int nz1 = G.nz + 1;
     float2* LA = reinterpret_cast<float2*>(smem4);                 // [Lt][LPC], padded
     float2* UA = LA + padded_len(G.Lt * LPC);                      // [nz][LPC], padded
+    const int icap = min(nz1, NER_ADJ_ICAP);
+    float2* it_v = UA + padded_len(G.nz * LPC);                    // [icap] (items of one line)
+    int* it_mu0 = reinterpret_cast<int*>(it_v + icap);             // [icap]
+    float* it_w = reinterpret_cast<float*>(it_mu0 + icap);         // [icap][W]
 
     const int llpc = ilog2(LPC), lnz = ilog2(G.nz);
     const int cpk = G.ny >> llpc;
@@ -229,51 +350,55 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines_adj(Geo G, 
         UA[padx((q << llpc) + c)] = cscale(V[((size_t)kx * G.ny + (ky & (G.ny - 1))) * G.nz + q], sg);
     }
     block_fft_ip<PER>(UA, G.nz, LPC, -1, tw);
+    auto slot_of = [&](int e) { return (e == G.nz) ? (-half_nz & (G.nz - 1)) : ((e - half_nz) & (G.nz - 1)); };
 
     if (k0 == -G.ny / 2) {
         // the line (kx, +ny/2), fed by group 0 through cb, in column 0
         for (int p = threadIdx.x; p < padded_len(G.Lt); p += NT) LA[p] = make_float2(0.f, 0.f);
         __syncthreads();
         const size_t lx = (size_t)kx * G.nyp + G.ny;
-        const float2 axy = __ldg(&axy_tab[lx]);
-        for (int e = threadIdx.x + 1; e <= G.nz; e += NT) {
-            const int l = e - half_nz;
-            const int slot = (e == G.nz) ? (-half_nz & (G.nz - 1)) : (l & (G.nz - 1));
-            ner_spread_value<W, D>(G, P, axy, false, l, cscale(UA[padx(slot << llpc)], cb), LA, 0, 0);
-        }
-        block_fft_ip<PER>(LA, G.Lt, 1, +1, tw);
+        auto tb_of = [&](int e) {
+            return e > 0 ? cscale(UA[padx(slot_of(e) << llpc)], cb) : make_float2(0.f, 0.f);
+        };
+        const bool zp = ner_adj_line<W, D, NT>(G, P, __ldg(&axy_tab[lx]), false, tb_of, LA, 0, 0, it_mu0, it_v,
+                                              it_w);
+        if (zp) block_fft_ip<PER, true>(LA, G.Lt, 1, +1, tw);
+        else block_fft_ip<PER>(LA, G.Lt, 1, +1, tw);
         float2* dst = Ghat + lx * G.Nt;
+        const float dy = __ldg(&deconv_y[G.ny]);
         for (int n = threadIdx.x; n < G.Nt; n += NT)
-            dst[n] = cscale(LA[padx((n - G.Nt / 2) & (G.Lt - 1))], __ldg(&deconv_t[n]));
+            dst[n] = cscale(LA[padx((n - G.Nt / 2) & (G.Lt - 1))], __ldg(&deconv_t[n]) * dy);
         __syncthreads();
     }
-    // the LPC lines (kx, k0 + c)
+    // the LPC lines (kx, k0 + c), one after another into their columns
     for (int p = threadIdx.x; p < padded_len(G.Lt * LPC); p += NT) LA[p] = make_float2(0.f, 0.f);
     __syncthreads();
-    for (int i = threadIdx.x; i < ((G.nz + 1) << llpc); i += NT) {
-        const int c = i / (G.nz + 1), e = i - c * (G.nz + 1);
-        const int l = e - half_nz;
+    bool zp = true;
+    for (int c = 0; c < LPC; ++c) {
         const int ky = k0 + c;
         const bool is_b = (ky != -G.ny / 2);                       // group -ny/2 feeds line +ny/2 instead
-        float2 tb = make_float2(0.f, 0.f);
-        if (e < G.nz) tb = cadd(tb, cscale(UA[padx(((l & (G.nz - 1)) << llpc) + c)], ca));
-        if (is_b && e > 0) {
-            const int slot = (e == G.nz) ? (-half_nz & (G.nz - 1)) : (l & (G.nz - 1));
-            tb = cadd(tb, cscale(UA[padx((slot << llpc) + c)], cb));
-        }
-        const float2 axy = __ldg(&axy_tab[line0 + c]);
-        ner_spread_value<W, D>(G, P, axy, kx == 0 && ky == 0, l, tb, LA, llpc, c);
+        auto tb_of = [&](int e) {
+            const int l = e - half_nz;
+            float2 tb = make_float2(0.f, 0.f);
+            if (e < G.nz) tb = cadd(tb, cscale(UA[padx(((l & (G.nz - 1)) << llpc) + c)], ca));
+            if (is_b && e > 0) tb = cadd(tb, cscale(UA[padx((slot_of(e) << llpc) + c)], cb));
+            return tb;
+        };
+        zp &= ner_adj_line<W, D, NT>(G, P, __ldg(&axy_tab[line0 + c]), kx == 0 && ky == 0, tb_of, LA, llpc, c,
+                                     it_mu0, it_v, it_w);
     }
-    block_fft_ip<PER>(LA, G.Lt, LPC, +1, tw);
+    if (zp) block_fft_ip<PER, true>(LA, G.Lt, LPC, +1, tw);
+    else block_fft_ip<PER>(LA, G.Lt, LPC, +1, tw);
     for (int i = threadIdx.x; i < (G.Nt << llpc); i += NT) {
         const int c = i >> ilog2(G.Nt), n = i & (G.Nt - 1);
         Ghat[(line0 + c) * G.Nt + n] = cscale(LA[padx((((n - G.Nt / 2) & (G.Lt - 1)) << llpc) + c)],
-                                              __ldg(&deconv_t[n]));
+                                              __ldg(&deconv_t[n]) * __ldg(&deconv_y[k0 + c + G.ny / 2]));
     }
 }
 
 // ---------------------------------------------------------------------------
-// Transpose of ned_yfft: R[jx][gy][n] = sum_jy exp(+2 pi i jy gy / Ly) Ghat[jx][jy][n] / phihat(jy/Ly).
+// Transpose of ned_yfft: R[jx][gy][n] = sum_jy exp(+2 pi i jy gy / Ly) Ghat[jx][jy][n] / phihat(jy/Ly)
+// (the division by phihat(jy/Ly) is done by k_ner_lines_adj when it writes Ghat).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 3) k_ned_yfft_adj(Geo G, int C, const float2* __restrict__ Ghat,
                                                          const float* __restrict__ deconv_y,
@@ -283,15 +408,17 @@ __global__ void __launch_bounds__(256, 3) k_ned_yfft_adj(Geo G, int C, const flo
     const int jx = blockIdx.y;                      // time chunks on blockIdx.x: neighbouring CTAs
     const int n0 = blockIdx.x * C;                  // read neighbouring pieces of the same rows
     const int lc = ilog2(C);
-    // jy = b - ny/2 sits at q = (jy mod Ly); the other Ly - (ny + 1) points are zero
-#pragma unroll 8
+    // jy = b - ny/2 sits at q = (jy mod Ly); the other Ly - (ny + 1) points are
+    // zero.  Ghat arrives already divided by phihat(jy/Ly) (k_ner_lines_adj).
     for (int it = threadIdx.x; it < G.Ly * C; it += 256) {
         const int q = it >> lc;
         const int c = it & (C - 1);
         const int b = (q <= G.ny / 2) ? q + G.ny / 2 : ((q >= G.Ly - G.ny / 2) ? q - G.Ly + G.ny / 2 : -1);
-        A[padx(it)] = (b >= 0) ? cscale(Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c], __ldg(&deconv_y[b]))
-                               : make_float2(0.f, 0.f);
+        if (b >= 0) cp_async(&A[padx(it)], &Ghat[((size_t)jx * G.nyp + b) * G.Nt + n0 + c], 8);
+        else A[padx(it)] = make_float2(0.f, 0.f);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     block_fft_ip<16>(A, G.Ly, C, +1, tw);
 #pragma unroll 8
     for (int it = threadIdx.x; it < G.Ly * C; it += 256) {
@@ -566,8 +693,8 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
         return e;
     const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
 #define NEDNER_ATTR_NER(W, D)                                                                                      \
-    if ((e = cudaFuncSetAttribute(k_ner_lines_adj<W, D, 256>, (cudaFuncAttribute)a, (int)c.smem3))) return e; \
-    if ((e = cudaFuncSetAttribute(k_ner_lines_adj<W, D, 512>, (cudaFuncAttribute)a, (int)c.smem3))) return e;
+    if ((e = cudaFuncSetAttribute(k_ner_lines_adj<W, D, 256>, (cudaFuncAttribute)a, (int)c.smem3a))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ner_lines_adj<W, D, 512>, (cudaFuncAttribute)a, (int)c.smem3a))) return e;
     NEDNER_ATTR_NER(4, 10) NEDNER_ATTR_NER(6, 10) NEDNER_ATTR_NER(8, 10) NEDNER_ATTR_NER(10, 10)
     NEDNER_ATTR_NER(12, 10) NEDNER_ATTR_NER(14, 12) NEDNER_ATTR_NER(16, 12)
 #undef NEDNER_ATTR_NER
@@ -604,11 +731,11 @@ cudaError_t launch_ner_lines_adj(const nedner_plan_s& p, const float2* V, float2
     const dim3 grid(G.nxh * (G.ny / p.ch.lpc));
 #define NEDNER_NER(W, D)                                                                                        \
     if (p.ch.threads3 <= 256)                                                                                   \
-        k_ner_lines_adj<W, D, 256><<<grid, 256, p.ch.smem3, s>>>(G, p.tap, p.ch.lpc, V, p.t.axy, p.t.deconv_t,  \
-                                                                 p.t.tw, Ghat);                                \
+        k_ner_lines_adj<W, D, 256><<<grid, 256, p.ch.smem3a, s>>>(G, p.tap, p.ch.lpc, V, p.t.axy, p.t.deconv_t, \
+                                                                  p.t.deconv_y, p.t.tw, Ghat);                  \
     else                                                                                                        \
-        k_ner_lines_adj<W, D, 512><<<grid, 512, p.ch.smem3, s>>>(G, p.tap, p.ch.lpc, V, p.t.axy, p.t.deconv_t,  \
-                                                                 p.t.tw, Ghat)
+        k_ner_lines_adj<W, D, 512><<<grid, 512, p.ch.smem3a, s>>>(G, p.tap, p.ch.lpc, V, p.t.axy, p.t.deconv_t, \
+                                                                  p.t.deconv_y, p.t.tw, Ghat)
     switch (G.w) {
         case 4: NEDNER_NER(4, 10); break;
         case 6: NEDNER_NER(6, 10); break;

@@ -562,6 +562,10 @@ void choose_chunks(nedner_plan_s& p) {
            (long)G.nz * c.lpc * 2 <= 16L * c.threads3)
         c.lpc *= 2;
     c.smem3 = (size_t)(padded(G.Lt * c.lpc) + (c.lpc + 1) * (G.nz + 1) + padded(G.nz * c.lpc)) * 8;
+    // transposed NER: line buffers, Ubar, then one line's items (value, first
+    // grid point, w tap weights)
+    c.smem3a = (size_t)(padded(G.Lt * c.lpc) + padded(G.nz * c.lpc)) * 8 +
+               (size_t)std::min(G.nz + 1, 1025) * (8 + 4 + 4 * G.w);
     // inverse y- and x-FFTs: C <= 16 columns (conflict-free padded loads and
     // stores), N * C <= 2048 (16 values per thread of 128)
     c.c4 = (int)std::min<long>(std::min<long>(16, G.nz), 2048 / G.ny);
@@ -921,7 +925,7 @@ int nedner_work_split(int nx, int ny, int nz, int Nt, int w, int64_t* out, int n
                          c.tpl_adj, c.threads_adj, c.lpc, c.threads3, (int64_t)c.smem1, (int64_t)c.smem2f,
                          (int64_t)c.smem3, (int64_t)c.smem4, (int64_t)c.smem5, (int64_t)c.smem_adj,
                          (int64_t)c.smem_grad, c.split1, c.tq, c.wpc_s, c.nbx, c.thx, c.perx, (int64_t)c.smem_s,
-                         (int64_t)c.smem_x};
+                         (int64_t)c.smem_x, (int64_t)c.smem3a};
     const int n = (int)(sizeof(v) / sizeof(v[0]));
     for (int i = 0; i < n && i < nout; ++i) out[i] = v[i];
     return n;

@@ -390,7 +390,7 @@ def reconstruct(plan: Plan, g, sensor_xy=None):
 
 WORK_SPLIT_FIELDS = ("c1", "c2f", "c4", "c5", "groups1", "threads1", "per1", "tpl1", "ca", "per_adj", "tpl_adj",
                      "threads_adj", "lpc", "threads3", "smem1", "smem2f", "smem3", "smem4", "smem5", "smem_adj",
-                     "smem_grad", "split1", "tq", "wpc_s", "nbx", "thx", "perx", "smem_s", "smem_x")
+                     "smem_grad", "split1", "tq", "wpc_s", "nbx", "thx", "perx", "smem_s", "smem_x", "smem3a")
 
 
 def work_split(nx: int, ny: int, nz: int, Nt: int, w: int = 12) -> dict:

@@ -55,7 +55,7 @@ def check(nx, ny, nz, Nt, s):
     # NER and its transpose: line FFT of Lt and z-FFT of nz, 16 values per thread
     need(s["threads3"] in (256, 512) and ny % s["lpc"] == 0, "NER: line groups")
     need(Lt * s["lpc"] <= 16 * s["threads3"] and nz * s["lpc"] <= 16 * s["threads3"], "NER: FFTs fit")
-    need(s["smem3"] <= SMEM_MAX, "NER: shared memory")
+    need(s["smem3"] <= SMEM_MAX and s["smem3a"] <= SMEM_MAX, "NER and its transpose: shared memory")
     # inverse image FFTs and their transposes: 128 threads, 16 values each
     need(nz % s["c4"] == 0 and ny * s["c4"] <= 16 * 128, "y-IFFT: fits")
     need(ny % s["c5"] == 0 and (nx // 2) * s["c5"] <= 16 * 128, "x-c2r: fits")
