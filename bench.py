@@ -137,23 +137,27 @@ def algorithmic_bytes(cfg, split=True):
     return d
 
 
-def algorithmic_bytes_transposed(cfg, grad: bool):
+def algorithmic_bytes_transposed(cfg, grad: bool, split=True):
     """The same for the transposed stages (each forward stage's bytes with
-    input and output swapped).  The gather reads the rebuilt rows R and writes
-    g (adjoint), or reads R and g and writes 2 floats per sensor (gradient);
-    its per-entry intermediate and the per-sensor sum are counted as the
-    sum's bytes (entries read, result written)."""
-    f = algorithmic_bytes(cfg, split=False)
-    M, Nt, w = cfg["sensor_xy"].shape[0], cfg["Nt"], 12
+    input and output swapped).  Split: the transposed x-FFT reads R and
+    writes the oversampled real grid Q, the block gather reads Q; fused: the
+    gather reads R and rebuilds the rows itself.  The gather writes one value
+    per entry and time sample (adjoint), or reads g and writes 2 floats per
+    entry and 64-sample chunk (gradient); the entry sum reads those and
+    writes g (adjoint) or 2 floats per sensor (gradient)."""
+    f = algorithmic_bytes(cfg, split=split)
+    M, Nt, nx, ny, w = cfg["sensor_xy"].shape[0], cfg["Nt"], cfg["nx"], cfg["ny"], 12
     g = M * Nt * 4
-    R = f["ned_spread"] - g
+    Q = 2 * ny * 2 * nx * Nt * 4
+    R = (nx // 2 + 1) * 2 * ny * Nt * 8
+    src = Q if split else R
     if grad:
         nch = Nt // 64
-        gather, esum = R + g + M * w * nch * 8, M * w * nch * 8 + M * 8
+        gather, esum = src + g + M * w * nch * 8, M * w * nch * 8 + M * 8
     else:
-        gather, esum = R + M * w * Nt * 4, M * w * Nt * 4 + g
+        gather, esum = src + M * w * Nt * 4, M * w * Nt * 4 + g
     return {"img_xr2c_adj": f["img_xc2r"], "img_yfft_adj": f["img_yifft"], "ner_lines_adj": f["ner_lines"],
-            "ned_yfft_adj": f["ned_yfft"], "gather": gather, "entry_sum": esum}
+            "ned_yfft_adj": f["ned_yfft"], "ned_xfft_adj": f["ned_xfft"], "gather": gather, "entry_sum": esum}
 
 
 def gather_alg_bytes(cfg):
@@ -475,8 +479,8 @@ def main():
     interp_roofline = None
     passes = transposed_passes(cfg)
     if do_t:
-        aa, ak = kernel_table(per_adj, algorithmic_bytes_transposed(cfg, False))
-        ga, gk = kernel_table(per_grad, algorithmic_bytes_transposed(cfg, True))
+        aa, ak = kernel_table(per_adj, algorithmic_bytes_transposed(cfg, False, split))
+        ga, gk = kernel_table(per_grad, algorithmic_bytes_transposed(cfg, True, split))
         adj_ms = max_over_ranks(sum(aa.values()), world, dev)
         grad_ms = max_over_ranks(sum(ga.values()), world, dev)
         transposed = {"adjoint": {"ms": round(adj_ms, 4), "voxels_per_s": whole_job_value(voxels, world, adj_ms),
@@ -484,9 +488,10 @@ def main():
                       "grad_positions": {"ms": round(grad_ms, 4),
                                          "voxels_per_s": whole_job_value(voxels, world, grad_ms), "kernels": gk}}
         gb = gather_alg_bytes(cfg)
-        gms = aa["gather"] + aa["entry_sum"]
+        gms = aa.get("ned_xfft_adj", 0.0) + aa["gather"] + aa["entry_sum"]
         tg = traffic_for("gather", cfg["name"])
-        interp_roofline = {"bound": "hbm", "kernel": "adjoint gather + entry sum (transposed interpolation)",
+        interp_roofline = {"bound": "hbm",
+                           "kernel": "adjoint transposed x-FFT + gather + entry sum (transposed interpolation)",
                            "achieved": round(gb / (gms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                            "frac": round(gb / (gms * 1e-3) / 1e9 / peak, 4),
                            "traffic": None if tg is None else tg * passes,

@@ -197,11 +197,12 @@ nedner_status nedner_forward_profiled(nedner_plan_t plan, const float* g, float*
  * stream and writes each stage's device time in milliseconds to stage_ms
  * (host array of NEDNER_TRANSPOSED_KERNELS floats): transposed x
  * complex-to-real, transposed y-IFFT, transposed NER, transposed y-FFT, the
- * transposed interpolation (gather, summed over its passes of time samples)
- * and the per-sensor sum of its entries.  Synchronous.  Same arguments and
- * errors as the unprofiled calls otherwise.
+ * transposed x-FFT and the transposed interpolation (gather; where the two
+ * are one kernel its time is the gather's and the x-FFT's is 0), both summed
+ * over their passes of time samples, and the per-sensor sum of the entries.
+ * Synchronous.  Same arguments and errors as the unprofiled calls otherwise.
  */
-#define NEDNER_TRANSPOSED_KERNELS 6
+#define NEDNER_TRANSPOSED_KERNELS 7
 nedner_status nedner_adjoint_profiled(nedner_plan_t plan, const float* p0, float* g, void* stream,
                                       float* stage_ms);
 nedner_status nedner_grad_positions_profiled(nedner_plan_t plan, const float* g, const float* dL_dp0,

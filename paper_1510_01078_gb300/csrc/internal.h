@@ -44,6 +44,9 @@ struct Chunks {
     int thx;       // threads per CTA of the x-FFT kernel
     int perx;      // values per thread of its in-place FFT (16 or 32)
     size_t smem_s, smem_x;
+    int gsplit;    // 1: the transposed interpolation runs as transposed x-FFT + block gather per pass of tp_g samples
+    int tp_g;      // time samples per pass of the block gather (its grid Q-bar is held in region A after R-bar)
+    size_t smem_ga, smem_gg;   // shared memory of the block gather (adjoint, gradient)
     int ca;        // time samples per CTA in the transposed interpolation stage
     int per_adj;   // values per thread in its in-place row FFT (16 or 32)
     int tpl_adj;   // time samples per lane in the transposed gather (1 or 2; 2 means ca = 64)
@@ -102,6 +105,9 @@ struct DevTables {
     int2* bseg = nullptr;         // [Ly][Lx/16]
     int* pent_bx = nullptr;       // [E'] first x column (negative for the second copy of a wrapped entry)
     float* pent_w = nullptr;      // [E'][4 ceil(w/4)] x tap times y tap times sensor factor, from pent_bx on
+    float* pent_gx = nullptr;     // [E'][4 ceil(w/4)] the same with the x-tap derivative (position gradient)
+    float* pent_gy = nullptr;     // [E'][4 ceil(w/4)] the same with the y-tap derivative
+    int2* gseg = nullptr;         // [Ly][Lx/16] entries whose first column lies in the block (block gather)
     int* status = nullptr;        // device flags: NEDNER_FLAG_NONFINITE when an output kernel wrote a non-finite value
 };
 

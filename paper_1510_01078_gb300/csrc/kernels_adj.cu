@@ -17,20 +17,12 @@
 #include <algorithm>
 
 #include "fft.cuh"
+#include "async_copy.cuh"
 #include "internal.h"
 #include "gather_window.cuh"
 
 namespace nedner {
 
-// asynchronous global -> shared copy of 8 bytes (cp.async), completed per
-// thread by cp.async.wait_group; both addresses 8-byte aligned
-__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Transpose of img_xc2r: Y[kx] = d_kx sum_qx p[qx] exp(-2 pi i kx qx / nx),
@@ -257,33 +249,48 @@ __device__ bool ner_adj_line(const Geo& G, const TapPoly& P, float2 axy, bool j0
         const int ni = min(NER_ADJ_ICAP, nz1 - e0);
         for (int i = threadIdx.x; i < ni; i += NT) {
             const NerAdjItem it = ner_adj_item(G, axy, j0, e0 + i - half_nz, tb_of(e0 + i));
+            float w[W];
+            ner_taps<W, D>(P, it.s, w);
             it_mu0[i] = it.mu0;
             it_v[i] = it.v;
-            ner_taps<W, D>(P, it.s, it_w + i * W);
+#pragma unroll
+            for (int k = 0; k < W; ++k) it_w[i * (W + 1) + k] = w[k];      // odd stride: no bank conflicts
         }
         __syncthreads();
         const int lo = it_mu0[0] - 2, hi = it_mu0[ni - 1] + W + 2;
         if (hi - lo <= G.Lt) {
-            for (int mu = lo + (int)threadIdx.x; mu < hi; mu += NT) {
-                // first item whose mu0 >= mu - W + 1, then two earlier for slack
-                int a = 0, b = ni;
-                while (a < b) {
-                    const int m = (a + b) >> 1;
-                    if (it_mu0[m] < mu - W + 1) a = m + 1;
-                    else b = m;
+            // a warp takes 32 consecutive grid points: lanes 0 and 1 find the
+            // items reaching the first and the last (binary search, two items of
+            // slack), and every lane walks that range with broadcast loads
+            const int lane = threadIdx.x & 31;
+            for (int mw = lo + (int)(threadIdx.x & ~31); mw < hi; mw += NT) {
+                const int mu = mw + lane;
+                int r = 0;
+                if (lane < 2) {
+                    const int key = lane == 0 ? mw - W + 1 : mw + 32;   // first mu0 >= key
+                    int a = 0, b = ni;
+                    while (a < b) {
+                        const int m = (a + b) >> 1;
+                        if (it_mu0[m] < key) a = m + 1;
+                        else b = m;
+                    }
+                    r = lane == 0 ? max(0, a - 2) : min(ni, a + 2);
                 }
+                const int ia = __shfl_sync(0xffffffffu, r, 0), ib = __shfl_sync(0xffffffffu, r, 1);
                 float2 acc = make_float2(0.f, 0.f);
-                for (int i = max(0, a - 2); i < ni && it_mu0[i] <= mu + 2; ++i) {
+                for (int i = ia; i < ib; ++i) {
                     const int k = mu - it_mu0[i];
                     if (k >= 0 && k < W) {
-                        const float wk = it_w[i * W + k];
+                        const float wk = it_w[i * (W + 1) + k];
                         const float2 v = it_v[i];
                         acc.x = fmaf(wk, v.x, acc.x);
                         acc.y = fmaf(wk, v.y, acc.y);
                     }
                 }
-                float2* d = &LA[padx((((mu + G.Lt) & (G.Lt - 1)) << lld) + col)];
-                *d = e0 == 0 ? acc : cadd(*d, acc);
+                if (mu < hi) {
+                    float2* d = &LA[padx((((mu + G.Lt) & (G.Lt - 1)) << lld) + col)];
+                    *d = e0 == 0 ? acc : cadd(*d, acc);
+                }
             }
         } else {
             for (int i = threadIdx.x; i < ni; i += NT) {
@@ -291,8 +298,8 @@ __device__ bool ner_adj_line(const Geo& G, const TapPoly& P, float2 axy, bool j0
                 if (v.x == 0.f && v.y == 0.f) continue;
                 for (int k = 0; k < W; ++k) {
                     float2* d = &LA[padx((((it_mu0[i] + k) & (G.Lt - 1)) << lld) + col)];
-                    atomicAdd(&d->x, it_w[i * W + k] * v.x);
-                    atomicAdd(&d->y, it_w[i * W + k] * v.y);
+                    atomicAdd(&d->x, it_w[i * (W + 1) + k] * v.x);
+                    atomicAdd(&d->y, it_w[i * (W + 1) + k] * v.y);
                 }
             }
         }
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines_adj(Geo G, 
     const int icap = min(nz1, NER_ADJ_ICAP);
     float2* it_v = UA + padded_len(G.nz * LPC);                    // [icap] (items of one line)
     int* it_mu0 = reinterpret_cast<int*>(it_v + icap);             // [icap]
-    float* it_w = reinterpret_cast<float*>(it_mu0 + icap);         // [icap][W]
+    float* it_w = reinterpret_cast<float*>(it_mu0 + icap);         // [icap][W + 1]
 
     const int llpc = ilog2(LPC), lnz = ilog2(G.nz);
     const int cpk = G.ny >> llpc;
@@ -638,6 +645,152 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_gather_rows2(Geo 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The transposed interpolation as two kernels per pass of Tp time samples
+// [nb, nb + Tp) (the transpose of the block spread and the x-FFT):
+//
+// k_ned_xfft_adj: one CTA per (grid row gy, 2 nbx samples of the pass)
+// rebuilds the real row (row_rebuild: inverse x-FFT of the Hermitian half
+// spectrum of R-bar, divided by phihat) and writes it to the pass's grid Qb
+// [Tp/32][Ly][Lx][32], the layout of the forward Q (with nbx = 16 each CTA
+// writes one contiguous block).
+// ---------------------------------------------------------------------------
+template <int PER>
+__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_xfft_adj(Geo G, int nb, int nbx,
+                                                                        const float2* __restrict__ R,
+                                                                        const float* __restrict__ deconv_x,
+                                                                        const float2* __restrict__ tw,
+                                                                        float* __restrict__ Qb) {
+    extern __shared__ float4 smem4[];
+    float2* Z = reinterpret_cast<float2*>(smem4);                    // padded [Lx][nbx]
+    const int gy = blockIdx.x;
+    const int nc = blockIdx.y * 2 * nbx;                             // first sample of the CTA in the pass
+    const int lnb = ilog2(nbx);
+    row_rebuild<PER>(G, 2 * nbx, R, gy, nb + nc, deconv_x, tw, Z);
+    // samples nc .. nc + 2 nbx: group nc / 32 of 32, offset nc % 32
+    float2* dst = reinterpret_cast<float2*>(Qb + ((size_t)(nc >> 5) * G.Ly + gy) * G.Lx * 32 + (nc & 31));
+    for (int it = threadIdx.x; it < (G.Lx << lnb); it += blockDim.x)
+        dst[(size_t)(it >> lnb) * 16 + (it & (nbx - 1))] = Z[padx(it)];
+}
+
+// k_ned_gather_blocks: one warp per (grid row, block of 16 columns, 64 time
+// samples of the pass).  It holds the 32 columns [c0, c0 + 32) (modulo Lx) of
+// the row in registers (two samples per lane) and evaluates every entry whose
+// first column bx lies in its block, from the exact first column on:
+//   v[t] = sum_k tap[k] r[bx + k][t],  k < W
+// (W packed FMAs, a branch on d = bx - c0 in [0, 16)).  Each entry is
+// evaluated by exactly one warp, so nothing is shared between warps.
+//   adjoint:  E[e][t - nb] = v[t] (e the entry's index in the row CSR)
+//   gradient: the two derivative tap sets give v_x, v_y, and the entry's
+//             sum_t g[m][t] (v_x[t], v_y[t]) over its 64 samples goes to
+//             Qe[e][time chunk].
+// Entries (first column, row-CSR index, sensor, taps) arrive 32 at a time by
+// asynchronous copies, the next batch while the current one is evaluated.
+// ---------------------------------------------------------------------------
+template <int W, int D>
+__device__ __forceinline__ float2 taps_dot(const float2 (&win)[32], const float* t) {
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < W; ++k) v = __ffma2_rn(make_float2(t[k], t[k]), win[D + k], v);
+    return v;
+}
+
+template <int W>
+__device__ __forceinline__ float2 block_taps_dot(const float2 (&win)[32], int d, const float* t) {
+#define NEDNER_DOT_CASE(I) \
+    case I: return taps_dot<W, I>(win, t);
+    switch (d) {
+        NEDNER_DOT_CASE(0) NEDNER_DOT_CASE(1) NEDNER_DOT_CASE(2) NEDNER_DOT_CASE(3)
+        NEDNER_DOT_CASE(4) NEDNER_DOT_CASE(5) NEDNER_DOT_CASE(6) NEDNER_DOT_CASE(7)
+        NEDNER_DOT_CASE(8) NEDNER_DOT_CASE(9) NEDNER_DOT_CASE(10) NEDNER_DOT_CASE(11)
+        NEDNER_DOT_CASE(12) NEDNER_DOT_CASE(13) NEDNER_DOT_CASE(14)
+        default: return taps_dot<W, 15>(win, t);
+    }
+#undef NEDNER_DOT_CASE
+}
+
+template <int W, bool GRAD>
+__global__ void __launch_bounds__(128, 4) k_ned_gather_blocks(Geo G, int nb, int Tp, const float* __restrict__ Qb,
+                                                              const int2* __restrict__ gseg,
+                                                              const int* __restrict__ pent_bx,
+                                                              const int* __restrict__ xent_rc,
+                                                              const int* __restrict__ xent_m,
+                                                              const float* __restrict__ taps_a,
+                                                              const float* __restrict__ taps_b,
+                                                              const float* __restrict__ g, float* __restrict__ E,
+                                                              float2* __restrict__ Qe) {
+    constexpr int PW = (W + 3) / 4 * 4;
+    constexpr int BE = 32;                                           // entries per staged batch
+    constexpr int NTAP = GRAD ? 2 * PW : PW;
+    constexpr int BSZ = BE * (3 + NTAP);                             // one batch (4-byte words)
+    extern __shared__ float4 smem4[];
+    const int q = threadIdx.x >> 5;
+    const int ln = threadIdx.x & 31;
+    const int nblk = G.Lx >> 4;
+    const int gb = blockIdx.x * (blockDim.x >> 5) + q;
+    const int gy = gb / nblk;
+    const int c0 = (gb - gy * nblk) << 4;
+    const int nc = blockIdx.y * 64;                                  // first sample of the warp in the pass
+    const int tl = 32 * (ln >> 4) + 2 * (ln & 15);                   // the lane's first sample of the 64
+
+    // the 32 columns of the window, two samples per lane
+    float2 win[32];
+    {
+        const float2* src = reinterpret_cast<const float2*>(Qb + ((size_t)((nc >> 5) + (ln >> 4)) * G.Ly + gy) *
+                                                                     G.Lx * 32) + (ln & 15);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) win[c] = __ldg(src + (size_t)((c0 + c) & (G.Lx - 1)) * 16);
+    }
+    const int2 rg = gseg[gb];
+    const int nent = rg.y - rg.x;
+    const int nbt = (nent + BE - 1) / BE;
+    int* st = reinterpret_cast<int*>(smem4) + (size_t)q * 2 * BSZ;  // [2][BSZ]: bx, rc, m [BE] each, taps [BE][NTAP]
+    auto issue = [&](int b) {
+        const int e0 = rg.x + b * BE, n = min(BE, rg.y - e0);
+        int* d = st + (b & 1) * BSZ;
+        if (ln < n) {
+            cp_async(d + ln, pent_bx + e0 + ln, 4);
+            cp_async(d + BE + ln, xent_rc + e0 + ln, 4);
+            if (GRAD) cp_async(d + 2 * BE + ln, xent_m + e0 + ln, 4);
+        }
+        float* tp = reinterpret_cast<float*>(d + 3 * BE);
+        for (int i = ln; i < n * (PW / 4); i += 32) {
+            const int j = i / (PW / 4), k4 = i - j * (PW / 4);
+            cp_async(tp + j * NTAP + 4 * k4, taps_a + (size_t)(e0 + j) * PW + 4 * k4, 16);
+            if (GRAD) cp_async(tp + j * NTAP + PW + 4 * k4, taps_b + (size_t)(e0 + j) * PW + 4 * k4, 16);
+        }
+    };
+    if (nbt > 0) issue(0);
+    cp_async_commit();
+    for (int b = 0; b < nbt; ++b) {
+        cp_async_wait_all();
+        __syncwarp();
+        if (b + 1 < nbt) issue(b + 1);
+        cp_async_commit();
+        const int* d = st + (b & 1) * BSZ;
+        const float* tp = reinterpret_cast<const float*>(d + 3 * BE);
+        const int n = min(BE, nent - b * BE);
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) {
+            const int dd = d[j] - c0;
+            const float2 va = block_taps_dot<W>(win, dd, tp + j * NTAP);
+            if (!GRAD) {
+                reinterpret_cast<float2*>(E + (size_t)d[BE + j] * Tp + nc)[tl >> 1] = va;
+            } else {
+                const float2 vb = block_taps_dot<W>(win, dd, tp + j * NTAP + PW);
+                const float2 gv = __ldg(reinterpret_cast<const float2*>(g + (size_t)d[2 * BE + j] * G.Nt + nb + nc + tl));
+                float sx = fmaf(gv.x, va.x, gv.y * va.y), sy = fmaf(gv.x, vb.x, gv.y * vb.y);
+                for (int o = 16; o > 0; o >>= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                }
+                if (ln == 0) Qe[(size_t)d[BE + j] * (G.Nt >> 6) + ((nb + nc) >> 6)] = make_float2(sx, sy);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // g[m][nb + t] = sum_k E[sens_ent[m][k]][t], t < Tp: the sensor's w entries (one per y tap);
 // a non-finite result sets NEDNER_FLAG_NONFINITE in *status
 __global__ void k_adj_sum(Geo G, int nb, int Tp, const float* __restrict__ E, const int* __restrict__ sens_ent,
@@ -711,6 +864,14 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
     if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, true, 512>, (cudaFuncAttribute)a, (int)c.smem_grad))) return e;
     NEDNER_ATTR_GATHER2(8) NEDNER_ATTR_GATHER2(12) NEDNER_ATTR_GATHER2(16) NEDNER_ATTR_GATHER2(20)
 #undef NEDNER_ATTR_GATHER2
+    if ((e = cudaFuncSetAttribute(k_ned_xfft_adj<16>, (cudaFuncAttribute)a, (int)c.smem_x))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_xfft_adj<32>, (cudaFuncAttribute)a, (int)c.smem_x))) return e;
+#define NEDNER_ATTR_BG(W)                                                                                   \
+    if ((e = cudaFuncSetAttribute(k_ned_gather_blocks<W, false>, (cudaFuncAttribute)a, (int)c.smem_ga))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ned_gather_blocks<W, true>, (cudaFuncAttribute)a, (int)c.smem_gg))) return e;
+    NEDNER_ATTR_BG(4) NEDNER_ATTR_BG(6) NEDNER_ATTR_BG(8) NEDNER_ATTR_BG(10) NEDNER_ATTR_BG(12) NEDNER_ATTR_BG(14)
+    NEDNER_ATTR_BG(16)
+#undef NEDNER_ATTR_BG
     return cudaSuccess;
 }
 
@@ -764,12 +925,64 @@ cudaError_t launch_ned_yfft_adj(const nedner_plan_s& p, const float2* Ghat, floa
         default: CALL(20); break;       \
     }
 
+// block gather of one pass [nb, nb + Tp): transposed x-FFT into Qb, then the
+// blocks (adjoint: entry values into E; gradient: per-entry sums into Qe)
+static cudaError_t launch_block_gather(const nedner_plan_s& p, const float2* R, float* Qb, int nb, int Tp, bool grad,
+                                       const float* g, float* E, float2* Qe, cudaStream_t s, StageTimer* tm) {
+    const Geo& G = p.geo;
+    const dim3 gx(G.Ly, Tp / (2 * p.ch.nbx));
+    if (p.ch.perx <= 16)
+        k_ned_xfft_adj<16><<<gx, p.ch.thx, p.ch.smem_x, s>>>(G, nb, p.ch.nbx, R, p.t.deconv_x, p.t.tw, Qb);
+    else
+        k_ned_xfft_adj<32><<<gx, p.ch.thx, p.ch.smem_x, s>>>(G, nb, p.ch.nbx, R, p.t.deconv_x, p.t.tw, Qb);
+    stage_mark(tm, 4);
+    const dim3 grid(G.Ly * (G.Lx / 16) / 4, Tp / 64);
+#define NEDNER_BG(W)                                                                                              \
+    if (grad)                                                                                                     \
+        k_ned_gather_blocks<W, true><<<grid, 128, p.ch.smem_gg, s>>>(G, nb, Tp, Qb, p.t.gseg, p.t.pent_bx,         \
+                                                                     p.t.xent_rc, p.t.xent_m, p.t.pent_gx,         \
+                                                                     p.t.pent_gy, g, E, Qe);                       \
+    else                                                                                                          \
+        k_ned_gather_blocks<W, false><<<grid, 128, p.ch.smem_ga, s>>>(G, nb, Tp, Qb, p.t.gseg, p.t.pent_bx,        \
+                                                                      p.t.xent_rc, p.t.xent_m, p.t.pent_w,         \
+                                                                      p.t.pent_w, g, E, Qe)
+    switch (G.w) {
+        case 4: NEDNER_BG(4); break;
+        case 6: NEDNER_BG(6); break;
+        case 8: NEDNER_BG(8); break;
+        case 10: NEDNER_BG(10); break;
+        case 12: NEDNER_BG(12); break;
+        case 14: NEDNER_BG(14); break;
+        default: NEDNER_BG(16); break;
+    }
+#undef NEDNER_BG
+    stage_mark(tm, 5);
+    return cudaGetLastError();
+}
+
+// region A after R-bar: the block gather's pass grid
+static float* pass_grid(const nedner_plan_s& p) {
+    const size_t rbar = ((size_t)p.geo.nxh * p.geo.Ly * p.geo.Nt * 8 + 255) / 256 * 256;
+    return (float*)((char*)p.ws + rbar);
+}
+
 cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E, float* g, cudaStream_t s,
                               StageTimer* tm) {
     const Geo& G = p.geo;
     const int C = p.ch.ca, Tp = p.ch.tp_adj;
     const size_t total = (size_t)G.M * Tp;
     const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    if (p.ch.gsplit) {
+        cudaError_t e = cudaSuccess;
+        for (int nb = 0; nb < G.Nt && !e; nb += Tp) {
+            e = launch_block_gather(p, R, pass_grid(p), nb, Tp, false, nullptr, E, nullptr, s, tm);
+            if (e) break;
+            k_adj_sum<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g, p.t.status);
+            stage_mark(tm, 6);
+            e = cudaGetLastError();
+        }
+        return e;
+    }
     for (int nb = 0; nb < G.Nt; nb += Tp) {
         const dim3 grid(G.Ly, Tp / C);
 #define NEDNER_ADJ(WT)                                                                                            \
@@ -792,9 +1005,9 @@ cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E,
                                                                       p.t.deconv_x, p.t.tw, E, nullptr)
         NEDNER_GATHER_SWITCH(NEDNER_ADJ)
 #undef NEDNER_ADJ
-        stage_mark(tm, 4);
-        k_adj_sum<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g, p.t.status);
         stage_mark(tm, 5);
+        k_adj_sum<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g, p.t.status);
+        stage_mark(tm, 6);
     }
     return cudaGetLastError();
 }
@@ -804,6 +1017,15 @@ cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const fl
     const Geo& G = p.geo;
     const int C = p.ch.ca;
     const dim3 grid(G.Ly, G.Nt / C);
+    if (p.ch.gsplit) {
+        cudaError_t e = cudaSuccess;
+        for (int nb = 0; nb < G.Nt && !e; nb += p.ch.tp_g)
+            e = launch_block_gather(p, R, pass_grid(p), nb, p.ch.tp_g, true, g, nullptr, Qe, s, tm);
+        if (e) return e;
+        k_grad_sum<<<(G.M + 7) / 8, 256, 0, s>>>(G, G.Nt / 64, Qe, p.t.sens_ent, dxy, p.t.status);
+        stage_mark(tm, 6);
+        return cudaGetLastError();
+    }
 #define NEDNER_GRAD(WT)                                                                                          \
     if (p.ch.tpl_adj == 2 && p.ch.threads_adj == 512)                                                             \
         k_ned_gather_rows2<WT, true, 512><<<grid, 512, p.ch.smem_grad, s>>>(G, 0, G.Nt, R, g, p.t.xrow_ptr,       \
@@ -824,9 +1046,9 @@ cudaError_t launch_grad_gather(const nedner_plan_s& p, const float2* R, const fl
                                                                       p.t.deconv_x, p.t.tw, nullptr, Qe)
     NEDNER_GATHER_SWITCH(NEDNER_GRAD)
 #undef NEDNER_GRAD
-    stage_mark(tm, 4);
-    k_grad_sum<<<(G.M + 7) / 8, 256, 0, s>>>(G, G.Nt / C, Qe, p.t.sens_ent, dxy, p.t.status);
     stage_mark(tm, 5);
+    k_grad_sum<<<(G.M + 7) / 8, 256, 0, s>>>(G, G.Nt / C, Qe, p.t.sens_ent, dxy, p.t.status);
+    stage_mark(tm, 6);
     return cudaGetLastError();
 }
 

@@ -13,22 +13,13 @@
 
 
 #include "fft.cuh"
+#include "async_copy.cuh"
 #include "internal.h"
 #include "ner_eval.cuh"
 #include "spread_window.cuh"
 
 namespace nedner {
 
-// asynchronous global -> shared copies (cp.async), completed per thread by
-// cp.async.wait_group; both addresses aligned to the copy size
-__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-    else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Stage (a), part 1: NED spreading (Eq. NED_NUFFT) fused with the x-FFT.

@@ -84,7 +84,9 @@ void free_sensor_tables(DevTables& t) {
     cudaFree(t.xent_gx); cudaFree(t.xent_gy); cudaFree(t.xrow_first);
     cudaFree(t.xent_rc); cudaFree(t.sens_ent);
     cudaFree(t.bseg); cudaFree(t.pent_bx); cudaFree(t.pent_w);
+    cudaFree(t.pent_gx); cudaFree(t.pent_gy); cudaFree(t.gseg);
     t.bseg = nullptr; t.pent_bx = nullptr; t.pent_w = nullptr;
+    t.pent_gx = nullptr; t.pent_gy = nullptr; t.gseg = nullptr;
     t.sens_bx = t.sens_by = nullptr;
     t.sens_wx = t.sens_wy = t.sens_dwx = t.sens_dwy = t.sens_fac = nullptr;
     t.row_ptr = t.row_m = nullptr;
@@ -306,8 +308,9 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     const int PW = (w + 3) / 4 * 4;
     const int nblk = G.Lx / 16;
     std::vector<int> pent_bx;
-    std::vector<float> pent_w;
+    std::vector<float> pent_w, pent_gx, pent_gy;
     std::vector<int2> bseg(C.split1 ? (size_t)G.Ly * nblk : 0);
+    std::vector<int2> gseg(C.split1 ? (size_t)G.Ly * nblk : 0);
     std::vector<XE> tmp;
     for (int r = 0; r < G.Ly; ++r) {
         tmp.clear();
@@ -327,7 +330,11 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
             xent_e.push_back(x.e);
             if (C.split1) {
                 pent_bx.push_back(x.bx);
-                for (int k = 0; k < PW; ++k) pent_w.push_back(k < w ? x.w * wx[(size_t)x.m * w + k] : 0.f);
+                for (int k = 0; k < PW; ++k) {
+                    pent_w.push_back(k < w ? x.w * wx[(size_t)x.m * w + k] : 0.f);
+                    pent_gx.push_back(k < w ? x.w * dwx[(size_t)x.m * w + k] : 0.f);
+                    pent_gy.push_back(k < w ? x.dw * wx[(size_t)x.m * w + k] : 0.f);
+                }
             }
             for (int k = 0; k < WT; ++k) {
                 const int t = k - off;
@@ -348,6 +355,15 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
                 if (hi < lo) hi = lo;
                 while (hi < Er && tmp[hi].bx < 16 * b + 16) ++hi;
                 bseg[(size_t)r * nblk + b] = make_int2(base + lo, base + hi);
+            }
+            // the block gather: entries whose first column is in block b
+            // (second copies of wrapped entries, at bx < 0, belong to none)
+            int a = 0;
+            for (int b = 0; b < nblk; ++b) {
+                while (a < Er && tmp[a].bx < 16 * b) ++a;
+                int z = a;
+                while (z < Er && tmp[z].bx < 16 * b + 16) ++z;
+                gseg[(size_t)r * nblk + b] = make_int2(base + a, base + z);
             }
         }
         // cut the columns so that each lane group's sweep costs about the same:
@@ -415,6 +431,9 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = upload(&p.t.bseg, bseg, s);
     if (!e) e = upload(&p.t.pent_bx, pent_bx, s);
     if (!e) e = upload(&p.t.pent_w, pent_w, s);
+    if (!e) e = upload(&p.t.pent_gx, pent_gx, s);
+    if (!e) e = upload(&p.t.pent_gy, pent_gy, s);
+    if (!e) e = upload(&p.t.gseg, gseg, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e == cudaErrorMemoryAllocation) return NEDNER_ENOMEM;
     return e ? NEDNER_ECUDA : NEDNER_OK;
@@ -500,6 +519,15 @@ void choose_chunks(nedner_plan_s& p) {
     c.thx = (int)((long)G.Lx * c.nbx / c.perx);
     c.smem_x = (size_t)((padded((long)G.Lx * c.nbx) + 1) & ~1L) * 8;
     c.tq = std::min(G.Nt, kChunkPref);
+    {
+        // block gather, per warp: two batches of 32 entries (first column,
+        // row-CSR index, sensor; taps; for the gradient a second tap set)
+        const long pw = (G.w + 3) / 4 * 4;
+        c.smem_ga = (size_t)4 * 2 * 32 * (3 + pw) * 4;
+        c.smem_gg = (size_t)4 * 2 * 32 * (3 + 2 * pw) * 4;
+    }
+    c.gsplit = 0;
+    c.tp_g = 0;
     // spread + x-FFT: lane groups of a full warp (32 time samples) while the
     // row fits in 128 KB of shared memory, smaller groups beyond
     c.c1 = std::min<long>(32, std::max<long>(2, pow2_floor((128L * 1024) / (8L * G.Lx))));
@@ -565,7 +593,7 @@ void choose_chunks(nedner_plan_s& p) {
     // transposed NER: line buffers, Ubar, then one line's items (value, first
     // grid point, w tap weights)
     c.smem3a = (size_t)(padded(G.Lt * c.lpc) + padded(G.nz * c.lpc)) * 8 +
-               (size_t)std::min(G.nz + 1, 1025) * (8 + 4 + 4 * G.w);
+               (size_t)std::min(G.nz + 1, 1025) * (8 + 4 + 4 * (G.w + 1));
     // inverse y- and x-FFTs: C <= 16 columns (conflict-free padded loads and
     // stores), N * C <= 2048 (16 values per thread of 128)
     c.c4 = (int)std::min<long>(std::min<long>(16, G.nz), 2048 / G.ny);
@@ -715,6 +743,16 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     cap = std::max(cap, extra);
     p->ch.tp_adj = Nt;
     while (p->ch.tp_adj > p->ch.ca && ents * p->ch.tp_adj * 4 > cap) p->ch.tp_adj /= 2;
+    // block gather: its pass grid Q-bar (Ly Lx tp_g floats) sits in region A
+    // after R-bar; passes no longer than the entry buffer's
+    {
+        const size_t rbar = (r_bytes + 255) / 256 * 256;
+        int tp = p->ch.tp_adj;
+        while (tp > 64 && rbar + (size_t)G.Ly * G.Lx * tp * 4 > p->region_a) tp /= 2;
+        p->ch.gsplit = (p->ch.split1 && tp >= 64 && rbar + (size_t)G.Ly * G.Lx * tp * 4 <= p->region_a) ? 1 : 0;
+        p->ch.tp_g = p->ch.gsplit ? tp : 0;
+        if (p->ch.gsplit) p->ch.tp_adj = tp;
+    }
     size_t pa_bytes = ents * p->ch.tp_adj * 4;
     size_t q_bytes = ents * (Nt / p->ch.ca) * 8;
     p->ws_bytes = p->region_a + std::max(std::max(gh_bytes, v_bytes), std::max(pa_bytes, q_bytes));

@@ -234,7 +234,8 @@ class Plan:
         _check(st, "nedner_forward_profiled")
         return dict(zip(self.FORWARD_KERNELS, [float(v) for v in ms]))
 
-    TRANSPOSED_KERNELS = ("img_xr2c_adj", "img_yfft_adj", "ner_lines_adj", "ned_yfft_adj", "gather", "entry_sum")
+    TRANSPOSED_KERNELS = ("img_xr2c_adj", "img_yfft_adj", "ner_lines_adj", "ned_yfft_adj", "ned_xfft_adj", "gather",
+                          "entry_sum")
 
     def adjoint_profiled(self, p0, out, stream=None):
         """adjoint() that also returns each stage's device time (ms), synchronously."""

@@ -75,8 +75,9 @@ def test_adjoint_and_gradient_flag_nonfinite_input(nd, case):
 def test_profiled_transposed_calls_match_plain_calls(nd):
     """The profiled adjoint and gradient give the plain calls' results (to
     FP32 rounding: the order of a few sums may differ between runs), and a
-    positive time for every stage (the gather summed over its passes: several
-    passes here, under a workspace limit)."""
+    positive time for every stage it launches (the gather summed over its
+    passes: several passes here, under a workspace limit; the transposed x-FFT
+    runs only with the block gather, else its time is zero)."""
     case = inputs.small_case(32, 32, 32, 400, 256, seed=43, layout="disc")
     rng = np.random.default_rng(44)
     p = torch.as_tensor(rng.standard_normal((case["nz"], case["ny"], case["nx"])), dtype=torch.float32,
@@ -88,10 +89,10 @@ def test_profiled_transposed_calls_match_plain_calls(nd):
         b = torch.empty_like(a)
         ms = plan.adjoint_profiled(p, b)
         check(b.cpu().numpy(), a.cpu().numpy(), 1e-6)
-        assert all(v > 0 for v in ms.values()), ms
+        assert all(v > 0 for k, v in ms.items() if k != "ned_xfft_adj") and ms["ned_xfft_adj"] >= 0, ms
         c = plan.grad_positions(g, p)
         d = torch.empty_like(c)
         ms = plan.grad_positions_profiled(g, p, d)
         check(d.cpu().numpy(), c.cpu().numpy(), 1e-6)
-        assert all(v > 0 for v in ms.values()), ms
+        assert all(v > 0 for k, v in ms.items() if k != "ned_xfft_adj") and ms["ned_xfft_adj"] >= 0, ms
         plan.close()
