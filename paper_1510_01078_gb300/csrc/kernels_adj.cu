@@ -650,11 +650,19 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_gather_rows2(Geo 
 // [nb, nb + Tp) (the transpose of the block spread and the x-FFT):
 //
 // k_ned_xfft_adj: one CTA per (grid row gy, 2 nbx samples of the pass)
-// rebuilds the real row (row_rebuild: inverse x-FFT of the Hermitian half
-// spectrum of R-bar, divided by phihat) and writes it to the pass's grid Qb
-// [Tp/32][Ly][Lx][32], the layout of the forward Q (with nbx = 16 each CTA
-// writes one contiguous block).
+// rebuilds the real row of the pass's grid Qb [Tp/32][Ly][Lx][32] (the layout
+// of the forward Q): the inverse x-FFT of the Hermitian half spectrum of
+// R-bar divided by phihat, two real samples packed per complex column as in
+// row_rebuild.  The packed spectrum H is nonzero only at k <= Lx/4 and
+// k >= 3 Lx/4, so the FFT's first pass skips the zero quarter points
+// (block_fft_ip's ZP), which also hold the raw R-bar values while they are
+// staged (loaded by asynchronous copies, all in flight at once).  The one
+// nonzero point there, H[Lx/4] (jx = nx/2), is added after the FFT as
+// H[Lx/4] i^gx.  With nbx = 16 each CTA writes one contiguous block.
 // ---------------------------------------------------------------------------
+// the padded row (the forward x-FFT's buffer) and H[Lx/4] of its nbx <= 16 columns
+static size_t xfft_adj_smem(const Chunks& c) { return c.smem_x + 16 * sizeof(float2); }
+
 template <int PER>
 __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_xfft_adj(Geo G, int nb, int nbx,
                                                                         const float2* __restrict__ R,
@@ -663,14 +671,50 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_xfft_adj(Geo G, 
                                                                         float* __restrict__ Qb) {
     extern __shared__ float4 smem4[];
     float2* Z = reinterpret_cast<float2*>(smem4);                    // padded [Lx][nbx]
+    float2* nyq = Z + ((padded_len(G.Lx * nbx) + 1) & ~1);           // [nbx]: H[Lx/4]
     const int gy = blockIdx.x;
     const int nc = blockIdx.y * 2 * nbx;                             // first sample of the CTA in the pass
     const int lnb = ilog2(nbx);
-    row_rebuild<PER>(G, 2 * nbx, R, gy, nb + nc, deconv_x, tw, Z);
+    const int half = G.nx / 2;                                       // Lx / 4
+    const int ys = (half + 1) << lnb;                                // Y2 of jx staged at row half + 1 + jx
+    const int nj = (half + 1) << lnb;
+    // raw R-bar: Y1 = R[jx][n + 2b] at row jx, Y2 = R[jx][n + 2b + 1] at row half + 1 + jx
+    const float2* src = R + (size_t)gy * G.Nt + nb + nc;
+    for (int it = threadIdx.x; it < nj; it += blockDim.x) {
+        const float2* q = src + (size_t)(it >> lnb) * G.Ly * G.Nt + 2 * (it & (nbx - 1));
+        cp_async(&Z[padx(it)], q, 8);
+        cp_async(&Z[padx(ys + it)], q + 1, 8);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    // H[0] = Re Y1[0] + i Re Y2[0]; H[jx] = (Y1 + i Y2) / 2 and
+    // H[Lx - jx] = (conj Y1 + i conj Y2) / 2 for 0 < jx <= nx/2 (rows written
+    // here never overlap the staged Y2 rows of other threads)
+    for (int it = threadIdx.x; it < nj; it += blockDim.x) {
+        const int jx = it >> lnb, b = it & (nbx - 1);
+        const float d = __ldg(&deconv_x[jx]);
+        const float2 y1 = cscale(Z[padx(it)], d), y2 = cscale(Z[padx(ys + it)], d);
+        if (jx == 0) {
+            Z[padx(it)] = make_float2(y1.x, y2.x);
+        } else {
+            const float2 hk = cscale(cadd(y1, mul_i(y2, +1)), 0.5f);
+            if (jx < half) Z[padx(it)] = hk;
+            else nyq[b] = hk;
+            Z[padx(((G.Lx - jx) << lnb) + b)] = cscale(cadd(cconj(y1), mul_i(cconj(y2), +1)), 0.5f);
+        }
+    }
+    block_fft_ip<PER, true>(Z, G.Lx, nbx, +1, tw);
     // samples nc .. nc + 2 nbx: group nc / 32 of 32, offset nc % 32
     float2* dst = reinterpret_cast<float2*>(Qb + ((size_t)(nc >> 5) * G.Ly + gy) * G.Lx * 32 + (nc & 31));
-    for (int it = threadIdx.x; it < (G.Lx << lnb); it += blockDim.x)
-        dst[(size_t)(it >> lnb) * 16 + (it & (nbx - 1))] = Z[padx(it)];
+    for (int it = threadIdx.x; it < (G.Lx << lnb); it += blockDim.x) {
+        const int gx = it >> lnb, b = it & (nbx - 1);
+        const float2 h = nyq[b];
+        const float2 z = Z[padx(it)];
+        const float2 hi = (gx & 1) ? make_float2(-h.y, h.x) : h;    // h i^(gx mod 2)
+        const float2 add = (gx & 2) ? make_float2(-hi.x, -hi.y) : hi;
+        dst[(size_t)gx * 16 + b] = cadd(z, add);
+    }
 }
 
 // k_ned_gather_blocks: one warp per (grid row, block of 16 columns, 64 time
@@ -770,21 +814,56 @@ __global__ void __launch_bounds__(128, 4) k_ned_gather_blocks(Geo G, int nb, int
         const int* d = st + (b & 1) * BSZ;
         const float* tp = reinterpret_cast<const float*>(d + 3 * BE);
         const int n = min(BE, nent - b * BE);
+        if (!GRAD) {
 #pragma unroll 1
-        for (int j = 0; j < n; ++j) {
-            const int dd = d[j] - c0;
-            const float2 va = block_taps_dot<W>(win, dd, tp + j * NTAP);
-            if (!GRAD) {
+            for (int j = 0; j < n; ++j) {
+                const float2 va = block_taps_dot<W>(win, d[j] - c0, tp + j * NTAP);
                 reinterpret_cast<float2*>(E + (size_t)d[BE + j] * Tp + nc)[tl >> 1] = va;
-            } else {
-                const float2 vb = block_taps_dot<W>(win, dd, tp + j * NTAP + PW);
-                const float2 gv = __ldg(reinterpret_cast<const float2*>(g + (size_t)d[2 * BE + j] * G.Nt + nb + nc + tl));
-                float sx = fmaf(gv.x, va.x, gv.y * va.y), sy = fmaf(gv.x, vb.x, gv.y * vb.y);
-                for (int o = 16; o > 0; o >>= 1) {
-                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+        } else {
+            // four entries at a time: their g loads in flight together, the
+            // eight sums (x and y per entry) reduced over the warp at once
+            // (8 values in 9 shuffles), lane 4 v ends with value v
+            for (int j0 = 0; j0 < n; j0 += 4) {
+                float2 gv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    gv[u] = (j0 + u < n) ? __ldg(reinterpret_cast<const float2*>(
+                                               g + (size_t)d[2 * BE + j0 + u] * G.Nt + nb + nc + tl))
+                                         : make_float2(0.f, 0.f);
+                float sv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+                for (int u = 0; u < 4; ++u) {
+                    float sx = 0.f, sy = 0.f;
+                    const int j = j0 + u;
+                    if (j < n) {
+                        const int dd = d[j] - c0;
+                        const float2 va = block_taps_dot<W>(win, dd, tp + j * NTAP);
+                        const float2 vb = block_taps_dot<W>(win, dd, tp + j * NTAP + PW);
+                        sx = fmaf(gv[0].x, va.x, gv[0].y * va.y);
+                        sy = fmaf(gv[0].x, vb.x, gv[0].y * vb.y);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) sv[i] = sv[i + 2];
+                    sv[6] = sx;
+                    sv[7] = sy;
+                    gv[0] = gv[1];
+                    gv[1] = gv[2];
+                    gv[2] = gv[3];
                 }
-                if (ln == 0) Qe[(size_t)d[BE + j] * (G.Nt >> 6) + ((nb + nc) >> 6)] = make_float2(sx, sy);
+                const bool h16 = ln & 16, h8 = ln & 8, h4 = ln & 4;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    sv[i] = (h16 ? sv[i + 4] : sv[i]) + __shfl_xor_sync(0xffffffffu, h16 ? sv[i] : sv[i + 4], 16);
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+                    sv[i] = (h8 ? sv[i + 2] : sv[i]) + __shfl_xor_sync(0xffffffffu, h8 ? sv[i] : sv[i + 2], 8);
+                float v = (h4 ? sv[1] : sv[0]) + __shfl_xor_sync(0xffffffffu, h4 ? sv[0] : sv[1], 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                const int vi = (ln >> 2) & 7, j = j0 + (vi >> 1);
+                if ((ln & 3) == 0 && j < n)
+                    reinterpret_cast<float*>(Qe)[2 * ((size_t)d[BE + j] * (G.Nt >> 6) + ((nb + nc) >> 6)) + (vi & 1)] = v;
             }
         }
         __syncwarp();
@@ -864,8 +943,8 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p) {
     if ((e = cudaFuncSetAttribute(k_ned_gather_rows2<WT, true, 512>, (cudaFuncAttribute)a, (int)c.smem_grad))) return e;
     NEDNER_ATTR_GATHER2(8) NEDNER_ATTR_GATHER2(12) NEDNER_ATTR_GATHER2(16) NEDNER_ATTR_GATHER2(20)
 #undef NEDNER_ATTR_GATHER2
-    if ((e = cudaFuncSetAttribute(k_ned_xfft_adj<16>, (cudaFuncAttribute)a, (int)c.smem_x))) return e;
-    if ((e = cudaFuncSetAttribute(k_ned_xfft_adj<32>, (cudaFuncAttribute)a, (int)c.smem_x))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_xfft_adj<16>, (cudaFuncAttribute)a, (int)xfft_adj_smem(c)))) return e;
+    if ((e = cudaFuncSetAttribute(k_ned_xfft_adj<32>, (cudaFuncAttribute)a, (int)xfft_adj_smem(c)))) return e;
 #define NEDNER_ATTR_BG(W)                                                                                   \
     if ((e = cudaFuncSetAttribute(k_ned_gather_blocks<W, false>, (cudaFuncAttribute)a, (int)c.smem_ga))) return e; \
     if ((e = cudaFuncSetAttribute(k_ned_gather_blocks<W, true>, (cudaFuncAttribute)a, (int)c.smem_gg))) return e;
@@ -932,9 +1011,9 @@ static cudaError_t launch_block_gather(const nedner_plan_s& p, const float2* R, 
     const Geo& G = p.geo;
     const dim3 gx(G.Ly, Tp / (2 * p.ch.nbx));
     if (p.ch.perx <= 16)
-        k_ned_xfft_adj<16><<<gx, p.ch.thx, p.ch.smem_x, s>>>(G, nb, p.ch.nbx, R, p.t.deconv_x, p.t.tw, Qb);
+        k_ned_xfft_adj<16><<<gx, p.ch.thx, xfft_adj_smem(p.ch), s>>>(G, nb, p.ch.nbx, R, p.t.deconv_x, p.t.tw, Qb);
     else
-        k_ned_xfft_adj<32><<<gx, p.ch.thx, p.ch.smem_x, s>>>(G, nb, p.ch.nbx, R, p.t.deconv_x, p.t.tw, Qb);
+        k_ned_xfft_adj<32><<<gx, p.ch.thx, xfft_adj_smem(p.ch), s>>>(G, nb, p.ch.nbx, R, p.t.deconv_x, p.t.tw, Qb);
     stage_mark(tm, 4);
     const dim3 grid(G.Ly * (G.Lx / 16) / 4, Tp / 64);
 #define NEDNER_BG(W)                                                                                              \
