@@ -704,16 +704,30 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_xfft_adj(Geo G, 
             Z[padx(((G.Lx - jx) << lnb) + b)] = cscale(cadd(cconj(y1), mul_i(cconj(y2), +1)), 0.5f);
         }
     }
-    block_fft_ip<PER, true>(Z, G.Lx, nbx, +1, tw);
+    // log2 Lx = 1 mod 4: the last radix-2 pass is done in the output loop
+    const bool fold = (ilog2(G.Lx) & 3) == 1;
+    block_fft_ip<PER, true>(Z, G.Lx, nbx, +1, tw, fold);
     // samples nc .. nc + 2 nbx: group nc / 32 of 32, offset nc % 32
-    float2* dst = reinterpret_cast<float2*>(Qb + ((size_t)(nc >> 5) * G.Ly + gy) * G.Lx * 32 + (nc & 31));
-    for (int it = threadIdx.x; it < (G.Lx << lnb); it += blockDim.x) {
-        const int gx = it >> lnb, b = it & (nbx - 1);
-        const float2 h = nyq[b];
-        const float2 z = Z[padx(it)];
-        const float2 hi = (gx & 1) ? make_float2(-h.y, h.x) : h;    // h i^(gx mod 2)
-        const float2 add = (gx & 2) ? make_float2(-hi.x, -hi.y) : hi;
-        dst[(size_t)gx * 16 + b] = cadd(z, add);
+    float2* dst = reinterpret_cast<float2*>(Qb + ((size_t)(nc >> 5) * G.Ly + gy) * G.Lx * 32 + (nc & 31)) +
+                  (threadIdx.x & (nbx - 1));
+    // every thread keeps one column b; its points gx step by blockDim / nbx =
+    // Lx / PER >= 4, a multiple of 4, so i^gx (the H[Lx/4] term) is fixed
+    const int b = threadIdx.x & (nbx - 1);
+    const int k0 = threadIdx.x >> lnb, ks = blockDim.x >> lnb;
+    const float2 h = nyq[b];
+    const float2 hi = (k0 & 1) ? make_float2(-h.y, h.x) : h;
+    const float2 add = (k0 & 2) ? make_float2(-hi.x, -hi.y) : hi;
+    if (fold) {
+        // x[k] = s[k] + w^k s[k + Lx/2], x[k + Lx/2] = s[k] - w^k s[k + Lx/2],
+        // w = exp(+2 pi i / Lx); i^(k + Lx/2) = i^k
+        const int H = G.Lx >> 1;
+        for (int k = k0; k < H; k += ks) {
+            const float2 s0 = Z[padx((k << lnb) + b)], s1 = cmul(cconj(__ldg(&tw[G.Lx + k])), Z[padx(((k + H) << lnb) + b)]);
+            dst[(size_t)k * 16] = cadd(cadd(s0, s1), add);
+            dst[(size_t)(k + H) * 16] = cadd(csub(s0, s1), add);
+        }
+    } else {
+        for (int k = k0; k < G.Lx; k += ks) dst[(size_t)k * 16] = cadd(Z[padx((k << lnb) + b)], add);
     }
 }
 
@@ -733,10 +747,18 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_xfft_adj(Geo G, 
 // ---------------------------------------------------------------------------
 template <int W, int D>
 __device__ __forceinline__ float2 taps_dot(const float2 (&win)[32], const float* t) {
-    float2 v = make_float2(0.f, 0.f);
+    // four independent accumulators (tap k into k mod 4), taps read as float4
+    const float4* t4 = reinterpret_cast<const float4*>(t);
+    float2 a[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-    for (int k = 0; k < W; ++k) v = __ffma2_rn(make_float2(t[k], t[k]), win[D + k], v);
-    return v;
+    for (int k4 = 0; k4 < (W + 3) / 4; ++k4) {
+        const float4 q = t4[k4];
+        const float tk[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (4 * k4 + r < W) a[r] = __ffma2_rn(make_float2(tk[r], tk[r]), win[D + 4 * k4 + r], a[r]);
+    }
+    return __fadd2_rn(__fadd2_rn(a[0], a[1]), __fadd2_rn(a[2], a[3]));
 }
 
 template <int W>
