@@ -318,20 +318,6 @@ def run_reference(args, cfg, voxels, rank, world):
 # --------------------------------------------------------------------------
 # the GPU arm
 # --------------------------------------------------------------------------
-def transposed_passes(cfg) -> int:
-    """Passes of time samples of the transposed gather (the plan's rule, no
-    workspace limit): its entry buffer of M w floats per sample must fit in
-    max(Ghat, V, 256 MB)."""
-    M, Nt, nx, ny, nz, w = cfg["sensor_xy"].shape[0], cfg["Nt"], cfg["nx"], cfg["ny"], cfg["nz"], 12
-    nxh = nx // 2 + 1
-    cap = max(nxh * (ny + 1) * Nt * 8, nxh * ny * nz * 8, 256 << 20)
-    ca = 64 if (2 * nx <= 512 and Nt >= 64) else None
-    tp = Nt
-    while (ca is None or tp > ca) and tp > 1 and M * w * tp * 4 > cap:
-        tp //= 2
-    return Nt // tp
-
-
 def timed_loop(fn, steps, flush):
     """Calls fn() `steps` times after an L2 flush each; fn returns a dict of
     per-kernel device times (ms).  Returns the per-kernel lists."""
@@ -342,6 +328,51 @@ def timed_loop(fn, steps, flush):
         for k, v in ms.items():
             per.setdefault(k, []).append(v)
     return per
+
+
+def cufft_comparison(cfg, dev, flush, reps, ours):
+    """cuFFT (through torch.fft), timed as a reference point only, on the
+    transforms our FFT stages contain: the 2-D real FFT of the oversampled
+    grid per time sample (stage a2 without the crop, deconvolution and our
+    layout), the zero-padded length-2Nt line FFT of the NER (without its
+    interpolation and z-IFFT) and the 2-D inverse real FFT per depth plane
+    (stage d).  ``ours``: our kernels' ms for the same stages."""
+    import torch
+    nx, ny, nz, Nt = cfg["nx"], cfg["ny"], cfg["nz"], cfg["Nt"]
+    Lx, Ly = 2 * nx, 2 * ny
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def time_op(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            ev0.record()
+            fn()
+            ev1.record()
+            ev1.synchronize()
+            ts.append(ev0.elapsed_time(ev1))
+        return round(sum(ts) / len(ts), 5)
+
+    out = {"library": "cuFFT via torch.fft %s" % torch.__version__, "note": "reference point only, not on the "
+           "product path; each transform alone, inputs in HBM, L2 flushed before each call"}
+    q = torch.randn((Nt, Ly, Lx), dtype=torch.float32, device=dev)
+    out["ned_rfft2"] = {"shape": [Nt, Ly, Lx], "ms": time_op(lambda: torch.fft.rfft2(q)),
+                        "ours_ms": ours.get("ned_xy"), "ours": "ned_xfft + ned_yfft (with crop, deconvolution)"}
+    del q
+    G = torch.randn(((nx // 2 + 1) * (ny + 1), Nt), dtype=torch.complex64, device=dev)
+    out["ner_line_fft"] = {"shape": [G.shape[0], Nt], "n": 2 * Nt,
+                           "ms": time_op(lambda: torch.fft.fft(G, n=2 * Nt, dim=-1)),
+                           "ours_ms": ours.get("ner"), "ours": "ner_lines (line FFT, 12-tap interpolation, "
+                                                                "Jacobian and z-IFFT)"}
+    del G
+    V = torch.randn((nz, ny, nx // 2 + 1), dtype=torch.complex64, device=dev)
+    out["image_irfft2"] = {"shape": [nz, ny, nx // 2 + 1], "ms": time_op(lambda: torch.fft.irfft2(V, s=(ny, nx))),
+                           "ours_ms": ours.get("image"), "ours": "img_yifft + img_xc2r"}
+    del V
+    torch.cuda.empty_cache()
+    return out
 
 
 def kernel_table(per, abytes):
@@ -355,12 +386,16 @@ def kernel_table(per, abytes):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=80)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="nedner", choices=["nedner", "reference"])
     ap.add_argument("--config", default="c3", choices=sorted(CONFIGS))
+    ap.add_argument("--nt", type=int, default=None,
+                    help="record length override (nz scaled with it): the workload's lateral geometry and kernels "
+                         "on a smaller case, for profiler captures; not a bench line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-transposed", action="store_true", help="time the forward only")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT reference timings")
     ap.add_argument("--oracle-fraction", type=float, default=0.01,
                     help="fraction of lateral lines of the accuracy check / cpu_baseline sample")
     ap.add_argument("--reference-fraction", type=float, default=0.001,
@@ -375,7 +410,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     from paper_1510_01078_gb300 import inputs
-    cfg = inputs.make_config(CONFIGS[args.config])
+    cfg = inputs.make_config(CONFIGS[args.config], Nt=args.nt)
     voxels = cfg["nx"] * cfg["ny"] * cfg["nz"]
 
     if args.impl == "reference":
@@ -477,7 +512,8 @@ def main():
 
     transposed = None
     interp_roofline = None
-    passes = transposed_passes(cfg)
+    info = plan.info()
+    passes = cfg["Nt"] // info["tp_adj"]
     if do_t:
         aa, ak = kernel_table(per_adj, algorithmic_bytes_transposed(cfg, False, split))
         ga, gk = kernel_table(per_grad, algorithmic_bytes_transposed(cfg, True, split))
@@ -488,27 +524,35 @@ def main():
                       "grad_positions": {"ms": round(grad_ms, 4),
                                          "voxels_per_s": whole_job_value(voxels, world, grad_ms), "kernels": gk}}
         gb = gather_alg_bytes(cfg)
-        gms = aa.get("ned_xfft_adj", 0.0) + aa["gather"] + aa["entry_sum"]
-        tg = traffic_for("gather", cfg["name"])
+        parts = [k for k in ("ned_xfft_adj", "gather", "entry_sum") if k in aa]
+        gms = sum(aa[k] for k in parts)
+        tr = [traffic_for(k, cfg["name"]) for k in parts]
         interp_roofline = {"bound": "hbm",
-                           "kernel": "adjoint transposed x-FFT + gather + entry sum (transposed interpolation)",
+                           "kernel": "adjoint " + " + ".join(parts) + " (transposed interpolation)",
                            "achieved": round(gb / (gms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                            "frac": round(gb / (gms * 1e-3) / 1e9 / peak, 4),
-                           "traffic": None if tg is None else tg * passes,
-                           "traffic_note": "DRAM bytes of the %d gather launches of one adjoint (entry sum not captured)"
-                                           % passes,
+                           "traffic": None if any(t is None for t in tr) else sum(tr) * passes,
+                           "traffic_note": ("DRAM bytes of one launch of each of %s, times the %d passes of one "
+                                            "adjoint" % (", ".join(parts), passes)),
+                           "alg_bytes": gb, "alg_note": "read the grid rows R once, write g once",
                            "peak_source": peak_kind}
 
-    # kernels launched in the timed region: five per reconstruction for the NUFFT
-    # path; the tensor-core stage a runs prep + two GEMMs per pass of 512 time
-    # samples, then the Nyquist line, plus the scale reduction in FP16 mode
-    if args.ned_mode == "nufft":
-        ws = nedner.work_split(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Nt"], 12)
-        fwd_launches = 3 * (cfg["Nt"] // ws["tq"]) + 3 if ws["split1"] else 5
-    else:
-        fwd_launches = 3 * (cfg["Nt"] // min(512, cfg["Nt"])) + 1 + 3 + (1 if args.ned_mode == "tensor_fp16" else 0)
-    t_launches = (4 + 2 * passes) + 6 if do_t else 0
+    # kernels launched in the timed region: the plan's own count per call
+    # (forward, adjoint, gradient; nedner_plan_info)
+    fwd_launches = info["launches_forward"]
+    t_launches = info["launches_adjoint"] + info["launches_grad_positions"] if do_t else 0
     launches = (fwd_launches + t_launches) * args.steps
+
+    cufft = None
+    if rank == 0 and not args.no_cufft:
+        try:
+            ours = {"ned_xy": (round(avg["ned_xfft"] + avg["ned_yfft"], 5)
+                               if "ned_xfft" in avg and "ned_yfft" in avg else None),
+                    "ner": round(avg["ner_lines"], 5) if "ner_lines" in avg else None,
+                    "image": round(avg.get("img_yifft", 0.0) + avg.get("img_xc2r", 0.0), 5)}
+            cufft = cufft_comparison(cfg, dev, flush, min(args.steps, 10), ours)
+        except Exception as ex:  # a reference point, not required
+            cufft = {"failed": str(ex)}
 
     cpu = None
     tol = {"nufft": 1e-5, "tensor_bf16": 3e-5, "tensor_fp16": 1e-5}[args.ned_mode]
@@ -557,7 +601,7 @@ def main():
                            "parallelism": "independent reconstruction per GPU", "ned_mode": args.ned_mode},
                 "roofline": roofline, "spread_frac_of_peak": spread_frac, "interp_roofline": interp_roofline,
                 "accuracy": accuracy, "kernels": kernels, "transposed": transposed,
-                "cpu_baseline": cpu, "clocks": clk, "device_status_flags": status_flags,
+                "cpu_baseline": cpu, "cufft_comparison": cufft, "clocks": clk, "device_status_flags": status_flags,
                 "e2e": {"value": whole_job_value(voxels, world, e2e_step), "unit": "voxels/s",
                         "h2d_bytes_per_step": int(g_host.numel() * 4), "d2h_bytes_per_step": int(p_host.numel() * 4)},
                 "gpu_launches": launches,

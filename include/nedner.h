@@ -286,6 +286,67 @@ nedner_status nedner_debug_set_wait_limit(nedner_plan_t plan, int polls);
 size_t nedner_workspace_bytes(nedner_plan_t plan);
 
 /*
+ * Data low-pass against spatial aliasing (Sec. 8): sensor m's time series
+ * keeps the frequencies |f| <= f_cut,m = c / (2 dx_m), dx_m the distance
+ * from sensor m to its nearest neighbour (the local sensor spacing; no
+ * filtering for a lone sensor).  Ideal filter on the length-Nt DFT of each
+ * series: bins k with |k| <= floor(f_cut,m Nt dt) are kept (the rest set to
+ * zero), out = the inverse DFT.  The cut-off bins are computed on the host
+ * from the plan's positions (nedner_plan, nedner_set_positions).
+ *   g, out: device, M x Nt float32, sensor-major, t contiguous (caller
+ *           owned; 4-byte aligned; out may equal g).
+ * Returns NEDNER_EINVAL for a null plan or pointer or a misaligned buffer,
+ * NEDNER_ECUDA on a launch failure.  Asynchronous on `stream`.
+ */
+nedner_status nedner_lowpass(nedner_plan_t plan, const float* g, float* out, void* stream);
+
+/*
+ * The low-pass's highest kept bin per sensor (host copy, M values written to
+ * out while nout allows).  Returns 0, or -1 for a null plan (or a null out
+ * with nout > 0).
+ */
+int nedner_lowpass_bins(nedner_plan_t plan, int* out, int64_t nout);
+
+/*
+ * Tenenbaum sharpness of B images (Appendix B): for image b (ny x nx, x
+ * fastest) F[b] = (1 / (nx ny)) sum over the pixels whose 3 x 3
+ * neighbourhood lies in the image of (S_x * U)^2 + (S_y * U)^2, S_x the
+ * Sobel operator [-1 0 1; -2 0 2; -1 0 1] and S_y its transpose; summed in
+ * FP64 in a fixed order (deterministic).
+ *   U: device, B x ny x nx float32 (4-byte aligned); F: device, B doubles
+ *   (8-byte aligned).  Caller owned.
+ * Returns NEDNER_EINVAL for negative sizes, null or misaligned pointers.
+ */
+nedner_status nedner_tenenbaum(const float* U, int64_t B, int ny, int nx, double* F, void* stream);
+
+/*
+ * Maximum intensity projection of a volume (nz, ny, nx), x fastest, along
+ * axis 0 (z: out is ny x nx), 1 (y: nz x nx) or 2 (x: nz x ny).  Device
+ * float32 buffers, caller owned, 4-byte aligned.  Returns NEDNER_EINVAL for
+ * non-positive sizes, a bad axis or null/misaligned pointers.
+ */
+nedner_status nedner_mip(const float* vol, int nz, int ny, int nx, int axis, float* out, void* stream);
+
+/*
+ * The plan's passes over time, as chosen at nedner_plan for its geometry,
+ * sensor count and workspace limit (host only, no device work).  Writes up
+ * to nout values to out (host), in this order:
+ *   [0] split:  1 if stage (a) runs as block spread + x-FFT + y-FFT kernels
+ *               (and the transposed interpolation as transposed x-FFT +
+ *               block gather), 0 for the fused spread and row gather;
+ *   [1] tq:     time samples per chunk of the split stage (a);
+ *   [2] tp_adj: time samples per pass of the adjoint's gather;
+ *   [3] gsplit: 1 if the adjoint and gradient use the block gather;
+ *   [4] tp_g:   time samples per pass of the gradient's block gather (0 if
+ *               gsplit is 0: one pass over the whole record);
+ *   [5] kernel launches of one nedner_forward, [6] of one nedner_adjoint,
+ *       [7] of one nedner_grad_positions (this library's kernels only).
+ * Returns the number of values available (8), or -1 for a null plan or out.
+ * No paper counterpart.
+ */
+int nedner_plan_info(nedner_plan_t plan, int64_t* out, int nout);
+
+/*
  * The work split a plan of this geometry uses (sigma = 2, window width w),
  * computed on the host without a device, so that the kernels' size
  * conditions can be checked for every geometry.  Writes up to nout values to

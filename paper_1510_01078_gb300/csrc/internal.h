@@ -109,6 +109,7 @@ struct DevTables {
     float* pent_gy = nullptr;     // [E'][4 ceil(w/4)] the same with the y-tap derivative
     int2* gseg = nullptr;         // [Ly][Lx/16] entries whose first column lies in the block (block gather)
     int* status = nullptr;        // device flags: NEDNER_FLAG_NONFINITE when an output kernel wrote a non-finite value
+    int* lp_kcut = nullptr;       // [M] highest kept frequency bin of the data low-pass (nedner_lowpass)
 };
 
 // Stage timer of the profiled entry points (defined in nedner_api.cu): marks
@@ -144,6 +145,7 @@ struct nedner_plan_s {
     double dt = 0, c = 0, sigma = 2;
     nedner_grid grid{};
     std::vector<double> xy, h;
+    std::vector<int> lp_kcut;     // host copy of t.lp_kcut
     nedner::DevTables t;
     nedner::TapPoly tap{};
     nedner::TPState tp;
@@ -194,6 +196,12 @@ cudaError_t configure_adj_kernels(const nedner_plan_s& p);
 // tensor-product NED (kernels_tp.cu)
 cudaError_t configure_tp_kernels();
 cudaError_t launch_tp_ned(const nedner_plan_s& p, const float* g, float2* Ghat, cudaStream_t s);
+int tp_chunk(int Nt);   // time samples per pass of the tensor-core stage (a)
+// data low-pass (kernels_util.cu): each sensor's distance to its nearest
+// neighbour (infinite for a lone sensor), and the highest kept DFT bin of
+// f_cut = c / (2 dx_m)
+std::vector<double> nearest_neighbour_distance(const std::vector<double>& xy, int64_t M, double X, double Y);
+std::vector<int> lowpass_bins(const nedner_plan_s& p);
 size_t tp_work_bytes(int Nt);
 constexpr int TP_SENSORS = 128;   // sensors per axis the tensor-core path is built for
 constexpr int TP_WAIT_LIMIT = 1 << 26;   // polls of a bounded mbarrier wait

@@ -84,9 +84,9 @@ void free_sensor_tables(DevTables& t) {
     cudaFree(t.xent_gx); cudaFree(t.xent_gy); cudaFree(t.xrow_first);
     cudaFree(t.xent_rc); cudaFree(t.sens_ent);
     cudaFree(t.bseg); cudaFree(t.pent_bx); cudaFree(t.pent_w);
-    cudaFree(t.pent_gx); cudaFree(t.pent_gy); cudaFree(t.gseg);
+    cudaFree(t.pent_gx); cudaFree(t.pent_gy); cudaFree(t.gseg); cudaFree(t.lp_kcut);
     t.bseg = nullptr; t.pent_bx = nullptr; t.pent_w = nullptr;
-    t.pent_gx = nullptr; t.pent_gy = nullptr; t.gseg = nullptr;
+    t.pent_gx = nullptr; t.pent_gy = nullptr; t.gseg = nullptr; t.lp_kcut = nullptr;
     t.sens_bx = t.sens_by = nullptr;
     t.sens_wx = t.sens_wy = t.sens_dwx = t.sens_dwy = t.sens_fac = nullptr;
     t.row_ptr = t.row_m = nullptr;
@@ -434,6 +434,8 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = upload(&p.t.pent_gx, pent_gx, s);
     if (!e) e = upload(&p.t.pent_gy, pent_gy, s);
     if (!e) e = upload(&p.t.gseg, gseg, s);
+    p.lp_kcut = lowpass_bins(p);
+    if (!e) e = upload(&p.t.lp_kcut, p.lp_kcut, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e == cudaErrorMemoryAllocation) return NEDNER_ENOMEM;
     return e ? NEDNER_ECUDA : NEDNER_OK;
@@ -943,6 +945,22 @@ nedner_status nedner_debug_set_wait_limit(nedner_plan_t p, int polls) {
 }
 
 size_t nedner_workspace_bytes(nedner_plan_t p) { return p ? p->ws_bytes : 0; }
+
+int nedner_plan_info(nedner_plan_t p, int64_t* out, int nout) {
+    if (!p || !out || nout < 0) return -1;
+    const Geo& G = p->geo;
+    const Chunks& c = p->ch;
+    int64_t fwd;
+    if (p->tp.enabled) fwd = 3 * (G.Nt / tp_chunk(G.Nt)) + 1 + (p->tp.fp16 ? 1 : 0) + 3;   // passes, Nyquist line, scale; NER, images
+    else if (c.split1) fwd = 3 * (G.Nt / c.tq) + 3;                                     // spread, x-FFT, y-FFT per chunk
+    else fwd = 5;
+    const int64_t adj = p->M == 0 ? 0 : 4 + (int64_t)(c.gsplit ? 3 : 2) * (G.Nt / c.tp_adj);
+    const int64_t grad = p->M == 0 ? 0 : 4 + (c.gsplit ? 2 * (int64_t)(G.Nt / c.tp_g) + 1 : 2);
+    const int64_t v[] = {c.split1, c.tq, c.tp_adj, c.gsplit, c.tp_g, fwd, adj, grad};
+    const int n = (int)(sizeof(v) / sizeof(v[0]));
+    for (int i = 0; i < n && i < nout; ++i) out[i] = v[i];
+    return n;
+}
 
 int nedner_work_split(int nx, int ny, int nz, int Nt, int w, int64_t* out, int nout) {
     if (!out || nout < 0) return -1;

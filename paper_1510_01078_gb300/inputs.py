@@ -156,10 +156,13 @@ def voxelise(balls: Balls, nx, ny, nz, dx, dy, dz) -> np.ndarray:
 CONFIG_NAMES = ["c1_tiny_fp64", "c2_fp32_64x64", "c3_paper_scale", "c4_differentiation", "c5_tensor_gemm"]
 
 
-def make_config(idx: int, with_data: bool = True) -> Dict:
+def make_config(idx: int, with_data: bool = True, Nt: Optional[int] = None) -> Dict:
     """Workload ``idx`` (0..4); seed 1510 + idx.  Returns a dict with the
     geometry (sensor_xy, h, Nt, dt, c, nx, ny, nz, dx, dy, dz), the phantom and,
-    if ``with_data``, the float64 data g (M, Nt)."""
+    if ``with_data``, the float64 data g (M, Nt).  ``Nt`` shortens (or
+    lengthens) the record, nz scaled with it so that dz stays the same: the
+    same lateral geometry and kernels on a smaller case."""
+    nt_req = Nt
     rng = np.random.default_rng(1510 + idx)
     c = C_SOUND
     extra: Dict = {}
@@ -206,10 +209,17 @@ def make_config(idx: int, with_data: bool = True) -> Dict:
         extra = {"xs": xs, "ys": ys}
     else:
         raise ValueError("config index must be 0..4")
+    Nt0 = Nt
+    if nt_req is not None and nt_req != Nt:
+        if nt_req < 16 or nt_req & (nt_req - 1) or (nz * nt_req) % Nt:
+            raise ValueError("Nt must be a power of two >= 16 that keeps nz whole")
+        nz = nz * nt_req // Nt
+        Nt = int(nt_req)
     dx = X / nx
     dy = X / ny
     dz = c * Nt * dt / nz          # Z = c Nt dt: the record spans the periodic depth range
-    cfg = dict(name=CONFIG_NAMES[idx], sensor_xy=xy, h=h, Nt=Nt, dt=dt, c=c, nx=nx, ny=ny, nz=nz,
+    name = CONFIG_NAMES[idx] + ("" if nt_req is None or nt_req == Nt0 else "_nt%d" % Nt)
+    cfg = dict(name=name, sensor_xy=xy, h=h, Nt=Nt, dt=dt, c=c, nx=nx, ny=ny, nz=nz,
                dx=dx, dy=dy, dz=dz, balls=balls, snr_db=snr, seed=1510 + idx, **extra)
     if with_data:
         g = nwave_data(xy, balls, Nt, dt, c)

@@ -65,6 +65,11 @@ SIGNATURES = {
     "nedner_grad_positions_profiled": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
     "nedner_ned_stage_static": (ctypes.c_int, [_P, _P, _P, _P]),
     "nedner_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "nedner_plan_info": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "nedner_lowpass": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nedner_lowpass_bins": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "nedner_tenenbaum": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "nedner_mip": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
     "nedner_work_split": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "nedner_forward_host": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -189,6 +194,35 @@ class Plan:
     @property
     def workspace_bytes(self) -> int:
         return int(_load().nedner_workspace_bytes(self._handle))
+
+    def lowpass(self, g, out=None, stream=None):
+        """Data low-pass of Sec. 8 (nedner_lowpass): each sensor's series cut at
+        c / (2 x its nearest-neighbour distance); (M, Nt) float32 CUDA tensors."""
+        import torch
+        if out is None:
+            out = torch.empty((self.M, self.Nt), dtype=torch.float32, device=g.device)
+        st = _load().nedner_lowpass(self._handle, _dev_ptr(g, torch.float32, (self.M, self.Nt), "g"),
+                                    _dev_ptr(out, torch.float32, (self.M, self.Nt), "out"), _stream_ptr(stream))
+        _check(st, "nedner_lowpass")
+        return out
+
+    def lowpass_bins(self) -> np.ndarray:
+        """Highest kept DFT bin of each sensor's low-pass (host)."""
+        out = np.zeros(self.M, dtype=np.int32)
+        if _load().nedner_lowpass_bins(self._handle, out.ctypes.data if self.M else None, self.M) != 0:
+            raise NednerError(EINVAL, "nedner_lowpass_bins")
+        return out
+
+    PLAN_INFO_FIELDS = ("split", "tq", "tp_adj", "gsplit", "tp_g", "launches_forward", "launches_adjoint",
+                        "launches_grad_positions")
+
+    def info(self) -> dict:
+        """The plan's passes over time and kernel launches per call (nedner_plan_info)."""
+        out = (ctypes.c_int64 * len(self.PLAN_INFO_FIELDS))()
+        n = _load().nedner_plan_info(self._handle, out, len(out))
+        if n < 0:
+            raise NednerError(EINVAL, "nedner_plan_info")
+        return dict(zip(self.PLAN_INFO_FIELDS, [int(v) for v in out[:n]]))
 
     def set_positions(self, sensor_xy):
         xy = np.ascontiguousarray(np.asarray(sensor_xy, dtype=np.float64).reshape(self.M, 2))
@@ -348,27 +382,52 @@ def _model_autograd():
 
     class ModelFunction(torch.autograd.Function):
         """g = R^T p0 (nedner_adjoint) as a differentiable op; its backward is
-        nedner_forward.  With an unweighted plan this is the physical forward
-        model A (data from an initial pressure), A^T being the unweighted R."""
+        nedner_forward for p0 and, for the sensor positions,
+        d/dx <dL/dg, R(x)^T p0> = d/dx <R(x) dL/dg, p0>, i.e.
+        nedner_grad_positions with (g, dL/dp0) = (dL/dg, p0).  With an
+        unweighted plan this is the physical forward model A (data from an
+        initial pressure), A^T being the unweighted R."""
 
         @staticmethod
-        def forward(ctx, p0, plan):
+        def forward(ctx, p0, sensor_xy, plan):
             ctx.plan = plan
+            ctx.xy_like = (sensor_xy.device, sensor_xy.dtype)
+            ctx.save_for_backward(p0)
             return plan.adjoint(p0.contiguous())
 
         @staticmethod
         def backward(ctx, dL_dg):
-            return ctx.plan.forward(dL_dg.contiguous()), None
+            (p0,) = ctx.saved_tensors
+            dL_dg = dL_dg.contiguous()
+            dp0 = ctx.plan.forward(dL_dg) if ctx.needs_input_grad[0] else None
+            dxy = None
+            if ctx.needs_input_grad[1]:
+                dxy = ctx.plan.grad_positions(dL_dg, p0.contiguous()).to(device=ctx.xy_like[0],
+                                                                          dtype=ctx.xy_like[1])
+            return dp0, dxy, None
 
     return ModelFunction
 
 
-def model(plan: Plan, p0):
-    """Differentiable g = R^T p0 (see ``ModelFunction``)."""
+def _move(plan: Plan, sensor_xy):
+    """The positions tensor to differentiate against; moves the plan there
+    first (nedner_set_positions) when they differ from the plan's."""
+    import torch
+    if sensor_xy is None:
+        return torch.as_tensor(plan._xy)
+    xy = sensor_xy.detach().to("cpu", torch.float64).numpy()
+    if not np.array_equal(xy, plan._xy):
+        plan.set_positions(xy)
+    return sensor_xy
+
+
+def model(plan: Plan, p0, sensor_xy=None):
+    """Differentiable g = R^T p0 (see ``ModelFunction``); ``sensor_xy`` as in
+    ``reconstruct``."""
     global _MODEL
     if _MODEL is None:
         _MODEL = _model_autograd()
-    return _MODEL.apply(p0, plan)
+    return _MODEL.apply(p0, _move(plan, sensor_xy), plan)
 
 
 def reconstruct(plan: Plan, g, sensor_xy=None):
@@ -379,19 +438,42 @@ def reconstruct(plan: Plan, g, sensor_xy=None):
     global _RECON
     if _RECON is None:
         _RECON = _autograd()
-    import torch
-    if sensor_xy is not None:
-        xy = sensor_xy.detach().to("cpu", torch.float64).numpy()
-        if not np.array_equal(xy, plan._xy):
-            plan.set_positions(xy)
-    else:
-        sensor_xy = torch.as_tensor(plan._xy)
-    return _RECON.apply(g, sensor_xy, plan)
+    return _RECON.apply(g, _move(plan, sensor_xy), plan)
 
 
 WORK_SPLIT_FIELDS = ("c1", "c2f", "c4", "c5", "groups1", "threads1", "per1", "tpl1", "ca", "per_adj", "tpl_adj",
                      "threads_adj", "lpc", "threads3", "smem1", "smem2f", "smem3", "smem4", "smem5", "smem_adj",
                      "smem_grad", "split1", "tq", "wpc_s", "nbx", "thx", "perx", "smem_s", "smem_x", "smem3a")
+
+
+def tenenbaum(U, stream=None):
+    """Tenenbaum sharpness (Appendix B) of an image (ny, nx) or a batch (B, ny,
+    nx) of float32 CUDA images; returns a float64 CUDA tensor of B values
+    (a 0-d tensor for one image)."""
+    import torch
+    one = U.dim() == 2
+    U3 = U.unsqueeze(0) if one else U
+    if U3.dim() != 3:
+        raise ValueError("U must be (ny, nx) or (B, ny, nx)")
+    B, ny, nx = (int(v) for v in U3.shape)
+    F = torch.empty(B, dtype=torch.float64, device=U.device)
+    st = _load().nedner_tenenbaum(_dev_ptr(U3, torch.float32, (B, ny, nx), "U"), B, ny, nx,
+                                  _dev_ptr(F, torch.float64, (B,), "F"), _stream_ptr(stream))
+    _check(st, "nedner_tenenbaum")
+    return F[0] if one else F
+
+
+def mip(vol, axis: int, stream=None):
+    """Maximum intensity projection of a (nz, ny, nx) float32 CUDA volume along
+    axis 0, 1 or 2 (nedner_mip)."""
+    import torch
+    nz, ny, nx = (int(v) for v in vol.shape)
+    shape = {0: (ny, nx), 1: (nz, nx), 2: (nz, ny)}[axis]
+    out = torch.empty(shape, dtype=torch.float32, device=vol.device)
+    st = _load().nedner_mip(_dev_ptr(vol, torch.float32, (nz, ny, nx), "vol"), nz, ny, nx, axis,
+                            _dev_ptr(out, torch.float32, shape, "out"), _stream_ptr(stream))
+    _check(st, "nedner_mip")
+    return out
 
 
 def work_split(nx: int, ny: int, nz: int, Nt: int, w: int = 12) -> dict:
@@ -410,5 +492,5 @@ def plan_from_config(cfg, **kw) -> Plan:
                 sensor_w=kw.pop("sensor_w", cfg.get("h")), **kw)
 
 
-__all__ = ["Plan", "plan_from_config", "work_split", "WORK_SPLIT_FIELDS", "ned_stage_static", "reconstruct", "model", "NednerError", "library", "LIB_PATH", "SIGNATURES",
+__all__ = ["Plan", "plan_from_config", "work_split", "tenenbaum", "mip", "WORK_SPLIT_FIELDS", "ned_stage_static", "reconstruct", "model", "NednerError", "library", "LIB_PATH", "SIGNATURES",
            "WINDOW_KB", "WINDOW_GAUSS"]

@@ -96,3 +96,28 @@ def test_profiled_transposed_calls_match_plain_calls(nd):
         check(d.cpu().numpy(), c.cpu().numpy(), 1e-6)
         assert all(v > 0 for k, v in ms.items() if k != "ned_xfft_adj") and ms["ned_xfft_adj"] >= 0, ms
         plan.close()
+
+
+def test_plan_info_reports_passes_and_launches(nd):
+    """nedner_plan_info: the split stage's chunks and the gathers' passes
+    divide the record, and the launch counts follow from them."""
+    case = inputs.small_case(32, 32, 32, 400, 256, seed=45, layout="disc")
+    for limit in (0, 6 << 20):
+        plan = nd.plan_from_config(case, max_workspace_bytes=limit)
+        i = plan.info()
+        Nt = case["Nt"]
+        assert set(i) == set(plan.PLAN_INFO_FIELDS)
+        assert i["split"] == 1 and Nt % i["tq"] == 0 and Nt % i["tp_adj"] == 0
+        assert i["launches_forward"] == 3 * (Nt // i["tq"]) + 3
+        if i["gsplit"]:
+            assert i["tp_g"] >= 64 and Nt % i["tp_g"] == 0
+            assert i["launches_adjoint"] == 4 + 3 * (Nt // i["tp_adj"])
+            assert i["launches_grad_positions"] == 4 + 2 * (Nt // i["tp_g"]) + 1
+        else:
+            assert i["launches_adjoint"] == 4 + 2 * (Nt // i["tp_adj"])
+            assert i["launches_grad_positions"] == 6
+        if limit == 0:
+            assert i["tq"] == Nt and i["gsplit"] == 1
+        else:
+            assert i["tq"] < Nt                              # the forward streams under the limit
+        plan.close()
