@@ -81,7 +81,27 @@ typedef struct {
                                      over the time samples where that lets the plan fit. */
     const double* sensor_w;       /* host [M] detector areas h_m (m^2), or NULL for X Y / M */
     int precision;                /* NEDNER_PRECISION_* (default FP32 NUFFT), see below */
+    int ner_interp;               /* NEDNER_NER_* (default the NER-NUFFT), see below */
 } nedner_opts;
+
+/*
+ * ner_interp selects how nedner_forward evaluates the non-equispaced range
+ * sums F[j, l] = sum_n Ghat[j, n] exp(-2 pi i nu_l n / Nt) (stage b):
+ *   NEDNER_NER_KB         the NER-NUFFT of Sec. 3.1 (centred, window
+ *                         deconvolution, w-tap window interpolation on the
+ *                         2 Nt grid);
+ *   NEDNER_NER_LINEAR_S2  the comparison method of Sec. 5.1: each line
+ *                         zero-padded at the end to 2 Nt, FFT'd, and the
+ *                         spectrum interpolated linearly at 2 nu (FFT, c = 2);
+ *   NEDNER_NER_LINEAR_S1  the same without padding (FFT, c = 1);
+ *   NEDNER_NER_DIRECT     the direct sum over n (the "direct FT" of Sec. 5.1,
+ *                         O(Nt) per value, FP32 with the phase re-anchored in
+ *                         FP64 every 16 terms).
+ * Plans with another value than NEDNER_NER_KB serve the comparison only: the
+ * transposed entry points (nedner_adjoint, nedner_grad_positions) answer
+ * NEDNER_EINVAL for them.
+ */
+enum { NEDNER_NER_KB = 0, NEDNER_NER_LINEAR_S2 = 1, NEDNER_NER_LINEAR_S1 = 2, NEDNER_NER_DIRECT = 3 };
 
 /*
  * precision selects the arithmetic of stage (a) in nedner_forward,
@@ -112,7 +132,7 @@ enum { NEDNER_PRECISION_FP32_NUFFT = 0, NEDNER_PRECISION_BF16_GEMM = 1, NEDNER_P
  *   out_grid   output grid (see nedner_grid).
  *   window     interpolation window of both NUFFTs (Sec. 3.1-3.2).
  *   sigma      oversampling factor (the paper's c > 1); this build supports 2.0.
- *   opts       NULL for defaults {1, 0, 0, NULL, NEDNER_PRECISION_FP32_NUFFT}.
+ *   opts       NULL for defaults {1, 0, 0, NULL, NEDNER_PRECISION_FP32_NUFFT, NEDNER_NER_KB}.
  *   stream     stream used for the table uploads (synchronised before return).
  *   out        receives the plan; untouched on error.
  * Returns NEDNER_OK, NEDNER_EINVAL, NEDNER_ERANGE, NEDNER_ENOMEM or NEDNER_ECUDA.

@@ -143,6 +143,7 @@ struct nedner_plan_s {
     int64_t M = 0;
     int Nt = 0;
     double dt = 0, c = 0, sigma = 2;
+    int ner_interp = NEDNER_NER_KB;   // nedner_opts.ner_interp
     nedner_grid grid{};
     std::vector<double> xy, h;
     std::vector<int> lp_kcut;     // host copy of t.lp_kcut

@@ -449,7 +449,12 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int 
 // it transforms and evaluates first in the same buffer.  The FFTs run in
 // place in padded buffers (see block_fft_ip), NT threads holding 16 values
 // each, so Lt * LPC and nz * LPC are at most 16 NT.
-template <int W, int D, int NT>
+// MODE (nedner_opts.ner_interp): NEDNER_NER_KB the NER-NUFFT above; the
+// comparison methods of Sec. 5.1: NEDNER_NER_LINEAR_S2 / _S1 the raw line
+// zero-padded at the end to 2 Nt / Nt, FFT'd and interpolated linearly
+// (ner_value_linear), NEDNER_NER_DIRECT the direct sum over the raw line
+// (ner_value_direct, no FFT).  Everything after the NER values is shared.
+template <int W, int D, int NT, int MODE = NEDNER_NER_KB>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, const __grid_constant__ TapPoly P, int LPC,
                                                                    const float2* __restrict__ Ghat,
                                                                    const float2* __restrict__ axy_tab,
@@ -457,11 +462,19 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, cons
                                                                    const float2* __restrict__ tw,
                                                                    float2* __restrict__ V) {
     constexpr int PER = 16;
+    constexpr int SIG = MODE == NEDNER_NER_LINEAR_S1 || MODE == NEDNER_NER_DIRECT ? 1 : 2;
     extern __shared__ float4 smem4[];
     const int nz1 = G.nz + 1;
+    const int Lt = SIG * G.Nt;
     float2* LA = reinterpret_cast<float2*>(smem4);                 // [Lt][LPC], padded
     float2* T = LA + padded_len(G.Lt * LPC);                       // [LPC + 1][nz + 1] values at l = -nz/2..nz/2
     float2* UA = T + (size_t)(LPC + 1) * nz1;                      // [nz][LPC], padded
+    // the NER value of column c of LA at l (e = l + nz/2)
+    auto value = [&](float2 axy, bool j0, int l, int lld, int c) {
+        if constexpr (MODE == NEDNER_NER_KB) return ner_value<W, D>(G, P, axy, j0, l, LA, lld, c);
+        else if constexpr (MODE == NEDNER_NER_DIRECT) return ner_value_direct(G, axy, j0, l, LA, lld, c);
+        else return ner_value_linear<SIG>(G, axy, j0, l, LA, lld, c);
+    };
 
     const int llpc = ilog2(LPC), lnz = ilog2(G.nz);
     const int cpk = G.ny >> llpc;                    // CTAs per kx
@@ -475,17 +488,22 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, cons
         // the line (kx, +ny/2): centred, deconvolved, zero-padded, in column 0
         const size_t lx = (size_t)kx * G.nyp + G.ny;
         const float2* src = Ghat + lx * G.Nt;
+        if constexpr (MODE == NEDNER_NER_KB) {
 #pragma unroll 4
-        for (int n = threadIdx.x; n < G.Nt; n += NT)
-            LA[padx((n - G.Nt / 2) & (G.Lt - 1))] = cscale(src[n], __ldg(&deconv_t[n]));
-        block_fft_ip<PER, true>(LA, G.Lt, 1, -1, tw);
+            for (int n = threadIdx.x; n < G.Nt; n += NT)
+                LA[padx((n - G.Nt / 2) & (G.Lt - 1))] = cscale(src[n], __ldg(&deconv_t[n]));
+            block_fft_ip<PER, true>(LA, G.Lt, 1, -1, tw);
+        } else {
+            for (int n = threadIdx.x; n < Lt; n += NT) LA[padx(n)] = n < G.Nt ? src[n] : make_float2(0.f, 0.f);
+            if constexpr (MODE == NEDNER_NER_DIRECT) __syncthreads();
+            else block_fft_ip<PER>(LA, Lt, 1, -1, tw);
+        }
         const float2 axy = __ldg(&axy_tab[lx]);
-        for (int e = threadIdx.x; e < nz1; e += NT)
-            T[LPC * nz1 + e] = ner_value<W, D>(G, P, axy, false, e - half_nz, LA, 0, 0);
+        for (int e = threadIdx.x; e < nz1; e += NT) T[LPC * nz1 + e] = value(axy, false, e - half_nz, 0, 0);
         __syncthreads();
     }
     // the LPC lines (theta = 2 pi n/N - pi of Sec. 3.1): centred, deconvolved, zero-padded
-    {
+    if constexpr (MODE == NEDNER_NER_KB) {
         const float2* src = Ghat + line0 * G.Nt;
 #pragma unroll 4
         for (int i = threadIdx.x; i < (G.Nt << llpc); i += NT) {
@@ -493,9 +511,17 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, cons
             const int p = (n - G.Nt / 2) & (G.Lt - 1);
             LA[padx((p << llpc) + c)] = cscale(src[(size_t)c * G.Nt + n], __ldg(&deconv_t[n]));
         }
+        // Lt = 2 Nt: the centred samples fill p < Nt/2 and p >= 3Nt/2 only
+        block_fft_ip<PER, true>(LA, G.Lt, LPC, -1, tw);
+    } else {
+        const float2* src = Ghat + line0 * G.Nt;
+        for (int i = threadIdx.x; i < (Lt << llpc); i += NT) {
+            const int n = i >> llpc, c = i & (LPC - 1);
+            LA[padx(i)] = n < G.Nt ? src[(size_t)c * G.Nt + n] : make_float2(0.f, 0.f);
+        }
+        if constexpr (MODE == NEDNER_NER_DIRECT) __syncthreads();
+        else block_fft_ip<PER>(LA, Lt, LPC, -1, tw);
     }
-    // Lt = 2 Nt: the centred samples fill p < Nt/2 and p >= 3Nt/2 only
-    block_fft_ip<PER, true>(LA, G.Lt, LPC, -1, tw);
 
     // NER values of the LPC lines at l = -nz/2..nz/2
     for (int i = threadIdx.x; i < (G.nz << llpc) + LPC; i += NT) {
@@ -503,7 +529,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, cons
         if (i < (G.nz << llpc)) { c = i >> lnz; e = i & (G.nz - 1); }
         else { c = i - (G.nz << llpc); e = G.nz; }
         const float2 axy = __ldg(&axy_tab[line0 + c]);
-        T[c * nz1 + e] = ner_value<W, D>(G, P, axy, kx == 0 && k0 + c == 0, e - half_nz, LA, llpc, c);
+        T[c * nz1 + e] = value(axy, kx == 0 && k0 + c == 0, e - half_nz, llpc, c);
     }
     __syncthreads();
 
@@ -651,6 +677,11 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     NEDNER_ATTR_NER(4, 10) NEDNER_ATTR_NER(6, 10) NEDNER_ATTR_NER(8, 10) NEDNER_ATTR_NER(10, 10)
     NEDNER_ATTR_NER(12, 10) NEDNER_ATTR_NER(14, 12) NEDNER_ATTR_NER(16, 12)
 #undef NEDNER_ATTR_NER
+#define NEDNER_ATTR_NER_M(MODE)                                                                                   \
+    if ((e = cudaFuncSetAttribute(k_ner_lines<4, 10, 256, MODE>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e; \
+    if ((e = cudaFuncSetAttribute(k_ner_lines<4, 10, 512, MODE>, (cudaFuncAttribute)a, (int)p.ch.smem3))) return e;
+    NEDNER_ATTR_NER_M(NEDNER_NER_LINEAR_S2) NEDNER_ATTR_NER_M(NEDNER_NER_LINEAR_S1) NEDNER_ATTR_NER_M(NEDNER_NER_DIRECT)
+#undef NEDNER_ATTR_NER_M
     if ((e = cudaFuncSetAttribute(k_img_yifft<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem4)))
         return e;
     if ((e = cudaFuncSetAttribute(k_img_xc2r<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem5)))
@@ -759,15 +790,31 @@ cudaError_t launch_ner_lines(const nedner_plan_s& p, const float2* Ghat, float2*
     else                                                                                                      \
         k_ner_lines<W, D, 512><<<grid, 512, p.ch.smem3, s>>>(G, p.tap, p.ch.lpc, Ghat, p.t.axy, p.t.deconv_t, \
                                                              p.t.tw, V)
-    switch (G.w) {
-        case 4: NEDNER_NER(4, 10); break;
-        case 6: NEDNER_NER(6, 10); break;
-        case 8: NEDNER_NER(8, 10); break;
-        case 10: NEDNER_NER(10, 10); break;
-        case 12: NEDNER_NER(12, 10); break;
-        case 14: NEDNER_NER(14, 12); break;
-        default: NEDNER_NER(16, 12); break;
+#define NEDNER_NER_M(MODE)                                                                                    \
+    if (p.ch.threads3 <= 256)                                                                                 \
+        k_ner_lines<4, 10, 256, MODE><<<grid, 256, p.ch.smem3, s>>>(G, p.tap, p.ch.lpc, Ghat, p.t.axy,         \
+                                                                    p.t.deconv_t, p.t.tw, V);                 \
+    else                                                                                                      \
+        k_ner_lines<4, 10, 512, MODE><<<grid, 512, p.ch.smem3, s>>>(G, p.tap, p.ch.lpc, Ghat, p.t.axy,         \
+                                                                    p.t.deconv_t, p.t.tw, V)
+    if (p.ner_interp == NEDNER_NER_LINEAR_S2) {
+        NEDNER_NER_M(NEDNER_NER_LINEAR_S2);
+    } else if (p.ner_interp == NEDNER_NER_LINEAR_S1) {
+        NEDNER_NER_M(NEDNER_NER_LINEAR_S1);
+    } else if (p.ner_interp == NEDNER_NER_DIRECT) {
+        NEDNER_NER_M(NEDNER_NER_DIRECT);
+    } else {
+        switch (G.w) {
+            case 4: NEDNER_NER(4, 10); break;
+            case 6: NEDNER_NER(6, 10); break;
+            case 8: NEDNER_NER(8, 10); break;
+            case 10: NEDNER_NER(10, 10); break;
+            case 12: NEDNER_NER(12, 10); break;
+            case 14: NEDNER_NER(14, 12); break;
+            default: NEDNER_NER(16, 12); break;
+        }
     }
+#undef NEDNER_NER_M
 #undef NEDNER_NER
     return cudaGetLastError();
 }

@@ -668,8 +668,9 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     if (sigma != 2.0) return NEDNER_EINVAL;
     if (window.kind != NEDNER_WINDOW_KB && window.kind != NEDNER_WINDOW_GAUSS) return NEDNER_EINVAL;
     if (window.width < 4 || window.width > 16 || (window.width & 1)) return NEDNER_EINVAL;
-    nedner_opts o = {1, 0, 0, nullptr, NEDNER_PRECISION_FP32_NUFFT};
+    nedner_opts o = {1, 0, 0, nullptr, NEDNER_PRECISION_FP32_NUFFT, NEDNER_NER_KB};
     if (opts) o = *opts;
+    if (o.ner_interp < NEDNER_NER_KB || o.ner_interp > NEDNER_NER_DIRECT) return NEDNER_EINVAL;
     if (o.precision != NEDNER_PRECISION_FP32_NUFFT && o.precision != NEDNER_PRECISION_BF16_GEMM &&
         o.precision != NEDNER_PRECISION_FP16_GEMM)
         return NEDNER_EINVAL;
@@ -681,6 +682,7 @@ nedner_status nedner_plan(const double* sensor_xy, int64_t M, int Nt, double dt,
     p->dt = dt;
     p->c = c;
     p->sigma = sigma;
+    p->ner_interp = o.ner_interp;
     p->grid = *og;
     p->win = make_window(window.kind, window.width, sigma);
     p->xy.assign(sensor_xy, sensor_xy + 2 * M);
@@ -847,6 +849,7 @@ static cudaError_t transposed_to_R(nedner_plan_t p, const float* p0, cudaStream_
 
 nedner_status nedner_adjoint(nedner_plan_t p, const float* p0, float* g, void* stream) {
     if (!p || !p0 || (p->M > 0 && !g)) return NEDNER_EINVAL;
+    if (p->ner_interp != NEDNER_NER_KB) return NEDNER_EINVAL;
     if (((uintptr_t)p0 & 7) != 0) return NEDNER_EINVAL;
     if (p->M == 0) return NEDNER_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -878,6 +881,7 @@ static cudaError_t transposed_to_R_timed(nedner_plan_t p, const float* p0, cudaS
 
 nedner_status nedner_adjoint_profiled(nedner_plan_t p, const float* p0, float* g, void* stream, float* stage_ms) {
     if (!p || !p0 || !stage_ms || (p->M > 0 && !g)) return NEDNER_EINVAL;
+    if (p->ner_interp != NEDNER_NER_KB) return NEDNER_EINVAL;
     if (((uintptr_t)p0 & 7) != 0) return NEDNER_EINVAL;
     for (int k = 0; k < NEDNER_TRANSPOSED_KERNELS; ++k) stage_ms[k] = 0.f;
     if (p->M == 0) return NEDNER_OK;
@@ -894,6 +898,7 @@ nedner_status nedner_adjoint_profiled(nedner_plan_t p, const float* p0, float* g
 nedner_status nedner_grad_positions_profiled(nedner_plan_t p, const float* g, const float* dL_dp0, float* dL_dxy,
                                              void* stream, float* stage_ms) {
     if (!p || !dL_dp0 || !stage_ms || (p->M > 0 && (!g || !dL_dxy))) return NEDNER_EINVAL;
+    if (p->ner_interp != NEDNER_NER_KB) return NEDNER_EINVAL;
     if (((uintptr_t)dL_dp0 & 7) != 0) return NEDNER_EINVAL;
     for (int k = 0; k < NEDNER_TRANSPOSED_KERNELS; ++k) stage_ms[k] = 0.f;
     if (p->M == 0) return NEDNER_OK;
@@ -910,6 +915,7 @@ nedner_status nedner_grad_positions_profiled(nedner_plan_t p, const float* g, co
 nedner_status nedner_grad_positions(nedner_plan_t p, const float* g, const float* dL_dp0, float* dL_dxy,
                                     void* stream) {
     if (!p || !dL_dp0 || (p->M > 0 && (!g || !dL_dxy))) return NEDNER_EINVAL;
+    if (p->ner_interp != NEDNER_NER_KB) return NEDNER_EINVAL;
     if (((uintptr_t)dL_dp0 & 7) != 0) return NEDNER_EINVAL;
     if (p->M == 0) return NEDNER_OK;
     cudaStream_t s = (cudaStream_t)stream;

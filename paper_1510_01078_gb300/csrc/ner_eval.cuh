@@ -71,12 +71,10 @@ __device__ __forceinline__ float2 ner_gather(const TapPoly& P, const float2* Bf,
     return acc;
 }
 
-// coefficient(l) * F(nu_l) for one line whose oversampled spectrum is column
-// `col` of the padded buffer Bf with 2^lld columns; j0: the line is j = 0
-template <int W, int D>
-__device__ __forceinline__ float2 ner_value(const Geo& G, const TapPoly& P, float2 axy, bool j0, int l,
-                                            const float2* Bf, int lld, int col) {
-    FF nu = nu_abs(G, axy, l);
+// nu_l (signed, float-float) and its coefficient: the Jacobian W (2 at j = l = 0,
+// 0 at l = 0 otherwise) times the scale, zero outside the band under band_mask
+__device__ __forceinline__ float ner_coef(const Geo& G, float2 axy, bool j0, int l, FF& nu) {
+    nu = nu_abs(G, axy, l);
     float Wj;
     if (l == 0) {
         Wj = j0 ? 2.f : 0.f;
@@ -90,6 +88,68 @@ __device__ __forceinline__ float2 ner_value(const Geo& G, const TapPoly& P, floa
         const double nd = (double)nu.hi + (double)nu.lo;
         if (!(nd >= -0.5 * G.Nt - 1e-9 && nd < 0.5 * G.Nt - 1e-9)) cl = 0.f;
     }
+    return cl;
+}
+
+// The comparison method of Sec. 5.1 (FFT with linear interpolation): the
+// line's spectrum B, zero-padded at the end to Lt = SIG Nt (SIG = 1: none), is
+// interpolated linearly between the grid points around v = SIG nu; no window,
+// no deconvolution, no centring.  Column `col` of the padded buffer Bf with
+// 2^lld columns.
+template <int SIG>
+__device__ __forceinline__ float2 ner_value_linear(const Geo& G, float2 axy, bool j0, int l, const float2* Bf,
+                                                   int lld, int col) {
+    FF nu;
+    const float cl = ner_coef(G, axy, j0, l, nu);
+    if (cl == 0.f) return make_float2(0.f, 0.f);
+    const int Lt = SIG * G.Nt;
+    const float vh = SIG * nu.hi, vl = SIG * nu.lo;
+    float fl = floorf(vh);
+    float t = (vh - fl) + vl;
+    if (t < 0.f) { t += 1.f; fl -= 1.f; }
+    if (t >= 1.f) { t -= 1.f; fl += 1.f; }
+    const int i0 = (int)fl;
+    const float2 b0 = Bf[padx(((i0 & (Lt - 1)) << lld) + col)];
+    const float2 b1 = Bf[padx((((i0 + 1) & (Lt - 1)) << lld) + col)];
+    return cscale(__ffma2_rn(make_float2(t, t), b1, cscale(b0, 1.f - t)), cl);
+}
+
+// The direct sum of the NER (the "direct FT" ground truth of Sec. 5.1):
+// sum_{n < Nt} Ghat[n] exp(-2 pi i nu n / Nt) over the raw line (column `col`
+// of Bf, sample n in row n).  The phase is re-anchored every 16 terms from
+// nu n / Nt reduced modulo 1 in FP64 and advanced by one complex rotation in
+// between.
+__device__ __forceinline__ float2 ner_value_direct(const Geo& G, float2 axy, bool j0, int l, const float2* Bf,
+                                                   int lld, int col) {
+    FF nu;
+    const float cl = ner_coef(G, axy, j0, l, nu);
+    if (cl == 0.f) return make_float2(0.f, 0.f);
+    const double a = ((double)nu.hi + (double)nu.lo) / G.Nt;      // turns per sample
+    float ss, cs;
+    const double fa = a - floor(a);
+    sincospif(-2.f * (float)fa, &ss, &cs);
+    const float2 step = make_float2(cs, ss);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int n0 = 0; n0 < G.Nt; n0 += 16) {
+        const double f = a * n0 - floor(a * n0);
+        sincospif(-2.f * (float)f, &ss, &cs);
+        float2 w = make_float2(cs, ss);
+        const int n1 = n0 + 16 < G.Nt ? n0 + 16 : G.Nt;
+        for (int n = n0; n < n1; ++n) {
+            acc = cadd(acc, cmul(w, Bf[padx((n << lld) + col)]));
+            w = cmul(w, step);
+        }
+    }
+    return cscale(acc, cl);
+}
+
+// coefficient(l) * F(nu_l) for one line whose oversampled spectrum is column
+// `col` of the padded buffer Bf with 2^lld columns; j0: the line is j = 0
+template <int W, int D>
+__device__ __forceinline__ float2 ner_value(const Geo& G, const TapPoly& P, float2 axy, bool j0, int l,
+                                            const float2* Bf, int lld, int col) {
+    FF nu;
+    const float cl = ner_coef(G, axy, j0, l, nu);
     if (cl == 0.f) return make_float2(0.f, 0.f);
     // v = sigma nu (sigma = 2): exact scaling of the pair
     const float vh = 2.f * nu.hi, vl = 2.f * nu.lo;

@@ -41,12 +41,14 @@ class _Window(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("apply_weights", ctypes.c_int), ("band_mask", ctypes.c_int),
                 ("max_workspace_bytes", ctypes.c_size_t), ("sensor_w", ctypes.c_void_p),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("ner_interp", ctypes.c_int)]
 
 
 PRECISION_FP32_NUFFT, PRECISION_BF16_GEMM, PRECISION_FP16_GEMM = 0, 1, 2
 # ned_mode names of the binding -> precision values of nedner_opts
 NED_MODES = {"nufft": PRECISION_FP32_NUFFT, "tensor_bf16": PRECISION_BF16_GEMM, "tensor_fp16": PRECISION_FP16_GEMM}
+# ner_interp names -> nedner_opts.ner_interp (the NER-NUFFT and the comparison methods of Sec. 5.1)
+NER_MODES = {"nufft": 0, "linear2": 1, "linear1": 2, "direct": 3}
 
 
 # symbol -> (restype, argtypes); mirrors include/nedner.h
@@ -140,7 +142,7 @@ class Plan:
 
     def __init__(self, sensor_xy, Nt: int, dt: float, c: float, grid, window=("kb", 12), sigma: float = 2.0,
                  apply_weights: bool = True, band_mask: bool = False, sensor_w=None,
-                 max_workspace_bytes: int = 0, stream=None, ned_mode: str = "nufft"):
+                 max_workspace_bytes: int = 0, stream=None, ned_mode: str = "nufft", ner_mode: str = "nufft"):
         lib = _load()
         self._xy = np.ascontiguousarray(np.asarray(sensor_xy, dtype=np.float64).reshape(-1, 2))
         self.M = int(self._xy.shape[0])
@@ -153,7 +155,7 @@ class Plan:
         self._h = None if sensor_w is None else np.ascontiguousarray(np.asarray(sensor_w, dtype=np.float64))
         mode = NED_MODES[ned_mode]
         opts = _Opts(int(bool(apply_weights)), int(bool(band_mask)), int(max_workspace_bytes),
-                     None if self._h is None else self._h.ctypes.data, mode)
+                     None if self._h is None else self._h.ctypes.data, mode, NER_MODES[ner_mode])
         handle = ctypes.c_void_p()
         st = lib.nedner_plan(self._xy.ctypes.data if self.M else None, self.M, self.Nt, float(dt), float(c),
                              ctypes.byref(g), w, float(sigma), ctypes.byref(opts), _stream_ptr(stream),

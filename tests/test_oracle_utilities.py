@@ -81,3 +81,28 @@ def test_mip_finds_a_planted_maximum():
         assert m[pos] == 5.0 and (m <= 5.0).all()
         assert m.shape == tuple(s for i, s in enumerate(v.shape) if i != axis)
         assert np.all(m >= np.take(v, 0, axis=axis))
+
+
+def test_linear_interpolation_oracle_against_direct_sums():
+    """The FFT-with-linear-interpolation oracle (Table 1's comparison method)
+    at grid frequencies nu = mu / sigma equals the direct NER sum there, and
+    in between it is the straight line between the direct sums at the two
+    neighbouring grid frequencies (direct sums from the C core)."""
+    import oracle
+    from oracle import comparison as C
+    pr = oracle.Problem(sensor_xy=np.zeros((1, 2)), Nt=64, dt=20e-9, c=1500.0, nx=8, ny=8, nz=16,
+                        dx=1e-4, dy=1e-4, dz=1500.0 * 64 * 20e-9 / 16)
+    rng = np.random.default_rng(9)
+    G = rng.standard_normal((3, 64)) + 1j * rng.standard_normal((3, 64))
+    for sigma in (1, 2):
+        grid = np.array([[-7.0, 0.0, 3.0, 31.5 if sigma == 2 else 31.0]] * 3) / 1.0
+        grid = np.round(grid * sigma) / sigma
+        assert np.allclose(C.ner_linear(pr, G, grid, sigma), oracle.ner(pr, G, grid), atol=1e-10)
+        nus = rng.uniform(-40, 40, size=(3, 5))
+        got = C.ner_linear(pr, G, nus, sigma)
+        v = sigma * nus
+        lo, t = np.floor(v) / sigma, v - np.floor(v)
+        want = (1 - t) * oracle.ner(pr, G, lo) + t * oracle.ner(pr, G, lo + 1.0 / sigma)
+        assert np.allclose(got, want, atol=1e-10)
+        # and it is not the direct sum off the grid
+        assert np.abs(got - oracle.ner(pr, G, nus)).max() > 1e-3
