@@ -348,6 +348,33 @@ nedner_status nedner_tenenbaum(const float* U, int64_t B, int ny, int nx, double
 nedner_status nedner_mip(const float* vol, int nz, int ny, int nx, int axis, float* out, void* stream);
 
 /*
+ * The two-dimensional variant (Sec. 7): sensors at x_m on the line z = 0,
+ * an output image of nz x nx pixels (x fastest), the reconstruction
+ *   p2[qz][qx] = Re (1/(nx nz)) sum_{jx, l} F[jx, l] exp(2 pi i (jx (qx - nx/2)/nx + l qz/nz)),
+ *   F = W s sum_n G[jx, n] exp(-2 pi i nu n / Nt),  nu = sign(l) c Nt dt sqrt((jx/X)^2 + (l/Z)^2),
+ *   G[jx, n] = sum_m (h_m / dx) g[m, n] exp(-2 pi i jx x_m / X),
+ * i.e. Eq. disc_rec with one lateral axis (W, s and the readings as in the
+ * 3-D plan).  The plan evaluates it on the 3-D path with every sensor at
+ * y = 0 on a grid of 8 rows of dy = dx and sums the 3-D image over its rows
+ * (exact: only the jy = 0 lines survive that sum); the adjoint copies the
+ * image to every row and runs the 3-D adjoint.
+ *   sensor_x   host [M] metres, strictly inside (-X/2, X/2), X = nx dx.
+ *   opts       as for nedner_plan; sensor_w are lengths h_m (m), default X/M;
+ *              precision must be NEDNER_PRECISION_FP32_NUFFT.
+ *   g          device [M][Nt] f32 (16-byte aligned); p2 device [nz][nx] f32.
+ * The plan owns a 3-D image buffer (nz x 8 x nx floats): calls on one plan
+ * must not overlap.  Errors as for the 3-D entry points.
+ */
+typedef struct nedner2d_plan_s* nedner2d_plan_t;
+nedner_status nedner2d_plan(const double* sensor_x, int64_t M, int Nt, double dt, double c, int nx, int nz,
+                            double dx, double dz, nedner_window window, double sigma, const nedner_opts* opts,
+                            void* stream, nedner2d_plan_t* out);
+nedner_status nedner2d_set_positions(nedner2d_plan_t plan, const double* sensor_x);
+nedner_status nedner2d_forward(nedner2d_plan_t plan, const float* g, float* p2, void* stream);
+nedner_status nedner2d_adjoint(nedner2d_plan_t plan, const float* p2, float* g, void* stream);
+nedner_status nedner2d_destroy(nedner2d_plan_t plan);
+
+/*
  * The plan's passes over time, as chosen at nedner_plan for its geometry,
  * sensor count and workspace limit (host only, no device work).  Writes up
  * to nout values to out (host), in this order:

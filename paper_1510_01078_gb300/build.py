@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnedner.so")
-SOURCES = ["nedner_api.cu", "kernels_fwd.cu", "kernels_adj.cu", "kernels_tp.cu", "kernels_util.cu", "static_scratch.cu",
-           "window.cpp"]
+SOURCES = ["nedner_api.cu", "kernels_fwd.cu", "kernels_adj.cu", "kernels_tp.cu", "kernels_util.cu", "nedner2d.cu",
+           "static_scratch.cu", "window.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -72,6 +72,13 @@ SIGNATURES = {
     "nedner_lowpass_bins": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "nedner_tenenbaum": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P]),
     "nedner_mip": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "nedner2d_plan": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_double, ctypes.c_double, _Window, ctypes.c_double, _P, _P,
+                                     _P]),
+    "nedner2d_set_positions": (ctypes.c_int, [_P, _P]),
+    "nedner2d_forward": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nedner2d_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nedner2d_destroy": (ctypes.c_int, [_P]),
     "nedner_work_split": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "nedner_forward_host": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -448,6 +455,66 @@ WORK_SPLIT_FIELDS = ("c1", "c2f", "c4", "c5", "groups1", "threads1", "per1", "tp
                      "smem_grad", "split1", "tq", "wpc_s", "nbx", "thx", "perx", "smem_s", "smem_x", "smem3a")
 
 
+class Plan2D:
+    """The two-dimensional variant (``nedner2d_plan``, Sec. 7): sensors at x_m
+    on a line, an output image (nz, nx).  sensor_x: (M,) metres; grid: (nx, nz,
+    dx, dz); sensor_w: lengths h_m (default X/M)."""
+
+    def __init__(self, sensor_x, Nt: int, dt: float, c: float, grid, window=("kb", 12), sigma: float = 2.0,
+                 apply_weights: bool = True, sensor_w=None, stream=None):
+        lib = _load()
+        self._x = np.ascontiguousarray(np.asarray(sensor_x, dtype=np.float64).reshape(-1))
+        self.M = int(self._x.shape[0])
+        self.Nt = int(Nt)
+        self.nx, self.nz = int(grid[0]), int(grid[1])
+        self.grid = tuple(grid)
+        kind = {"kb": WINDOW_KB, "gauss": WINDOW_GAUSS}[window[0]] if isinstance(window[0], str) else int(window[0])
+        self._h = None if sensor_w is None else np.ascontiguousarray(np.asarray(sensor_w, dtype=np.float64))
+        opts = _Opts(int(bool(apply_weights)), 0, 0, None if self._h is None else self._h.ctypes.data,
+                     PRECISION_FP32_NUFFT, 0)
+        handle = ctypes.c_void_p()
+        st = lib.nedner2d_plan(self._x.ctypes.data if self.M else None, self.M, self.Nt, float(dt), float(c),
+                               self.nx, self.nz, float(grid[2]), float(grid[3]), _Window(kind, int(window[1])),
+                               float(sigma), ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(handle))
+        _check(st, "nedner2d_plan")
+        self._handle = handle
+
+    def close(self):
+        if getattr(self, "_handle", None) is not None and self._handle.value:
+            _load().nedner2d_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_positions(self, sensor_x):
+        x = np.ascontiguousarray(np.asarray(sensor_x, dtype=np.float64).reshape(self.M))
+        _check(_load().nedner2d_set_positions(self._handle, x.ctypes.data if self.M else None),
+               "nedner2d_set_positions")
+        self._x = x
+
+    def forward(self, g, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.nz, self.nx), dtype=torch.float32, device=g.device)
+        st = _load().nedner2d_forward(self._handle, _dev_ptr(g, torch.float32, (self.M, self.Nt), "g"),
+                                      _dev_ptr(out, torch.float32, (self.nz, self.nx), "p2"), _stream_ptr(stream))
+        _check(st, "nedner2d_forward")
+        return out
+
+    def adjoint(self, p2, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.M, self.Nt), dtype=torch.float32, device=p2.device)
+        st = _load().nedner2d_adjoint(self._handle, _dev_ptr(p2, torch.float32, (self.nz, self.nx), "p2"),
+                                      _dev_ptr(out, torch.float32, (self.M, self.Nt), "g"), _stream_ptr(stream))
+        _check(st, "nedner2d_adjoint")
+        return out
+
+
 def tenenbaum(U, stream=None):
     """Tenenbaum sharpness (Appendix B) of an image (ny, nx) or a batch (B, ny,
     nx) of float32 CUDA images; returns a float64 CUDA tensor of B values
@@ -494,5 +561,5 @@ def plan_from_config(cfg, **kw) -> Plan:
                 sensor_w=kw.pop("sensor_w", cfg.get("h")), **kw)
 
 
-__all__ = ["Plan", "plan_from_config", "work_split", "tenenbaum", "mip", "WORK_SPLIT_FIELDS", "ned_stage_static", "reconstruct", "model", "NednerError", "library", "LIB_PATH", "SIGNATURES",
+__all__ = ["Plan", "Plan2D", "plan_from_config", "work_split", "tenenbaum", "mip", "WORK_SPLIT_FIELDS", "ned_stage_static", "reconstruct", "model", "NednerError", "library", "LIB_PATH", "SIGNATURES",
            "WINDOW_KB", "WINDOW_GAUSS"]

@@ -113,6 +113,21 @@ def equi_steradian(N: int, D: float, r0: float, return_slices: bool = False):
     return xy, h
 
 
+def equi_angular(N: int, D: float, r0: float):
+    """Equi-angular layout on a line (Sec. 6.1, the 2-D variant): N sensors
+    whose lines to the point of interest (0, r0) enclose equal angles, the
+    angle of the detection region 2 atan(D / (2 r0)) split into N equal parts
+    with a sensor at each part's middle angle, x_i = r0 tan(theta_i); h_i
+    proportional to r_i^2 (Sec. 6.2, 2-D), normalised to D."""
+    if N < 1 or not (D > 0 and r0 > 0):
+        raise ValueError("need N >= 1, D > 0, r0 > 0")
+    tmax = math.atan(0.5 * D / r0)
+    theta = -tmax + (np.arange(N) + 0.5) * (2.0 * tmax / N)
+    x = r0 * np.tan(theta)
+    h = x * x + r0 * r0
+    return x, h / h.sum() * D
+
+
 def regular_grid(M: int, D: float):
     """The regular comparison layout with about M sensors: an n x n grid of
     cell centres over the square of side D (n = round(sqrt M)), h = (D/n)^2."""
@@ -261,7 +276,7 @@ def compare_layouts(N: int = 1024, D: float = 18e-3, r0: float = 5e-3, grid=(128
     return out
 
 
-__all__ = ["equi_steradian", "regular_grid", "corrcoef", "upper_half_mask", "optimise_placement", "layout_rho",
+__all__ = ["equi_steradian", "equi_angular", "regular_grid", "corrcoef", "upper_half_mask", "optimise_placement", "layout_rho",
            "compare_layouts"]
 
 

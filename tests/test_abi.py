@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared_symbols():
     text = open(os.path.join(ROOT, "include", "nedner.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(nedner_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(nedner(?:2d)?_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")

@@ -127,3 +127,23 @@ def test_bad_arguments():
         P.equi_steradian(0, D, R0)
     with pytest.raises(ValueError):
         P.equi_steradian(10, -1.0, R0)
+
+
+def test_equi_angular_layout():
+    """Equal angles between neighbouring sensor lines seen from (0, r0), all
+    inside the detection region, and h proportional to r^2 stands for the
+    sensor's share of the line (the local spacing grows like r^2 / r0)."""
+    N, D, r0 = 32, 40e-3, 6e-3
+    x, h = P.equi_angular(N, D, r0)
+    th = np.arctan(x / r0)
+    assert np.allclose(np.diff(th), 2 * math.atan(0.5 * D / r0) / N, rtol=1e-12)
+    assert np.abs(x).max() < 0.5 * D and np.allclose(x, -x[::-1], atol=1e-15)
+    assert h.sum() == pytest.approx(D, rel=1e-12)
+    spacing = 0.5 * (x[2:] - x[:-2])
+    ratio = h[1:-1] / spacing
+    assert np.allclose(ratio, np.median(ratio), rtol=0.04)
+    # the discretisation error of that statement falls with N
+    x2, h2 = P.equi_angular(4 * N, D, r0)
+    r2 = h2[1:-1] / (0.5 * (x2[2:] - x2[:-2]))
+    assert np.abs(r2 / np.median(r2) - 1).max() < 0.25 * np.abs(ratio / np.median(ratio) - 1).max()
+    assert h.max() / h.min() == pytest.approx((x.max() ** 2 + r0 ** 2) / (x[N // 2] ** 2 + r0 ** 2), rel=1e-12)
