@@ -95,5 +95,5 @@ def test_known_splits(nd):
     assert (c2["tpl1"], c2["c1"], c2["threads1"], c2["lpc"], c2["tpl_adj"]) == (2, 64, 256, 4, 2)
     c3 = nd.work_split(256, 256, 512, 2048, 12)
     assert (c3["tpl1"], c3["threads1"], c3["lpc"], c3["threads_adj"], c3["c4"], c3["c5"]) == (2, 512, 1, 512, 8, 16)
-    assert (c3["split1"], c3["tq"], c3["nbx"], c3["thx"], c3["perx"]) == (1, 2048, 16, 256, 32)
+    assert (c3["split1"], c3["tq"], c3["nbx"], c3["thx"], c3["perx"]) == (1, 2048, 8, 256, 16)
     assert (c2["split1"], c2["nbx"], c2["thx"], c2["perx"]) == (1, 16, 256, 16)
