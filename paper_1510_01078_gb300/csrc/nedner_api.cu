@@ -83,9 +83,9 @@ void free_sensor_tables(DevTables& t) {
     cudaFree(t.xrow_ptr); cudaFree(t.xent_m); cudaFree(t.xent_wx); cudaFree(t.xent_bx); cudaFree(t.seg);
     cudaFree(t.xent_gx); cudaFree(t.xent_gy); cudaFree(t.xrow_first);
     cudaFree(t.xent_rc); cudaFree(t.sens_ent);
-    cudaFree(t.bseg); cudaFree(t.pent_bx); cudaFree(t.pent_w); cudaFree(t.pent_wd);
+    cudaFree(t.bseg); cudaFree(t.pent_bx); cudaFree(t.pent_w);
     cudaFree(t.pent_gx); cudaFree(t.pent_gy); cudaFree(t.gseg); cudaFree(t.lp_kcut);
-    t.bseg = nullptr; t.pent_bx = nullptr; t.pent_w = nullptr; t.pent_wd = nullptr;
+    t.bseg = nullptr; t.pent_bx = nullptr; t.pent_w = nullptr;
     t.pent_gx = nullptr; t.pent_gy = nullptr; t.gseg = nullptr; t.lp_kcut = nullptr;
     t.sens_bx = t.sens_by = nullptr;
     t.sens_wx = t.sens_wy = t.sens_dwx = t.sens_dwy = t.sens_fac = nullptr;
@@ -308,7 +308,7 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     const int PW = (w + 3) / 4 * 4;
     const int nblk = G.Lx / 16;
     std::vector<int> pent_bx;
-    std::vector<float> pent_w, pent_wd, pent_gx, pent_gy;
+    std::vector<float> pent_w, pent_gx, pent_gy;
     std::vector<int2> bseg(C.split1 ? (size_t)G.Ly * nblk : 0);
     std::vector<int2> gseg(C.split1 ? (size_t)G.Ly * nblk : 0);
     std::vector<XE> tmp;
@@ -332,8 +332,6 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
                 pent_bx.push_back(x.bx);
                 for (int k = 0; k < PW; ++k) {
                     pent_w.push_back(k < w ? x.w * wx[(size_t)x.m * w + k] : 0.f);
-                    pent_wd.push_back(pent_w.back());
-                    pent_wd.push_back(pent_w.back());
                     pent_gx.push_back(k < w ? x.w * dwx[(size_t)x.m * w + k] : 0.f);
                     pent_gy.push_back(k < w ? x.dw * wx[(size_t)x.m * w + k] : 0.f);
                 }
@@ -433,7 +431,6 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = upload(&p.t.bseg, bseg, s);
     if (!e) e = upload(&p.t.pent_bx, pent_bx, s);
     if (!e) e = upload(&p.t.pent_w, pent_w, s);
-    if (!e) e = upload(&p.t.pent_wd, pent_wd, s);
     if (!e) e = upload(&p.t.pent_gx, pent_gx, s);
     if (!e) e = upload(&p.t.pent_gy, pent_gy, s);
     if (!e) e = upload(&p.t.gseg, gseg, s);
@@ -516,9 +513,9 @@ void choose_chunks(nedner_plan_s& p) {
     c.wpc_s = 4;
     {
         // per warp, double-buffered batches of 8 entries: sensor indices, and
-        // first columns, duplicated taps and 64 samples of g
+        // first columns, taps and 64 samples of g
         const long pw = (G.w + 3) / 4 * 4;
-        c.smem_s = (size_t)c.wpc_s * (2 * 8 + 2 * (8 + 8 * 2 * pw + 8 * 64)) * 4;
+        c.smem_s = (size_t)c.wpc_s * (2 * 8 + 2 * (8 + 8 * pw + 8 * 64)) * 4;
     }
     c.nbx = (int)std::min<long>(16, std::max<long>(1, 4096 / G.Lx));
     c.perx = ((long)G.Lx * c.nbx >= 8192) ? 32 : 16;
