@@ -761,6 +761,30 @@ __device__ __forceinline__ float2 taps_dot(const float2 (&win)[32], const float*
     return __fadd2_rn(__fadd2_rn(a[0], a[1]), __fadd2_rn(a[2], a[3]));
 }
 
+// both derivative tap sets of one entry (ta, tb) at the same offset D: one
+// branch for the two dot products
+template <int W, int D>
+__device__ __forceinline__ void taps_dot2(const float2 (&win)[32], const float* ta, const float* tb, float2& va,
+                                          float2& vb) {
+    va = taps_dot<W, D>(win, ta);
+    vb = taps_dot<W, D>(win, tb);
+}
+
+template <int W>
+__device__ __forceinline__ void block_taps_dot2(const float2 (&win)[32], int d, const float* ta, const float* tb,
+                                                float2& va, float2& vb) {
+#define NEDNER_DOT2_CASE(I) \
+    case I: taps_dot2<W, I>(win, ta, tb, va, vb); break;
+    switch (d) {
+        NEDNER_DOT2_CASE(0) NEDNER_DOT2_CASE(1) NEDNER_DOT2_CASE(2) NEDNER_DOT2_CASE(3)
+        NEDNER_DOT2_CASE(4) NEDNER_DOT2_CASE(5) NEDNER_DOT2_CASE(6) NEDNER_DOT2_CASE(7)
+        NEDNER_DOT2_CASE(8) NEDNER_DOT2_CASE(9) NEDNER_DOT2_CASE(10) NEDNER_DOT2_CASE(11)
+        NEDNER_DOT2_CASE(12) NEDNER_DOT2_CASE(13) NEDNER_DOT2_CASE(14)
+        default: taps_dot2<W, 15>(win, ta, tb, va, vb); break;
+    }
+#undef NEDNER_DOT2_CASE
+}
+
 template <int W>
 __device__ __forceinline__ float2 block_taps_dot(const float2 (&win)[32], int d, const float* t) {
 #define NEDNER_DOT_CASE(I) \
@@ -860,8 +884,8 @@ __global__ void __launch_bounds__(128, 4) k_ned_gather_blocks(Geo G, int nb, int
                     const int j = j0 + u;
                     if (j < n) {
                         const int dd = d[j] - c0;
-                        const float2 va = block_taps_dot<W>(win, dd, tp + j * NTAP);
-                        const float2 vb = block_taps_dot<W>(win, dd, tp + j * NTAP + PW);
+                        float2 va, vb;
+                        block_taps_dot2<W>(win, dd, tp + j * NTAP, tp + j * NTAP + PW, va, vb);
                         sx = fmaf(gv[0].x, va.x, gv[0].y * va.y);
                         sy = fmaf(gv[0].x, vb.x, gv[0].y * vb.y);
                     }
