@@ -102,7 +102,9 @@ struct DevTables {
     // the block spread (split1): per (row, 16-column block) the range of
     // entries whose exact taps reach into the block, and per entry its exact
     // first column and its w taps
-    int2* bseg = nullptr;         // [Ly][Lx/16]
+    int2* bseg = nullptr;         // [Ly][Lx/16] range of the block's entries in bent_m / bent_w
+    int* bent_m = nullptr;        // [.] sensor of each (block, entry reaching into it)
+    float* bent_w = nullptr;      // [.][16] its taps aligned to the block's columns (block_taps16)
     int* pent_bx = nullptr;       // [E'] first x column (negative for the second copy of a wrapped entry)
     float* pent_w = nullptr;      // [E'][4 ceil(w/4)] x tap times y tap times sensor factor, from pent_bx on
     float* pent_gx = nullptr;     // [E'][4 ceil(w/4)] the same with the x-tap derivative (position gradient)

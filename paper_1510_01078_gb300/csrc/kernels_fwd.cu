@@ -242,25 +242,24 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
 // grid Q [tq/32][Ly][Lx][32] (real; groups of 32 time samples, time fastest).
 // One warp owns one block of 16 columns of one grid row for 64 time samples
 // (two per lane, packed FMAs) and adds every entry (sensor, y tap) of the row
-// whose W x taps reach into the block, from the entry's exact first column on
-// (block_entry); the row's entries are sorted by first column, so a block's
-// entries are one range bseg[row][block].  Entries are staged eight at a time
-// per warp (sensor indices one batch ahead, then first column, taps and
-// samples of g by asynchronous copies while the current batch is added).  The
-// warp then stores its 16 columns (128 contiguous bytes per column and 32
-// samples) and is done: no shared row buffer and no barrier, so warps of dense
-// and sparse blocks do not wait for one another, and many small CTAs keep
-// every SM busy.
+// whose x taps reach into the block.  The plan stores each such entry with
+// its taps aligned to the block's 16 columns (block_taps16), so an entry is
+// 16 packed FMAs with no branch on its offset (block_entry16); the block's
+// entries are one range bseg[row][block] of bent_m / bent_w.  Entries are
+// staged eight at a time per warp (sensor indices one batch ahead, then taps
+// and samples of g by asynchronous copies while the current batch is added).
+// The warp then stores its 16 columns (128 contiguous bytes per column and
+// 32 samples) and is done: no shared row buffer and no barrier, so warps of
+// dense and sparse blocks do not wait for one another, and many small CTAs
+// keep every SM busy.
 // ---------------------------------------------------------------------------
-template <int W>
 __global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int tq, const float* __restrict__ g,
                                                               const int2* __restrict__ bseg,
-                                                              const int* __restrict__ xent_m,
-                                                              const float* __restrict__ pent_w,
-                                                              const int* __restrict__ pent_bx, float* __restrict__ Q) {
+                                                              const int* __restrict__ bent_m,
+                                                              const float* __restrict__ bent_w,
+                                                              float* __restrict__ Q) {
     constexpr int B = 8, C = 64, NB = 32;
-    constexpr int WQ = (W + 3) / 4;                                 // float4 of taps per entry
-    constexpr int DB = B + B * 4 * WQ;                              // ints + floats before the g block
+    constexpr int DB = B * 16;                                      // taps before the g block (floats)
     constexpr int dsz = DB + B * C;                                 // one data buffer (4-byte words)
     extern __shared__ float4 smem4[];
     const int wpc = blockDim.x >> 5;
@@ -278,20 +277,19 @@ __global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int
     for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
 
     int* st_m = reinterpret_cast<int*>(smem4) + (size_t)q * (2 * B + 2 * dsz);   // [2][B]
-    int* st_d = st_m + 2 * B;                                                     // [2][dsz]
+    float* st_d = reinterpret_cast<float*>(st_m + 2 * B);                         // [2][dsz]
     const int nent = rg.y - rg.x;
     const int nbt = (nent + B - 1) / B;
     auto issue_m = [&](int b) {
         const int e0 = rg.x + b * B, nb_ = min(B, rg.y - e0);
-        if (ln < nb_) cp_async(st_m + (b & 1) * B + ln, xent_m + e0 + ln, 4);
+        if (ln < nb_) cp_async(st_m + (b & 1) * B + ln, bent_m + e0 + ln, 4);
     };
     auto issue_data = [&](int b) {
         const int e0 = rg.x + b * B, nb_ = min(B, rg.y - e0);
-        int* d = st_d + (b & 1) * dsz;
+        float* d = st_d + (b & 1) * dsz;
         const int* mm = st_m + (b & 1) * B;
-        if (ln < nb_) cp_async(d + ln, pent_bx + e0 + ln, 4);
-        const float* wsrc = pent_w + (size_t)e0 * 4 * WQ;
-        for (int i = ln; i < nb_ * WQ; i += 32) cp_async(d + B + 4 * i, wsrc + 4 * i, 16);
+        // 8 entries x 16 taps = 32 copies of 16 bytes: one per lane
+        if ((ln >> 2) < nb_) cp_async(d + 4 * ln, bent_w + (size_t)e0 * 16 + 4 * ln, 16);
 #pragma unroll
         for (int r = 0; r < B * (C / 4) / 32; ++r) {
             const int i = ln + 32 * r;
@@ -315,15 +313,12 @@ __global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int
         if (b + 2 < nbt) issue_m(b + 2);
         cp_async_commit();
         const int nbat = min(B, nent - b * B);
-        const int* st_bx = st_d + (b & 1) * dsz;
-        const float4* wst = reinterpret_cast<const float4*>(st_bx + B);
-        const float2* st_g = reinterpret_cast<const float2*>(st_bx + DB);
+        const float4* wst = reinterpret_cast<const float4*>(st_d + (b & 1) * dsz);
+        const float2* st_g = reinterpret_cast<const float2*>(st_d + (b & 1) * dsz + DB);
 #pragma unroll 1
         for (int j = 0; j < nbat; ++j) {
-            float4 wa[WQ];
-#pragma unroll
-            for (int k4 = 0; k4 < WQ; ++k4) wa[k4] = wst[j * WQ + k4];
-            block_entry<W>(acc, st_bx[j], c0, wa, st_g[j * NB + ln]);
+            const float4 t[4] = {wst[4 * j], wst[4 * j + 1], wst[4 * j + 2], wst[4 * j + 3]};
+            block_entry16(acc, t, st_g[j * NB + ln]);
         }
         __syncwarp();
     }
@@ -662,11 +657,7 @@ cudaError_t configure_fwd_kernels(const nedner_plan_s& p) {
     NEDNER_ATTR_SPREAD2(8) NEDNER_ATTR_SPREAD2(12) NEDNER_ATTR_SPREAD2(16) NEDNER_ATTR_SPREAD2(20)
 #undef NEDNER_ATTR_SPREAD2
 #undef NEDNER_ATTR_SPREAD
-#define NEDNER_ATTR_BLOCKS(W) \
-    if ((e = cudaFuncSetAttribute(k_ned_spread_blocks<W>, (cudaFuncAttribute)a, (int)p.ch.smem_s))) return e;
-    NEDNER_ATTR_BLOCKS(4) NEDNER_ATTR_BLOCKS(6) NEDNER_ATTR_BLOCKS(8) NEDNER_ATTR_BLOCKS(10) NEDNER_ATTR_BLOCKS(12)
-    NEDNER_ATTR_BLOCKS(14) NEDNER_ATTR_BLOCKS(16)
-#undef NEDNER_ATTR_BLOCKS
+    if ((e = cudaFuncSetAttribute(k_ned_spread_blocks, (cudaFuncAttribute)a, (int)p.ch.smem_s))) return e;
     if ((e = cudaFuncSetAttribute(k_ned_xfft<16>, (cudaFuncAttribute)a, (int)p.ch.smem_x))) return e;
     if ((e = cudaFuncSetAttribute(k_ned_xfft<32>, (cudaFuncAttribute)a, (int)p.ch.smem_x))) return e;
     if ((e = cudaFuncSetAttribute(k_ned_yfft<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ch.smem2f))) return e;
@@ -736,19 +727,7 @@ cudaError_t launch_ned_spread_blocks(const nedner_plan_s& p, const float* g, flo
     const Geo& G = p.geo;
     const int tq = p.ch.tq, wpc = p.ch.wpc_s;
     const dim3 grid(G.Ly * (G.Lx / 16) / wpc, tq / 64);
-#define NEDNER_BLOCKS(W)                                                                                 \
-    k_ned_spread_blocks<W><<<grid, 32 * wpc, p.ch.smem_s, s>>>(G, t0, tq, g, p.t.bseg, p.t.xent_m, p.t.pent_w, \
-                                                               p.t.pent_bx, Q)
-    switch (G.w) {
-        case 4: NEDNER_BLOCKS(4); break;
-        case 6: NEDNER_BLOCKS(6); break;
-        case 8: NEDNER_BLOCKS(8); break;
-        case 10: NEDNER_BLOCKS(10); break;
-        case 12: NEDNER_BLOCKS(12); break;
-        case 14: NEDNER_BLOCKS(14); break;
-        default: NEDNER_BLOCKS(16); break;
-    }
-#undef NEDNER_BLOCKS
+    k_ned_spread_blocks<<<grid, 32 * wpc, p.ch.smem_s, s>>>(G, t0, tq, g, p.t.bseg, p.t.bent_m, p.t.bent_w, Q);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "fft.cuh"
+#include "spread_window.cuh"
 #include "internal.h"
 
 // Stage timer for the profiled entry points: records a CUDA event on the
@@ -83,9 +84,9 @@ void free_sensor_tables(DevTables& t) {
     cudaFree(t.xrow_ptr); cudaFree(t.xent_m); cudaFree(t.xent_wx); cudaFree(t.xent_bx); cudaFree(t.seg);
     cudaFree(t.xent_gx); cudaFree(t.xent_gy); cudaFree(t.xrow_first);
     cudaFree(t.xent_rc); cudaFree(t.sens_ent);
-    cudaFree(t.bseg); cudaFree(t.pent_bx); cudaFree(t.pent_w);
+    cudaFree(t.bseg); cudaFree(t.bent_m); cudaFree(t.bent_w); cudaFree(t.pent_bx); cudaFree(t.pent_w);
     cudaFree(t.pent_gx); cudaFree(t.pent_gy); cudaFree(t.gseg); cudaFree(t.lp_kcut);
-    t.bseg = nullptr; t.pent_bx = nullptr; t.pent_w = nullptr;
+    t.bseg = nullptr; t.bent_m = nullptr; t.bent_w = nullptr; t.pent_bx = nullptr; t.pent_w = nullptr;
     t.pent_gx = nullptr; t.pent_gy = nullptr; t.gseg = nullptr; t.lp_kcut = nullptr;
     t.sens_bx = t.sens_by = nullptr;
     t.sens_wx = t.sens_wy = t.sens_dwx = t.sens_dwy = t.sens_fac = nullptr;
@@ -310,6 +311,8 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     std::vector<int> pent_bx;
     std::vector<float> pent_w, pent_gx, pent_gy;
     std::vector<int2> bseg(C.split1 ? (size_t)G.Ly * nblk : 0);
+    std::vector<int> bent_m;           // per (row, block): the sensors of the entries reaching into it
+    std::vector<float> bent_w;         // and their taps aligned to the block's columns, [.][16]
     std::vector<int2> gseg(C.split1 ? (size_t)G.Ly * nblk : 0);
     std::vector<XE> tmp;
     for (int r = 0; r < G.Ly; ++r) {
@@ -354,7 +357,16 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
                 while (lo < Er && tmp[lo].bx < 16 * b - w + 1) ++lo;
                 if (hi < lo) hi = lo;
                 while (hi < Er && tmp[hi].bx < 16 * b + 16) ++hi;
-                bseg[(size_t)r * nblk + b] = make_int2(base + lo, base + hi);
+                // the block's entries with their taps aligned to its 16 columns
+                const int start = (int)bent_m.size();
+                for (int i = lo; i < hi; ++i) {
+                    float taps[16], t16[16];
+                    for (int k = 0; k < w; ++k) taps[k] = tmp[i].w * wx[(size_t)tmp[i].m * w + k];
+                    block_taps16(tmp[i].bx, 16 * b, taps, w, t16);
+                    bent_m.push_back(tmp[i].m);
+                    bent_w.insert(bent_w.end(), t16, t16 + 16);
+                }
+                bseg[(size_t)r * nblk + b] = make_int2(start, (int)bent_m.size());
             }
             // the block gather: entries whose first column is in block b
             // (second copies of wrapped entries, at bx < 0, belong to none)
@@ -429,6 +441,8 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
     if (!e) e = upload(&p.t.sens_ent, sens_ent, s);
     if (!e) e = upload(&p.t.seg, seg, s);
     if (!e) e = upload(&p.t.bseg, bseg, s);
+    if (!e) e = upload(&p.t.bent_m, bent_m, s);
+    if (!e) e = upload(&p.t.bent_w, bent_w, s);
     if (!e) e = upload(&p.t.pent_bx, pent_bx, s);
     if (!e) e = upload(&p.t.pent_w, pent_w, s);
     if (!e) e = upload(&p.t.pent_gx, pent_gx, s);
@@ -513,9 +527,8 @@ void choose_chunks(nedner_plan_s& p) {
     c.wpc_s = 4;
     {
         // per warp, double-buffered batches of 8 entries: sensor indices, and
-        // first columns, taps and 64 samples of g
-        const long pw = (G.w + 3) / 4 * 4;
-        c.smem_s = (size_t)c.wpc_s * (2 * 8 + 2 * (8 + 8 * pw + 8 * 64)) * 4;
+        // block-aligned taps (16) and 64 samples of g
+        c.smem_s = (size_t)c.wpc_s * (2 * 8 + 2 * (8 * 16 + 8 * 64)) * 4;
     }
     c.nbx = (int)std::min<long>(16, std::max<long>(1, 4096 / G.Lx));
     c.perx = ((long)G.Lx * c.nbx >= 8192) ? 32 : 16;

@@ -103,42 +103,27 @@ __device__ __forceinline__ void sweep_entry2(float2 (&acc)[2 * WT], float2* Z, i
 }
 
 // Block spread (k_ned_spread_blocks): one warp accumulates one block of 16
-// columns [c0, c0 + 16) of a grid row for 64 time samples (two per lane, as
-// above) over every entry whose W taps reach into the block.  The taps start at
-// the entry's exact first column bx (no alignment padding); with d = bx - c0 in
-// [1 - W, 15] only taps k with 0 <= d + k < 16 land in the block, so every FMA
-// adds to a column of the block and every entry's W taps are applied exactly
-// once over the blocks it touches.
-template <int W, int D>
-__device__ __forceinline__ void add_taps_block(float2 (&acc)[16], const float4 (&wv)[(W + 3) / 4], float2 g2) {
-    constexpr int k0 = D < 0 ? -D : 0;
-    constexpr int k1 = (16 - D) < W ? (16 - D) : W;
-#pragma unroll
-    for (int k = k0; k < k1; ++k) {
-        const float4 q = wv[k >> 2];
-        const float t = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
-        acc[D + k] = __ffma2_rn(make_float2(t, t), g2, acc[D + k]);
+// columns [c0, c0 + 16) of a grid row for 64 time samples (two per lane)
+// over every entry whose w taps reach into the block.  The plan stores, for
+// every (grid row, 16-column block) and every entry reaching into the block,
+// the entry's taps aligned to the block's columns (block_taps16: column c of
+// the block gets tap c0 + c - bx, zero where that is not one of the w taps),
+// so that adding an entry is 16 packed FMAs whatever its offset.
+__host__ __device__ inline void block_taps16(int bx, int c0, const float* taps, int w, float* out) {
+    for (int c = 0; c < 16; ++c) {
+        const int k = c0 + c - bx;
+        out[c] = (k >= 0 && k < w) ? taps[k] : 0.f;
     }
 }
 
-// adds one entry (first column bx) to the block starting at column c0
-template <int W>
-__device__ __forceinline__ void block_entry(float2 (&acc)[16], int bx, int c0, const float4 (&wv)[(W + 3) / 4],
-                                            float2 g2) {
-#define NEDNER_BLOCK_CASE(I) \
-    case I: add_taps_block<W, (I) - (W - 1)>(acc, wv, g2); break;
-    switch (bx - c0 + (W - 1)) {
-        NEDNER_BLOCK_CASE(0) NEDNER_BLOCK_CASE(1) NEDNER_BLOCK_CASE(2) NEDNER_BLOCK_CASE(3)
-        NEDNER_BLOCK_CASE(4) NEDNER_BLOCK_CASE(5) NEDNER_BLOCK_CASE(6) NEDNER_BLOCK_CASE(7)
-        NEDNER_BLOCK_CASE(8) NEDNER_BLOCK_CASE(9) NEDNER_BLOCK_CASE(10) NEDNER_BLOCK_CASE(11)
-        NEDNER_BLOCK_CASE(12) NEDNER_BLOCK_CASE(13) NEDNER_BLOCK_CASE(14) NEDNER_BLOCK_CASE(15)
-        NEDNER_BLOCK_CASE(16) NEDNER_BLOCK_CASE(17) NEDNER_BLOCK_CASE(18) NEDNER_BLOCK_CASE(19)
-        NEDNER_BLOCK_CASE(20) NEDNER_BLOCK_CASE(21) NEDNER_BLOCK_CASE(22) NEDNER_BLOCK_CASE(23)
-        NEDNER_BLOCK_CASE(24) NEDNER_BLOCK_CASE(25) NEDNER_BLOCK_CASE(26) NEDNER_BLOCK_CASE(27)
-        NEDNER_BLOCK_CASE(28) NEDNER_BLOCK_CASE(29) NEDNER_BLOCK_CASE(30)
-        default: break;
+__device__ __forceinline__ void block_entry16(float2 (&acc)[16], const float4 (&t)[4], float2 g2) {
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {
+        acc[4 * c4 + 0] = __ffma2_rn(make_float2(t[c4].x, t[c4].x), g2, acc[4 * c4 + 0]);
+        acc[4 * c4 + 1] = __ffma2_rn(make_float2(t[c4].y, t[c4].y), g2, acc[4 * c4 + 1]);
+        acc[4 * c4 + 2] = __ffma2_rn(make_float2(t[c4].z, t[c4].z), g2, acc[4 * c4 + 2]);
+        acc[4 * c4 + 3] = __ffma2_rn(make_float2(t[c4].w, t[c4].w), g2, acc[4 * c4 + 3]);
     }
-#undef NEDNER_BLOCK_CASE
 }
 
 // Output step of the spread stage: jx = 0..nx/2 of the row, divided by

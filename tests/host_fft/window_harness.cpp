@@ -200,7 +200,7 @@ extern "C" int host_spread_output(int Lx, int nb, int fold, const float* Zin, co
     return 0;
 }
 
-// The block spread (block_entry): the 32 lanes of a warp accumulate the
+// The block spread (block_taps16 + block_entry16): the 32 lanes of a warp accumulate the
 // 16-column block [c0, c0 + 16) over the entries whose W taps (from their
 // exact first column bx, taps [nent][4 ceil(W/4)]) reach into it; g is
 // [nent][64].  out: [16][64] (column, time sample).
@@ -211,11 +211,12 @@ static void block_sweep(int c0, int nent, const int* bx, const float* taps, cons
         float2 acc[16];
         for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
         for (int e = 0; e < nent; ++e) {
-            float4 wv[WQ];
-            for (int k4 = 0; k4 < WQ; ++k4)
-                wv[k4] = float4{taps[e * 4 * WQ + 4 * k4], taps[e * 4 * WQ + 4 * k4 + 1],
-                                taps[e * 4 * WQ + 4 * k4 + 2], taps[e * 4 * WQ + 4 * k4 + 3]};
-            block_entry<W>(acc, bx[e], c0, wv, make_float2(g[e * 64 + 2 * ln], g[e * 64 + 2 * ln + 1]));
+            // the plan's table entry: the taps aligned to the block's columns
+            float t16[16];
+            block_taps16(bx[e], c0, taps + e * 4 * WQ, W, t16);
+            float4 t[4];
+            for (int c4 = 0; c4 < 4; ++c4) t[c4] = float4{t16[4 * c4], t16[4 * c4 + 1], t16[4 * c4 + 2], t16[4 * c4 + 3]};
+            block_entry16(acc, t, make_float2(g[e * 64 + 2 * ln], g[e * 64 + 2 * ln + 1]));
         }
         for (int k = 0; k < 16; ++k) {
             out[k * 64 + 2 * ln] = acc[k].x;

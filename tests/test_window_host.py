@@ -189,7 +189,8 @@ def test_spread_output_step(lib, Lx, nb, fold):
 
 @pytest.mark.parametrize("w", [4, 6, 8, 10, 12, 14, 16])
 def test_block_spread_accumulates_exact_taps(lib, w):
-    """The block spread's accumulation (block_entry in csrc/spread_window.cuh):
+    """The block spread's accumulation (block_taps16, the plan's table entry,
+    and block_entry16 in csrc/spread_window.cuh):
     a warp's 16-column block [c0, c0 + 16) gets, from every entry whose w taps
     start anywhere in [c0 - w + 1, c0 + 15], exactly the taps that land in the
     block (all w of them for entries inside, the overlapping part at both
