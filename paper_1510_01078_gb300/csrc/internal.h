@@ -11,6 +11,10 @@
 
 namespace nedner {
 
+// taps per entry of the adjoint's block gather: the 16 + w - 1 columns an
+// entry starting anywhere in a 16-column block can reach, rounded up to 4
+__host__ __device__ constexpr int gather_aligned_taps(int w) { return (16 + w - 1 + 3) / 4 * 4; }
+
 // bits of the device status word (DevTables::status)
 constexpr int NEDNER_FLAG_NONFINITE = 2;
 
@@ -106,7 +110,8 @@ struct DevTables {
     int* bent_m = nullptr;        // [.] sensor of each (block, entry reaching into it)
     float* bent_w = nullptr;      // [.][16] its taps aligned to the block's columns (block_taps16)
     int* pent_bx = nullptr;       // [E'] first x column (negative for the second copy of a wrapped entry)
-    float* pent_w = nullptr;      // [E'][4 ceil(w/4)] x tap times y tap times sensor factor, from pent_bx on
+    float* pent_w = nullptr;      // [E'][gather_aligned_taps(w)] x tap times y tap times sensor factor, aligned to
+                                  // the 32-column window of the entry's 16-column block (the adjoint's block gather)
     float* pent_gx = nullptr;     // [E'][4 ceil(w/4)] the same with the x-tap derivative (position gradient)
     float* pent_gy = nullptr;     // [E'][4 ceil(w/4)] the same with the y-tap derivative
     int2* gseg = nullptr;         // [Ly][Lx/16] entries whose first column lies in the block (block gather)

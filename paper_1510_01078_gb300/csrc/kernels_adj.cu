@@ -785,18 +785,21 @@ __device__ __forceinline__ void block_taps_dot2(const float2 (&win)[32], int d, 
 #undef NEDNER_DOT2_CASE
 }
 
-template <int W>
-__device__ __forceinline__ float2 block_taps_dot(const float2 (&win)[32], int d, const float* t) {
-#define NEDNER_DOT_CASE(I) \
-    case I: return taps_dot<W, I>(win, t);
-    switch (d) {
-        NEDNER_DOT_CASE(0) NEDNER_DOT_CASE(1) NEDNER_DOT_CASE(2) NEDNER_DOT_CASE(3)
-        NEDNER_DOT_CASE(4) NEDNER_DOT_CASE(5) NEDNER_DOT_CASE(6) NEDNER_DOT_CASE(7)
-        NEDNER_DOT_CASE(8) NEDNER_DOT_CASE(9) NEDNER_DOT_CASE(10) NEDNER_DOT_CASE(11)
-        NEDNER_DOT_CASE(12) NEDNER_DOT_CASE(13) NEDNER_DOT_CASE(14)
-        default: return taps_dot<W, 15>(win, t);
+// sum_c t[c] win[c] over the NA window-aligned taps (zero outside the entry's
+// w), in four independent accumulators, taps read as float4
+template <int NA>
+__device__ __forceinline__ float2 aligned_taps_dot(const float2 (&win)[32], const float* t) {
+    const float4* t4 = reinterpret_cast<const float4*>(t);
+    float2 a[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int c4 = 0; c4 < NA / 4; ++c4) {
+        const float4 q = t4[c4];
+        a[0] = __ffma2_rn(make_float2(q.x, q.x), win[4 * c4 + 0], a[0]);
+        a[1] = __ffma2_rn(make_float2(q.y, q.y), win[4 * c4 + 1], a[1]);
+        a[2] = __ffma2_rn(make_float2(q.z, q.z), win[4 * c4 + 2], a[2]);
+        a[3] = __ffma2_rn(make_float2(q.w, q.w), win[4 * c4 + 3], a[3]);
     }
-#undef NEDNER_DOT_CASE
+    return __fadd2_rn(__fadd2_rn(a[0], a[1]), __fadd2_rn(a[2], a[3]));
 }
 
 template <int W, bool GRAD>
@@ -811,7 +814,10 @@ __global__ void __launch_bounds__(128, 4) k_ned_gather_blocks(Geo G, int nb, int
                                                               float2* __restrict__ Qe) {
     constexpr int PW = (W + 3) / 4 * 4;
     constexpr int BE = 32;                                           // entries per staged batch
-    constexpr int NTAP = GRAD ? 2 * PW : PW;
+    // adjoint: taps aligned to the window (no branch on the offset); gradient:
+    // the two derivative tap sets from the entry's first column
+    constexpr int TW = GRAD ? PW : gather_aligned_taps(W);          // taps per set in the table
+    constexpr int NTAP = GRAD ? 2 * PW : TW;
     constexpr int BSZ = BE * (3 + NTAP);                             // one batch (4-byte words)
     extern __shared__ float4 smem4[];
     const int q = threadIdx.x >> 5;
@@ -844,9 +850,9 @@ __global__ void __launch_bounds__(128, 4) k_ned_gather_blocks(Geo G, int nb, int
             if (GRAD) cp_async(d + 2 * BE + ln, xent_m + e0 + ln, 4);
         }
         float* tp = reinterpret_cast<float*>(d + 3 * BE);
-        for (int i = ln; i < n * (PW / 4); i += 32) {
-            const int j = i / (PW / 4), k4 = i - j * (PW / 4);
-            cp_async(tp + j * NTAP + 4 * k4, taps_a + (size_t)(e0 + j) * PW + 4 * k4, 16);
+        for (int i = ln; i < n * (TW / 4); i += 32) {
+            const int j = i / (TW / 4), k4 = i - j * (TW / 4);
+            cp_async(tp + j * NTAP + 4 * k4, taps_a + (size_t)(e0 + j) * TW + 4 * k4, 16);
             if (GRAD) cp_async(tp + j * NTAP + PW + 4 * k4, taps_b + (size_t)(e0 + j) * PW + 4 * k4, 16);
         }
     };
@@ -863,7 +869,7 @@ __global__ void __launch_bounds__(128, 4) k_ned_gather_blocks(Geo G, int nb, int
         if (!GRAD) {
 #pragma unroll 1
             for (int j = 0; j < n; ++j) {
-                const float2 va = block_taps_dot<W>(win, d[j] - c0, tp + j * NTAP);
+                const float2 va = aligned_taps_dot<TW>(win, tp + j * NTAP);
                 reinterpret_cast<float2*>(E + (size_t)d[BE + j] * Tp + nc)[tl >> 1] = va;
             }
         } else {

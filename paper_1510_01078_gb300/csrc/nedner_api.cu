@@ -333,8 +333,14 @@ nedner_status build_sensor_tables(nedner_plan_s& p, cudaStream_t s) {
             xent_e.push_back(x.e);
             if (C.split1) {
                 pent_bx.push_back(x.bx);
+                // the adjoint's block gather: taps aligned to the 32-column
+                // window of the entry's 16-column block (offset bx mod 16)
+                const int d16 = ((x.bx % 16) + 16) % 16;
+                for (int c = 0; c < gather_aligned_taps(w); ++c) {
+                    const int k = c - d16;
+                    pent_w.push_back(k >= 0 && k < w ? x.w * wx[(size_t)x.m * w + k] : 0.f);
+                }
                 for (int k = 0; k < PW; ++k) {
-                    pent_w.push_back(k < w ? x.w * wx[(size_t)x.m * w + k] : 0.f);
                     pent_gx.push_back(k < w ? x.w * dwx[(size_t)x.m * w + k] : 0.f);
                     pent_gy.push_back(k < w ? x.dw * wx[(size_t)x.m * w + k] : 0.f);
                 }
@@ -539,7 +545,7 @@ void choose_chunks(nedner_plan_s& p) {
         // block gather, per warp: two batches of 32 entries (first column,
         // row-CSR index, sensor; taps; for the gradient a second tap set)
         const long pw = (G.w + 3) / 4 * 4;
-        c.smem_ga = (size_t)4 * 2 * 32 * (3 + pw) * 4;
+        c.smem_ga = (size_t)4 * 2 * 32 * (3 + gather_aligned_taps(G.w)) * 4;
         c.smem_gg = (size_t)4 * 2 * 32 * (3 + 2 * pw) * 4;
     }
     c.gsplit = 0;
