@@ -13,6 +13,9 @@ namespace nedner {
 
 // taps per entry of the adjoint's block gather: the 16 + w - 1 columns an
 // entry starting anywhere in a 16-column block can reach, rounded up to 4
+// entries per staged batch of a warp of the block spread
+constexpr int SPREAD_BATCH = 8;    // 16 was measured slower on C3 (0.81 against 0.76 ms): 5 CTAs per SM instead of 6
+
 __host__ __device__ constexpr int gather_aligned_taps(int w) { return (16 + w - 1 + 3) / 4 * 4; }
 
 // bits of the device status word (DevTables::status)

@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
 // its taps aligned to the block's 16 columns (block_taps16), so an entry is
 // 16 packed FMAs with no branch on its offset (block_entry16); the block's
 // entries are one range bseg[row][block] of bent_m / bent_w.  Entries are
-// staged eight at a time per warp (sensor indices one batch ahead, then taps
+// staged SPREAD_BATCH at a time per warp (sensor indices one batch ahead, then taps
 // and samples of g by asynchronous copies while the current batch is added).
 // The warp then stores its 16 columns (128 contiguous bytes per column and
 // 32 samples) and is done: no shared row buffer and no barrier, so warps of
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int
                                                               const int* __restrict__ bent_m,
                                                               const float* __restrict__ bent_w,
                                                               float* __restrict__ Q) {
-    constexpr int B = 8, C = 64, NB = 32;
+    constexpr int B = SPREAD_BATCH, C = 64, NB = 32;
     constexpr int DB = B * 16;                                      // taps before the g block (floats)
     constexpr int dsz = DB + B * C;                                 // one data buffer (4-byte words)
     extern __shared__ float4 smem4[];
@@ -288,8 +288,12 @@ __global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int
         const int e0 = rg.x + b * B, nb_ = min(B, rg.y - e0);
         float* d = st_d + (b & 1) * dsz;
         const int* mm = st_m + (b & 1) * B;
-        // 8 entries x 16 taps = 32 copies of 16 bytes: one per lane
-        if ((ln >> 2) < nb_) cp_async(d + 4 * ln, bent_w + (size_t)e0 * 16 + 4 * ln, 16);
+        // B entries x 16 taps = 4 B copies of 16 bytes
+#pragma unroll
+        for (int r = 0; r < B / 8; ++r) {
+            const int i = ln + 32 * r;
+            if ((i >> 2) < nb_) cp_async(d + 4 * i, bent_w + (size_t)e0 * 16 + 4 * i, 16);
+        }
 #pragma unroll
         for (int r = 0; r < B * (C / 4) / 32; ++r) {
             const int i = ln + 32 * r;
