@@ -276,18 +276,25 @@ __global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
 
-    int* st_m = reinterpret_cast<int*>(smem4) + (size_t)q * (2 * B + 2 * dsz);   // [2][B]
-    float* st_d = reinterpret_cast<float*>(st_m + 2 * B);                         // [2][dsz]
+    // sensor indices NM batches deep, data ND batches deep: group k of copies
+    // holds the data of batch k and the indices of batch k + 3, so the data of
+    // batch b + 2 are issued while batch b is added (their indices arrived two
+    // groups earlier)
+    constexpr int NM = 4, ND = 3;
+    int* st_m = reinterpret_cast<int*>(smem4) + (size_t)q * (NM * B + ND * dsz);  // [NM][B]
+    float* st_d = reinterpret_cast<float*>(st_m + NM * B);                          // [ND][dsz]
     const int nent = rg.y - rg.x;
     const int nbt = (nent + B - 1) / B;
     auto issue_m = [&](int b) {
+        if (b >= nbt) return;
         const int e0 = rg.x + b * B, nb_ = min(B, rg.y - e0);
-        if (ln < nb_) cp_async(st_m + (b & 1) * B + ln, bent_m + e0 + ln, 4);
+        if (ln < nb_) cp_async(st_m + (b % NM) * B + ln, bent_m + e0 + ln, 4);
     };
     auto issue_data = [&](int b) {
+        if (b >= nbt) return;
         const int e0 = rg.x + b * B, nb_ = min(B, rg.y - e0);
-        float* d = st_d + (b & 1) * dsz;
-        const int* mm = st_m + (b & 1) * B;
+        float* d = st_d + (b % ND) * dsz;
+        const int* mm = st_m + (b % NM) * B;
         // B entries x 16 taps = 4 B copies of 16 bytes
 #pragma unroll
         for (int r = 0; r < B / 8; ++r) {
@@ -303,22 +310,27 @@ __global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int
     };
     if (nbt > 0) {
         issue_m(0);
+        issue_m(1);
+        issue_m(2);
         cp_async_commit();
         cp_async_wait_all();
         __syncwarp();
         issue_data(0);
-        if (nbt > 1) issue_m(1);
-        cp_async_commit();
+        issue_m(3);
+        cp_async_commit();                                          // group 0
+        issue_data(1);
+        issue_m(4);
+        cp_async_commit();                                          // group 1
     }
     for (int b = 0; b < nbt; ++b) {
-        cp_async_wait_all();
+        cp_async_wait_group<1>();                                   // groups up to b done
         __syncwarp();
-        if (b + 1 < nbt) issue_data(b + 1);
-        if (b + 2 < nbt) issue_m(b + 2);
-        cp_async_commit();
+        issue_data(b + 2);                                          // its indices: group b - 1
+        issue_m(b + 5);
+        cp_async_commit();                                          // group b + 2
         const int nbat = min(B, nent - b * B);
-        const float4* wst = reinterpret_cast<const float4*>(st_d + (b & 1) * dsz);
-        const float2* st_g = reinterpret_cast<const float2*>(st_d + (b & 1) * dsz + DB);
+        const float4* wst = reinterpret_cast<const float4*>(st_d + (b % ND) * dsz);
+        const float2* st_g = reinterpret_cast<const float2*>(st_d + (b % ND) * dsz + DB);
 #pragma unroll 1
         for (int j = 0; j < nbat; ++j) {
             const float4 t[4] = {wst[4 * j], wst[4 * j + 1], wst[4 * j + 2], wst[4 * j + 3]};
@@ -326,6 +338,7 @@ __global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int
         }
         __syncwarp();
     }
+    cp_async_wait_all();
     // Q is [tq/32][Ly][Lx][32]: lanes 0-15 hold the first 32 samples of the
     // warp's 64, lanes 16-31 the next 32; a column's 32 samples are 128
     // contiguous bytes, and the 16 columns of the block 2 KB

@@ -532,10 +532,10 @@ void choose_chunks(nedner_plan_s& p) {
     c.split1 = (G.Nt >= 64 && G.Lx >= 64) ? 1 : 0;
     c.wpc_s = 4;
     {
-        // per warp, double-buffered batches of SPREAD_BATCH entries: sensor
-        // indices, and block-aligned taps (16) and 64 samples of g
+        // per warp, batches of SPREAD_BATCH entries: sensor indices (four
+        // buffers), and block-aligned taps (16) and 64 samples of g (three)
         constexpr long B = SPREAD_BATCH;
-        c.smem_s = (size_t)c.wpc_s * (2 * B + 2 * (B * 16 + B * 64)) * 4;
+        c.smem_s = (size_t)c.wpc_s * (4 * B + 3 * (B * 16 + B * 64)) * 4;
     }
     c.nbx = (int)std::min<long>(16, std::max<long>(1, 4096 / G.Lx));
     c.perx = ((long)G.Lx * c.nbx >= 8192) ? 32 : 16;
