@@ -939,6 +939,40 @@ __global__ void k_adj_sum(Geo G, int nb, int Tp, const float* __restrict__ E, co
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, NEDNER_FLAG_NONFINITE);
 }
 
+// the same, four consecutive samples per thread (16-byte loads and stores;
+// Tp a multiple of 4, g 16-byte aligned); the same sums in the same order
+__global__ void k_adj_sum4(Geo G, int nb, int Tp, const float* __restrict__ E, const int* __restrict__ sens_ent,
+                           float* __restrict__ g, int* __restrict__ status) {
+    const size_t total = (size_t)G.M * Tp / 4;
+    const int ltp = ilog2(Tp) - 2;
+    bool bad = false;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i >> ltp), t = 4 * (int)(i & ((Tp >> 2) - 1));
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < G.w; ++k) {
+            const float4 e = *reinterpret_cast<const float4*>(
+                &E[(size_t)__ldg(&sens_ent[(size_t)m * G.w + k]) * Tp + t]);
+            v.x += e.x;
+            v.y += e.y;
+            v.z += e.z;
+            v.w += e.w;
+        }
+        bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+        *reinterpret_cast<float4*>(&g[(size_t)m * G.Nt + nb + t]) = v;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, NEDNER_FLAG_NONFINITE);
+}
+
+// entry sum of one pass: the four-sample form where alignment allows
+static void launch_adj_sum(const nedner_plan_s& p, int nb, int Tp, const float* E, float* g, cudaStream_t s) {
+    const Geo& G = p.geo;
+    const bool vec = (Tp % 4) == 0 && (G.Nt % 4) == 0 && ((uintptr_t)g & 15) == 0;
+    const size_t total = (size_t)G.M * Tp / (vec ? 4 : 1);
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    if (vec) k_adj_sum4<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g, p.t.status);
+    else k_adj_sum<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g, p.t.status);
+}
+
 // dL/d(x_m, y_m) = sum over the sensor's w entries and the time chunks of Qe
 // (one warp per sensor, lanes over (entry, chunk) pairs, fixed order)
 __global__ void k_grad_sum(Geo G, int nch, const float2* __restrict__ Qe, const int* __restrict__ sens_ent,
@@ -1101,14 +1135,12 @@ cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E,
                               StageTimer* tm) {
     const Geo& G = p.geo;
     const int C = p.ch.ca, Tp = p.ch.tp_adj;
-    const size_t total = (size_t)G.M * Tp;
-    const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
     if (p.ch.gsplit) {
         cudaError_t e = cudaSuccess;
         for (int nb = 0; nb < G.Nt && !e; nb += Tp) {
             e = launch_block_gather(p, R, pass_grid(p), nb, Tp, false, nullptr, E, nullptr, s, tm);
             if (e) break;
-            k_adj_sum<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g, p.t.status);
+            launch_adj_sum(p, nb, Tp, E, g, s);
             stage_mark(tm, 6);
             e = cudaGetLastError();
         }
@@ -1137,7 +1169,7 @@ cudaError_t launch_adj_gather(const nedner_plan_s& p, const float2* R, float* E,
         NEDNER_GATHER_SWITCH(NEDNER_ADJ)
 #undef NEDNER_ADJ
         stage_mark(tm, 5);
-        k_adj_sum<<<blocks, 256, 0, s>>>(G, nb, Tp, E, p.t.sens_ent, g, p.t.status);
+        launch_adj_sum(p, nb, Tp, E, g, s);
         stage_mark(tm, 6);
     }
     return cudaGetLastError();
