@@ -803,7 +803,7 @@ __device__ __forceinline__ float2 aligned_taps_dot(const float2 (&win)[32], cons
 }
 
 template <int W, bool GRAD>
-__global__ void __launch_bounds__(128, 4) k_ned_gather_blocks(Geo G, int nb, int Tp, const float* __restrict__ Qb,
+__global__ void __launch_bounds__(128, GRAD ? 4 : 5) k_ned_gather_blocks(Geo G, int nb, int Tp, const float* __restrict__ Qb,
                                                               const int2* __restrict__ gseg,
                                                               const int* __restrict__ pent_bx,
                                                               const int* __restrict__ xent_rc,
@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(128, 4) k_ned_gather_blocks(Geo G, int nb, int
                                                g + (size_t)d[2 * BE + j0 + u] * G.Nt + nb + nc + tl))
                                          : make_float2(0.f, 0.f);
                 float sv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
+#pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     float sx = 0.f, sy = 0.f;
                     const int j = j0 + u;
