@@ -4,14 +4,20 @@
 // Each kernel is the exact transpose (for real inner products) of one forward
 // stage, run in reverse order:
 //   p  [nz][ny][nx]
-//     -- img_xr2c_adj    -->  Y [nx/2+1][nz][ny]    r2c along x, times 1 or 2
-//     -- img_yfft_adj    -->  V [nx/2+1][ny][nz]    forward FFT along y
+//     -- img_xr2c_adj    -->  Y [nx/2+1][nz][ny]       r2c along x, times 1 or 2
+//     -- img_yfft_adj    -->  V [nx/2+1][ny][nz]       forward FFT along y
 //     -- ner_lines_adj   -->  Ghat [nx/2+1][ny+1][Nt]  z-FFT, fold^T, W, NER spreading, IFFT
-//     -- ned_yfft_adj    -->  R [nx/2+1][Ly][Nt]    pad, deconvolve, IFFT along y
-//     -- ned_interp_adj  -->  P [2][M][Nt]          real IFFT along x, interpolation per row block
-//     -- adj_finish      -->  g [M][Nt]             sum of the (at most two) row-block partials
-// The position gradient replaces the last two by ned_grad (derivative taps,
-// dotted with g over time) and grad_finish.
+//     -- ned_yfft_adj    -->  R [nx/2+1][Ly][Nt]       pad, deconvolve, IFFT along y
+// then, per pass of Tp time samples,
+//     -- ned_xfft_adj    -->  Qb [Tp/32][Ly][Lx][32]   real IFFT along x (the forward grid's layout)
+//     -- ned_gather_blocks --> E [entry][Tp]          the window taps of every (sensor, row block)
+//                                                      entry dotted with the grid
+//     -- adj_sum         -->  g [M][Nt]                sum of a sensor's entries
+// For records too short for passes (or a plan without room for the pass
+// grid) ned_gather_rows does the real IFFT along x and the gather per grid
+// row in one kernel.  The position gradient gathers with the derivative taps,
+// dots them with g over time (one value per entry and chunk of samples) and
+// sums them per sensor (grad_sum).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -94,8 +100,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_img_yfft_adj(Geo G, int C, con
 //   Tbar      *= coefficient(e) (Jacobian, scale, band mask)
 //   Bbar[mu] = sum_e exp(+i pi nu_e) phi(sigma nu_e - mu) Tbar[e]   (spreading)
 //   Ghat-bar[n] = IFFT_Lt(Bbar)[(n - Nt/2) mod Lt] / phihat((n - Nt/2)/Lt)
-// Spreading uses shared-memory atomics: a CTA owns its line, so nothing is
-// shared between CTAs.
+// The spreading is done as a gather per grid point (ner_adj_line): no atomics
+// unless a band is longer than the grid, and a CTA owns its lines, so nothing
+// is shared between CTAs.
 // ---------------------------------------------------------------------------
 struct FF2 {
     float hi, lo;
@@ -123,33 +130,6 @@ __device__ __forceinline__ FF2 nu_abs2(const Geo& G, float2 axy, int l) {
     const float r = sqrtf(s.hi);
     const float resid = fmaf(-r, r, s.hi) + s.lo;
     return quick_two_sum2(r, resid * (0.5f / r));
-}
-
-// B[(mu0 + k) mod Lt] += P_k(s) v for the W taps, into column col of the padded
-// buffer with 2^lld columns; tap W-1-k is tap k at -s (see ner_gather)
-template <int W, int D>
-__device__ __forceinline__ void ner_scatter(const TapPoly& P, float2* LA, int mu0, float s, int Lt, int lld, int col,
-                                            float2 v) {
-    constexpr int DE = D & ~1;
-    constexpr int DO = (D & 1) ? D : D - 1;
-    const float u = s * s;
-#pragma unroll
-    for (int k = 0; k < W / 2; ++k) {
-        float e = P.c[k * (D + 1) + DE];
-#pragma unroll
-        for (int d = DE - 2; d >= 0; d -= 2) e = fmaf(e, u, P.c[k * (D + 1) + d]);
-        float o = P.c[k * (D + 1) + DO];
-#pragma unroll
-        for (int d = DO - 2; d >= 1; d -= 2) o = fmaf(o, u, P.c[k * (D + 1) + d]);
-        const float so = s * o;
-        const float pk = e + so, pm = e - so;
-        float2* dk = &LA[padx((((mu0 + k) & (Lt - 1)) << lld) + col)];
-        float2* dm = &LA[padx((((mu0 + W - 1 - k) & (Lt - 1)) << lld) + col)];
-        atomicAdd(&dk->x, pk * v.x);
-        atomicAdd(&dk->y, pk * v.y);
-        atomicAdd(&dm->x, pm * v.x);
-        atomicAdd(&dm->y, pm * v.y);
-    }
 }
 
 // The transposed NER value of one depth frequency l of a line: its weight
