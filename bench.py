@@ -393,6 +393,10 @@ def main():
     ap.add_argument("--nt", type=int, default=None,
                     help="record length override (nz scaled with it): the workload's lateral geometry and kernels "
                          "on a smaller case, for profiler captures; not a bench line")
+    ap.add_argument("--lateral", type=int, default=None,
+                    help="lateral grid override (the central lateral x lateral voxels at the same spacing, the "
+                         "sensors inside): the workload's record and depth on fewer lines, for profiler "
+                         "captures; not a bench line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-transposed", action="store_true", help="time the forward only")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT reference timings")
@@ -410,7 +414,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     from paper_1510_01078_gb300 import inputs
-    cfg = inputs.make_config(CONFIGS[args.config], Nt=args.nt)
+    cfg = inputs.make_config(CONFIGS[args.config], Nt=args.nt, lateral=args.lateral)
     voxels = cfg["nx"] * cfg["ny"] * cfg["nz"]
 
     if args.impl == "reference":

@@ -156,12 +156,16 @@ def voxelise(balls: Balls, nx, ny, nz, dx, dy, dz) -> np.ndarray:
 CONFIG_NAMES = ["c1_tiny_fp64", "c2_fp32_64x64", "c3_paper_scale", "c4_differentiation", "c5_tensor_gemm"]
 
 
-def make_config(idx: int, with_data: bool = True, Nt: Optional[int] = None) -> Dict:
+def make_config(idx: int, with_data: bool = True, Nt: Optional[int] = None,
+                lateral: Optional[int] = None) -> Dict:
     """Workload ``idx`` (0..4); seed 1510 + idx.  Returns a dict with the
     geometry (sensor_xy, h, Nt, dt, c, nx, ny, nz, dx, dy, dz), the phantom and,
     if ``with_data``, the float64 data g (M, Nt).  ``Nt`` shortens (or
     lengthens) the record, nz scaled with it so that dz stays the same: the
-    same lateral geometry and kernels on a smaller case."""
+    same lateral geometry and kernels on a smaller case.  ``lateral`` (a power
+    of two below nx, square lateral grids only) keeps the central lateral x
+    lateral voxels at the same spacing, with the sensors and balls inside that
+    square: the same record, depth and sensor density on fewer lines."""
     nt_req = Nt
     rng = np.random.default_rng(1510 + idx)
     c = C_SOUND
@@ -219,6 +223,17 @@ def make_config(idx: int, with_data: bool = True, Nt: Optional[int] = None) -> D
     dy = X / ny
     dz = c * Nt * dt / nz          # Z = c Nt dt: the record spans the periodic depth range
     name = CONFIG_NAMES[idx] + ("" if nt_req is None or nt_req == Nt0 else "_nt%d" % Nt)
+    if lateral is not None and lateral != nx:
+        if nx != ny or lateral < 8 or lateral > nx or lateral & (lateral - 1):
+            raise ValueError("lateral must be a power of two >= 8 below nx, on a square grid")
+        half = 0.5 * lateral * dx
+        keep = np.all(np.abs(xy) < 0.98 * half, axis=1)
+        xy, h = xy[keep], h[keep]
+        inside = np.all(np.abs(balls.centres[:, :2]) + balls.radii[:, None] < half, axis=1)
+        balls = Balls(balls.centres[inside], balls.radii[inside], balls.amps[inside])
+        extra = {}                        # a cropped tensor grid is no longer the workload's grid
+        nx = ny = int(lateral)
+        name += "_lat%d" % nx
     cfg = dict(name=name, sensor_xy=xy, h=h, Nt=Nt, dt=dt, c=c, nx=nx, ny=ny, nz=nz,
                dx=dx, dy=dy, dz=dz, balls=balls, snr_db=snr, seed=1510 + idx, **extra)
     if with_data:

@@ -39,3 +39,20 @@ def test_sampled_error_sees_a_planted_error():
     F = oracle.spectrum_block(pr, cfg["g"], jx, jy, oracle.index_set(cfg["nz"]))
     rl2, _ = bench.sampled_errors(bad, jx, jy, F)
     assert 3e-4 < rl2 < 3e-3, rl2
+
+
+def test_lateral_crop_keeps_spacing_density_and_aperture():
+    full = inputs.make_config(2, with_data=False)
+    lat = inputs.make_config(2, with_data=False, lateral=128)
+    assert (lat["nx"], lat["ny"], lat["nz"], lat["Nt"]) == (128, 128, full["nz"], full["Nt"])
+    assert lat["dx"] == full["dx"] and lat["dy"] == full["dy"] and lat["dz"] == full["dz"]
+    half = 0.5 * lat["nx"] * lat["dx"]
+    xy_full, xy_lat = full["sensor_xy"], lat["sensor_xy"]
+    assert np.abs(xy_lat).max() < half
+    # exactly the full layout's sensors inside the square, with their weights
+    keep = np.all(np.abs(xy_full) < 0.98 * half, axis=1)
+    np.testing.assert_array_equal(xy_lat, xy_full[keep])
+    np.testing.assert_array_equal(lat["h"], full["h"][keep])
+    b = lat["balls"]
+    assert np.all(np.abs(b.centres[:, :2]) + b.radii[:, None] < half)
+    assert lat["name"] == "c3_paper_scale_lat128"
