@@ -405,8 +405,9 @@ int nedner_plan_info(nedner_plan_t plan, int64_t* out, int nout);
  * (adjoint, gradient) kernels; then split1 (1: stage (a) runs as block spread,
  * x-FFT and y-FFT per chunk of tq time samples), tq, the block spread's warps
  * per CTA, the x-FFT kernel's complex columns, threads and values per thread
- * per CTA, the shared memory of both, and that of the transposed NER.
- * Returns the number of values (30), or -1 for
+ * per CTA, the shared memory of both, that of the transposed NER and the
+ * depth frequencies of one line it holds at a time.
+ * Returns the number of values (31), or -1 for
  * a geometry nedner_plan rejects or a null out.  No paper counterpart.
  */
 int nedner_work_split(int nx, int ny, int nz, int Nt, int w, int64_t* out, int nout);

@@ -60,6 +60,7 @@ struct Chunks {
     int threads_adj;   // threads of the two-sample gather CTA (256, or 512 for 2nx = 512)
     int tp_adj;    // time samples per pass of the transposed gather (its entry buffer holds M w tp_adj floats)
     int lpc;       // line groups per CTA in the NER stage
+    int icap3a;    // depth frequencies of one line held at a time by the transposed NER
     int threads3;  // threads per CTA in the NER stage
     size_t smem1, smem2f, smem3, smem3a, smem4, smem5;   // smem3a: the transposed NER
     size_t smem_adj, smem_grad;

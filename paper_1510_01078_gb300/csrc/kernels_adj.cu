@@ -204,13 +204,10 @@ __device__ __forceinline__ void ner_taps(const TapPoly& P, float s, float* w) {
     }
 }
 
-// items of one line held at a time by the transposed NER (a line has nz + 1)
-constexpr int NER_ADJ_ICAP = 1025;
-
 // One line of the transposed NER into column col of the padded line buffer
 // LA (2^lld columns, zero on entry): Bbar[mu] = sum_l P_{mu - mu0_l}(s_l) v_l
 // over the depth frequencies whose taps reach mu.  The nz + 1 depth
-// frequencies are taken in chunks of at most NER_ADJ_ICAP: phase 1 stores each
+// frequencies are taken in chunks of at most icap: phase 1 stores each
 // one's mu0, v and W tap weights (it_mu0, it_v, it_w); phase 2 gives each grid
 // point of the chunk's band [mu0_first, mu0_last + W) to one thread, which
 // finds the l reaching it by binary search in the non-decreasing mu0 (two
@@ -222,11 +219,11 @@ constexpr int NER_ADJ_ICAP = 1025;
 // inverse FFT's input is zero on [Lt/4, 3Lt/4).
 template <int W, int D, int NT, typename TB>
 __device__ bool ner_adj_line(const Geo& G, const TapPoly& P, float2 axy, bool j0, TB tb_of, float2* LA, int lld,
-                             int col, int* it_mu0, float2* it_v, float* it_w) {
+                             int col, int icap, int* it_mu0, float2* it_v, float* it_w) {
     const int nz1 = G.nz + 1, half_nz = G.nz / 2;
     bool zp = true;
-    for (int e0 = 0; e0 < nz1; e0 += NER_ADJ_ICAP) {
-        const int ni = min(NER_ADJ_ICAP, nz1 - e0);
+    for (int e0 = 0; e0 < nz1; e0 += icap) {
+        const int ni = min(icap, nz1 - e0);
         for (int i = threadIdx.x; i < ni; i += NT) {
             const NerAdjItem it = ner_adj_item(G, axy, j0, e0 + i - half_nz, tb_of(e0 + i));
             float w[W];
@@ -302,8 +299,9 @@ __device__ bool ner_adj_line(const Geo& G, const TapPoly& P, float2 axy, bool j0
 // samples, divided by phihat in time and by phihat(jy/Ly) (the transposed
 // y-FFT's deconvolution, applied here), are the lines of Ghat.
 template <int W, int D, int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines_adj(Geo G, const __grid_constant__ TapPoly P,
-                                                                       int LPC, const float2* __restrict__ V,
+__global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) k_ner_lines_adj(Geo G, const __grid_constant__ TapPoly P,
+                                                                       int LPC, int icap,
+                                                                       const float2* __restrict__ V,
                                                                        const float2* __restrict__ axy_tab,
                                                                        const float* __restrict__ deconv_t,
                                                                        const float* __restrict__ deconv_y,
@@ -314,7 +312,6 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines_adj(Geo G, 
     const int nz1 = G.nz + 1;
     float2* LA = reinterpret_cast<float2*>(smem4);                 // [Lt][LPC], padded
     float2* UA = LA + padded_len(G.Lt * LPC);                      // [nz][LPC], padded
-    const int icap = min(nz1, NER_ADJ_ICAP);
     float2* it_v = UA + padded_len(G.nz * LPC);                    // [icap] (items of one line)
     int* it_mu0 = reinterpret_cast<int*>(it_v + icap);             // [icap]
     float* it_w = reinterpret_cast<float*>(it_mu0 + icap);         // [icap][W + 1]
@@ -347,8 +344,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines_adj(Geo G, 
         auto tb_of = [&](int e) {
             return e > 0 ? cscale(UA[padx(slot_of(e) << llpc)], cb) : make_float2(0.f, 0.f);
         };
-        const bool zp = ner_adj_line<W, D, NT>(G, P, __ldg(&axy_tab[lx]), false, tb_of, LA, 0, 0, it_mu0, it_v,
-                                              it_w);
+        const bool zp = ner_adj_line<W, D, NT>(G, P, __ldg(&axy_tab[lx]), false, tb_of, LA, 0, 0, icap, it_mu0,
+                                              it_v, it_w);
         if (zp) block_fft_ip<PER, true>(LA, G.Lt, 1, +1, tw);
         else block_fft_ip<PER>(LA, G.Lt, 1, +1, tw);
         float2* dst = Ghat + lx * G.Nt;
@@ -372,7 +369,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines_adj(Geo G, 
             return tb;
         };
         zp &= ner_adj_line<W, D, NT>(G, P, __ldg(&axy_tab[line0 + c]), kx == 0 && ky == 0, tb_of, LA, llpc, c,
-                                     it_mu0, it_v, it_w);
+                                     icap, it_mu0, it_v, it_w);
     }
     if (zp) block_fft_ip<PER, true>(LA, G.Lt, LPC, +1, tw);
     else block_fft_ip<PER>(LA, G.Lt, LPC, +1, tw);
@@ -1037,10 +1034,12 @@ cudaError_t launch_ner_lines_adj(const nedner_plan_s& p, const float2* V, float2
     const dim3 grid(G.nxh * (G.ny / p.ch.lpc));
 #define NEDNER_NER(W, D)                                                                                        \
     if (p.ch.threads3 <= 256)                                                                                   \
-        k_ner_lines_adj<W, D, 256><<<grid, 256, p.ch.smem3a, s>>>(G, p.tap, p.ch.lpc, V, p.t.axy, p.t.deconv_t, \
+        k_ner_lines_adj<W, D, 256><<<grid, 256, p.ch.smem3a, s>>>(G, p.tap, p.ch.lpc, p.ch.icap3a, V, p.t.axy,   \
+                                                                  p.t.deconv_t,                                \
                                                                   p.t.deconv_y, p.t.tw, Ghat);                  \
     else                                                                                                        \
-        k_ner_lines_adj<W, D, 512><<<grid, 512, p.ch.smem3a, s>>>(G, p.tap, p.ch.lpc, V, p.t.axy, p.t.deconv_t, \
+        k_ner_lines_adj<W, D, 512><<<grid, 512, p.ch.smem3a, s>>>(G, p.tap, p.ch.lpc, p.ch.icap3a, V, p.t.axy,   \
+                                                                  p.t.deconv_t,                                \
                                                                   p.t.deconv_y, p.t.tw, Ghat)
     switch (G.w) {
         case 4: NEDNER_NER(4, 10); break;

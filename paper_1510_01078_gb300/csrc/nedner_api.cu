@@ -613,10 +613,19 @@ void choose_chunks(nedner_plan_s& p) {
            (long)G.nz * c.lpc * 2 <= 16L * c.threads3)
         c.lpc *= 2;
     c.smem3 = (size_t)(padded(G.Lt * c.lpc) + (c.lpc + 1) * (G.nz + 1) + padded(G.nz * c.lpc)) * 8;
-    // transposed NER: line buffers, Ubar, then one line's items (value, first
-    // grid point, w tap weights)
-    c.smem3a = (size_t)(padded(G.Lt * c.lpc) + padded(G.nz * c.lpc)) * 8 +
-               (size_t)std::min(G.nz + 1, 1025) * (8 + 4 + 4 * (G.w + 1));
+    // transposed NER: line buffers, Ubar, then the items (value, first grid
+    // point, w tap weights) of icap3a depth frequencies of one line at a time:
+    // all nz + 1 (at most 1025), or half of them where that lets a fourth CTA
+    // of 256 threads share an SM
+    {
+        const size_t base = (size_t)(padded(G.Lt * c.lpc) + padded(G.nz * c.lpc)) * 8;
+        const size_t per_item = 8 + 4 + 4 * (size_t)(G.w + 1);
+        const size_t four = 228 * 1024 / 4 - 1024;       // per CTA for four CTAs per SM
+        const int all = std::min(G.nz + 1, 1025), half = (G.nz + 2) / 2;
+        c.icap3a = (c.threads3 <= 256 && base + all * per_item > four && base + half * per_item <= four) ? half
+                                                                                                       : all;
+        c.smem3a = base + (size_t)c.icap3a * per_item;
+    }
     // inverse y- and x-FFTs: C <= 16 columns (conflict-free padded loads and
     // stores), N * C <= 2048 (16 values per thread of 128)
     c.c4 = (int)std::min<long>(std::min<long>(16, G.nz), 2048 / G.ny);
@@ -1011,7 +1020,7 @@ int nedner_work_split(int nx, int ny, int nz, int Nt, int w, int64_t* out, int n
                          c.tpl_adj, c.threads_adj, c.lpc, c.threads3, (int64_t)c.smem1, (int64_t)c.smem2f,
                          (int64_t)c.smem3, (int64_t)c.smem4, (int64_t)c.smem5, (int64_t)c.smem_adj,
                          (int64_t)c.smem_grad, c.split1, c.tq, c.wpc_s, c.nbx, c.thx, c.perx, (int64_t)c.smem_s,
-                         (int64_t)c.smem_x, (int64_t)c.smem3a};
+                         (int64_t)c.smem_x, (int64_t)c.smem3a, c.icap3a};
     const int n = (int)(sizeof(v) / sizeof(v[0]));
     for (int i = 0; i < n && i < nout; ++i) out[i] = v[i];
     return n;

@@ -452,7 +452,8 @@ def reconstruct(plan: Plan, g, sensor_xy=None):
 
 WORK_SPLIT_FIELDS = ("c1", "c2f", "c4", "c5", "groups1", "threads1", "per1", "tpl1", "ca", "per_adj", "tpl_adj",
                      "threads_adj", "lpc", "threads3", "smem1", "smem2f", "smem3", "smem4", "smem5", "smem_adj",
-                     "smem_grad", "split1", "tq", "wpc_s", "nbx", "thx", "perx", "smem_s", "smem_x", "smem3a")
+                     "smem_grad", "split1", "tq", "wpc_s", "nbx", "thx", "perx", "smem_s", "smem_x", "smem3a",
+                     "icap3a")
 
 
 class Plan2D:
