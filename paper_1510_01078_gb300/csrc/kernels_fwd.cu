@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int 
 // (ner_value_linear), NEDNER_NER_DIRECT the direct sum over the raw line
 // (ner_value_direct, no FFT).  Everything after the NER values is shared.
 template <int W, int D, int NT, int MODE = NEDNER_NER_KB>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_ner_lines(Geo G, const __grid_constant__ TapPoly P, int LPC,
+__global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) k_ner_lines(Geo G, const __grid_constant__ TapPoly P, int LPC,
                                                                    const float2* __restrict__ Ghat,
                                                                    const float2* __restrict__ axy_tab,
                                                                    const float* __restrict__ deconv_t,
