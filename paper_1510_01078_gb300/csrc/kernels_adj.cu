@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) k_ner_lines_adj(Geo G, 
 // Transpose of ned_yfft: R[jx][gy][n] = sum_jy exp(+2 pi i jy gy / Ly) Ghat[jx][jy][n] / phihat(jy/Ly)
 // (the division by phihat(jy/Ly) is done by k_ner_lines_adj when it writes Ghat).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 3) k_ned_yfft_adj(Geo G, int C, const float2* __restrict__ Ghat,
+__global__ void __launch_bounds__(256, 4) k_ned_yfft_adj(Geo G, int C, const float2* __restrict__ Ghat,
                                                          const float* __restrict__ deconv_y,
                                                          const float2* __restrict__ tw, float2* __restrict__ R) {
     extern __shared__ float4 smem4[];
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_gather_rows2(Geo 
 static size_t xfft_adj_smem(const Chunks& c) { return c.smem_x + 16 * sizeof(float2); }
 
 template <int PER>
-__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_xfft_adj(Geo G, int nb, int nbx,
+__global__ void __launch_bounds__(256, PER <= 16 ? 4 : 2) k_ned_xfft_adj(Geo G, int nb, int nbx,
                                                                         const float2* __restrict__ R,
                                                                         const float* __restrict__ deconv_x,
                                                                         const float2* __restrict__ tw,

@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int
 // of Q is one contiguous block of Lx x 32 samples.
 // ---------------------------------------------------------------------------
 template <int PER>
-__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_xfft(Geo G, int tq, int nbx, const float* __restrict__ Q,
+__global__ void __launch_bounds__(256, PER <= 16 ? 4 : 2) k_ned_xfft(Geo G, int tq, int nbx, const float* __restrict__ Q,
                                                                     const float* __restrict__ deconv_x,
                                                                     const float2* __restrict__ tw,
                                                                     float2* __restrict__ R) {
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_xfft(Geo G, int 
 // ---------------------------------------------------------------------------
 // R holds time samples [roff, roff + rstride) (the whole record, or one chunk).
 template <int PER>
-__global__ void __launch_bounds__(256, PER <= 16 ? 3 : 2) k_ned_yfft(Geo G, int C, int yb, const float2* __restrict__ R,
+__global__ void __launch_bounds__(256, PER <= 16 ? 4 : 2) k_ned_yfft(Geo G, int C, int yb, const float2* __restrict__ R,
                                                      int rstride, int roff,
                                                      const float* __restrict__ deconv_y,
                                                      const float2* __restrict__ tw, float2* __restrict__ Ghat) {
