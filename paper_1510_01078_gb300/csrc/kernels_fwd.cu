@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_ned_spread2_xfft(Geo 
 // dense and sparse blocks do not wait for one another, and many small CTAs
 // keep every SM busy.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 6) k_ned_spread_blocks(Geo G, int t0, int tq, const float* __restrict__ g,
+__global__ void __launch_bounds__(128, 7) k_ned_spread_blocks(Geo G, int t0, int tq, const float* __restrict__ g,
                                                               const int2* __restrict__ bseg,
                                                               const int* __restrict__ bent_m,
                                                               const float* __restrict__ bent_w,
