@@ -56,6 +56,19 @@ def check(nx, ny, nz, Nt, s):
     need(s["threads3"] in (256, 512) and ny % s["lpc"] == 0, "NER: line groups")
     need(Lt * s["lpc"] <= 16 * s["threads3"] and nz * s["lpc"] <= 16 * s["threads3"], "NER: FFTs fit")
     need(s["smem3"] <= SMEM_MAX and s["smem3a"] <= SMEM_MAX, "NER and its transpose: shared memory")
+    # transposed NER: the nz + 1 depth frequencies of a line in chunks of icap3a
+    # items (value, first grid point, w + 1 tap-weight slots), all of them (at
+    # most 1025) or half where only the half fits four CTAs of 256 per SM
+    pad = lambda n: n + (n >> 4)
+    base = (pad(Lt * s["lpc"]) + pad(nz * s["lpc"])) * 8
+    per_item, four = 8 + 4 + 4 * (s["w"] + 1), 228 * 1024 // 4 - 1024
+    need(s["smem3a"] == base + s["icap3a"] * per_item, "transposed NER: items fill the rest")
+    all_items, half = min(nz + 1, 1025), (nz + 2) // 2
+    if s["icap3a"] == half and half != all_items:
+        need(s["threads3"] == 256 and base + all_items * per_item > four >= s["smem3a"],
+             "transposed NER: halves only to fit a fourth CTA")
+    else:
+        need(s["icap3a"] == all_items, "transposed NER: all items, at most 1025")
     # inverse image FFTs and their transposes: 128 threads, 16 values each
     need(nz % s["c4"] == 0 and ny * s["c4"] <= 16 * 128, "y-IFFT: fits")
     need(ny % s["c5"] == 0 and (nx // 2) * s["c5"] <= 16 * 128, "x-c2r: fits")
@@ -75,7 +88,7 @@ def test_every_accepted_geometry_meets_the_kernel_size_conditions(nd):
     failures = []
     for nx, ny, nz, Nt in itertools.product(POW2, POW2, POW2, NTS):
         for w in WIDTHS:
-            s = nd.work_split(nx, ny, nz, Nt, w)
+            s = dict(nd.work_split(nx, ny, nz, Nt, w), w=w)
             bad = check(nx, ny, nz, Nt, s)
             if bad:
                 failures.append(((nx, ny, nz, Nt, w), bad))
@@ -97,3 +110,7 @@ def test_known_splits(nd):
     assert (c3["tpl1"], c3["threads1"], c3["lpc"], c3["threads_adj"], c3["c4"], c3["c5"]) == (2, 512, 1, 512, 8, 16)
     assert (c3["split1"], c3["tq"], c3["nbx"], c3["thx"], c3["perx"]) == (1, 2048, 8, 256, 16)
     assert (c2["split1"], c2["nbx"], c2["thx"], c2["perx"]) == (1, 16, 256, 16)
+    # the transposed NER holds half of a line's depth frequencies at a time on
+    # both (257 of 513 on C3, 55.6 KB; 129 of 257 on C2), for four CTAs per SM
+    assert (c3["icap3a"], c3["smem3a"]) == (257, 55616)
+    assert (c2["icap3a"], c2["smem3a"]) == (129, 51776)
